@@ -1,0 +1,141 @@
+/*
+ * ttround.h -- C ABI of the GB300 randomized TT-rounding library.
+ *
+ * Method: Al Daas, Ballard, Cazeaux, Hallman, Miedlar, Pasha, Reid, Saibaba,
+ * "Randomized algorithms for rounding in the Tensor-Train format".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - A TT-tensor of order N has cores T_n, n = 1..N, with ranks R_0 = R_N = 1
+ *   (Section 2.1). Core n is an array of R_{n-1} * I_n * R_n doubles in C
+ *   order (R_{n-1}, I_n, R_n): element (a, i, b) is at offset (a*I_n + i)*R_n + b.
+ *   With this layout the horizontal unfolding H(T_n) (R_{n-1} x I_n R_n) and a
+ *   row-permuted vertical unfolding V(T_n) ((R_{n-1} I_n) x R_n) are plain
+ *   row-major views (Section 2.1, Fig. 1).
+ * - A sum of K TT-tensors (Section 3.4) is passed as K*N core pointers,
+ *   cores[j*N + n-1] = core n of summand j, and ranks[j*(N+1) + n] = R^{(j)}_n.
+ * - Pointers named "device" are CUDA device pointers owned by the caller; the
+ *   library never frees or keeps them. Pointers named "host" are host memory
+ *   read during the call only.
+ * - stream is a cudaStream_t passed as void*. All device work is enqueued on it;
+ *   inputs are never modified. Calls return after enqueueing unless a tolerance
+ *   is given (the data-dependent output ranks are then read back, which
+ *   synchronizes the stream once at the end).
+ * - workspace: device scratch of at least the size the matching *_workspace
+ *   query returns, 256-byte aligned. NULL lets the library allocate (and free)
+ *   it stream-ordered with cudaMallocAsync.
+ * - Every function returns a tt_status; on failure tt_last_error() (thread
+ *   local) describes it. Nothing is written to outputs on argument errors.
+ */
+#ifndef TTROUND_H
+#define TTROUND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_OK = 0,
+  TT_EINVAL = 1,        /* invalid sizes, ranks, pointers or options */
+  TT_ENOMEM = 2,        /* allocation failed or workspace too small */
+  TT_ECUDA = 3,         /* a CUDA call failed (message has the CUDA error) */
+  TT_ENONFINITE = 4,    /* non-finite values met where the method needs finite ones */
+  TT_ESINGULAR = 5,     /* a triangular factor needed by the adjoint is singular */
+  TT_ETIMEOUT = 6,      /* a bounded device wait gave up */
+  TT_EUNSUPPORTED = 7   /* size or option outside what this build handles */
+} tt_status;
+
+typedef enum {
+  TT_PREC_FP64 = 0,     /* every step in float64 */
+  TT_PREC_MIXED = 1     /* contractions on the tensor cores (see tt_round_sum_rand) */
+} tt_precision;
+
+/* Library version string and the last error message of the calling thread. */
+const char* tt_version(void);
+const char* tt_last_error(void);
+
+/*
+ * tt_sketch_gaussian -- random Gaussian TT of Definition 3.1 (Section 3.2):
+ * core n (ells[n-1] x dims[n-1] x ells[n]) gets i.i.d. N(0, 1/(l_{n-1} I_n l_n))
+ * entries drawn with the counter-based generator Philox4x32-10 (Salmon et al.,
+ * SC'11) and the Box-Muller transform: entry e of core n uses counter
+ * (e/2 mod 2^32, e/2 div 2^32, n-1, 0x7474726e) and key (seed mod 2^32,
+ * seed div 2^32); u = (52 bits of the output + 1/2) 2^-52; even entries take
+ * the cosine, odd entries the sine branch.
+ *   N     order;  dims (host, N);  ells (host, N+1, ells[0] = ells[N] = 1)
+ *   out   (host array of N device pointers), core n needs ells[n-1]*dims[n-1]*ells[n] doubles
+ * Errors: TT_EINVAL for N < 1, non-positive sizes, NULL pointers.
+ */
+int tt_sketch_gaussian(int32_t N, const int64_t* dims, const int64_t* ells, uint64_t seed,
+                       double* const* out, void* stream);
+
+/*
+ * tt_round_sum_rand -- Algorithm 7 (TT-Rounding of a Sum,
+ * Randomize-then-Orthogonalize, Section 3.4), with Algorithm 3 (right-to-left
+ * partial contractions, Section 2.3) for every summand against one shared
+ * Gaussian TT sketch (Definition 3.1), then the left-to-right sweep: sketch
+ * Y_n = V(X_n)[W^{(1)}_n; ...; W^{(K)}_n], thin QR, projection
+ * [M^{(1)}_n ... M^{(K)}_n] = V(X_n)^T Z_n, next-core update slice by slice and
+ * X_N = sum_j M^{(j)}_{N-1} Y^{(j)}_N. The block cores of the sum are never
+ * formed. With tol > 0 the left-orthogonal result is truncated as in
+ * Section 3.2 (Algorithm 2's truncation loop run right to left):
+ * eps = tol ||X|| / sqrt(N-1), so that ||X_out - X|| <= tol ||X|| where X is
+ * the untruncated randomized result.
+ *   N, K          order and number of summands (K >= 1)
+ *   dims          host, N mode sizes
+ *   ranks         host, K*(N+1) summand ranks (ranks[j*(N+1)] = ranks[j*(N+1)+N] = 1)
+ *   cores         host array of K*N device pointers (see conventions)
+ *   coeffs        host, K scalars multiplying the summands, or NULL for all ones
+ *   ells          host, N+1 target sketch ranks l_n (oversampling included,
+ *                 Section 3); clamped to l_n <= min(l_{n-1} I_n, I_{n+1} l_{n+1})
+ *   sketch        host array of N device pointers to the sketch cores
+ *                 (l_{n-1} x I_n x l_n, clamped ranks), or NULL to draw them on
+ *                 the device from seed exactly as tt_sketch_gaussian does
+ *   tol           <= 0: fixed ranks l_n; > 0: relative truncation tolerance
+ *   precision     TT_PREC_FP64 or TT_PREC_MIXED
+ *   out           host array of N device pointers; core n needs
+ *                 l_{n-1}*I_n*l_n doubles (clamped ranks); the result is written
+ *                 compactly as (r_{n-1}, I_n, r_n)
+ *   out_ranks     host, N+1, receives r_0..r_N
+ * Errors: TT_EINVAL (bad sizes/ranks/pointers), TT_EUNSUPPORTED (a target rank
+ * above 96 or other limits of this build), TT_ENOMEM, TT_ECUDA.
+ */
+int tt_round_sum_rand(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                      const double* const* cores, const double* coeffs, const int64_t* ells,
+                      const double* const* sketch, uint64_t seed, double tol, int32_t precision,
+                      double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
+                      void* stream);
+size_t tt_round_sum_rand_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                                   const int64_t* ells, double tol, int32_t precision);
+
+/*
+ * tt_round_rand -- Algorithm 5 (Randomize-then-Orthogonalize, Section 3.2):
+ * the single-tensor case K = 1 of tt_round_sum_rand, same arguments with
+ * ranks of length N+1 and N core pointers.
+ */
+int tt_round_rand(int32_t N, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+                  const int64_t* ells, const double* const* sketch, uint64_t seed, double tol,
+                  int32_t precision, double* const* out, int64_t* out_ranks, void* workspace,
+                  size_t workspace_bytes, void* stream);
+
+/*
+ * Measurement hooks (no counterpart in the paper; used by the benchmark).
+ * tt_prof_enable(1) makes the library record a CUDA event pair on the caller's
+ * stream around every grouped-GEMM launch (all contraction steps) and add up the
+ * algorithmic flops 2*M*N*K of those launches; every kernel launch of the
+ * library is counted whether or not profiling is on. tt_prof_read waits for the
+ * recorded events and returns: total GEMM time (ms), GEMM flops, number of
+ * GEMM launches and of all kernel launches since the last tt_prof_reset.
+ * Any output pointer may be NULL. Errors: TT_ECUDA if an event query fails.
+ */
+int tt_prof_enable(int on);
+int tt_prof_reset(void);
+int tt_prof_read(double* gemm_ms, double* gemm_flops, int64_t* gemm_launches, int64_t* kernel_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTROUND_H */

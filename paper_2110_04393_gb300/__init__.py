@@ -1,0 +1,20 @@
+"""Randomized TT-rounding on GB300 (Al Daas et al., "Randomized algorithms for
+rounding in the Tensor-Train format").
+
+Python names mirror the C ABI of include/ttround.h. This layer only marshals
+arguments: it checks and allocates torch CUDA tensors, passes raw device
+pointers and the current CUDA stream, and reshapes the outputs. Every step of
+the computation runs in the library's CUDA kernels; there is no fallback.
+
+TT cores are torch.float64 CUDA tensors of shape (R_{n-1}, I_n, R_n),
+C-contiguous.
+"""
+from __future__ import annotations
+
+from .api import (tt_version, tt_sketch_gaussian, tt_round_sum_rand, tt_round_rand, TTError,
+                  prof_enable, prof_reset, prof_read,
+                  PREC_FP64, PREC_MIXED)
+from .costs import flops_sum_randorth, bytes_sum_randorth
+
+__all__ = ["tt_version", "tt_sketch_gaussian", "tt_round_sum_rand", "tt_round_rand", "TTError",
+           "PREC_FP64", "PREC_MIXED", "flops_sum_randorth", "bytes_sum_randorth"]

@@ -1,0 +1,52 @@
+"""Loader of the in-tree CUDA library (libttround.so). There is no CPU
+fallback: importing a compute entry point without the library raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libttround.so")
+_lib = None
+
+c_i32, c_i64, c_u64, c_dbl, c_size, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
+                                             ctypes.c_size_t, ctypes.c_void_p)
+P_i64 = ctypes.POINTER(ctypes.c_int64)
+P_dbl = ctypes.POINTER(ctypes.c_double)
+P_vp = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes), mirroring include/ttround.h
+SIGNATURES = {
+    "tt_version": (ctypes.c_char_p, []),
+    "tt_last_error": (ctypes.c_char_p, []),
+    "tt_sketch_gaussian": (c_i32, [c_i32, P_i64, P_i64, c_u64, P_vp, c_vp]),
+    "tt_round_sum_rand": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl, c_i32,
+                                  P_vp, P_i64, c_vp, c_size, c_vp]),
+    "tt_round_sum_rand_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64, c_dbl, c_i32]),
+    "tt_round_rand": (c_i32, [c_i32, P_i64, P_i64, P_vp, P_i64, P_vp, c_u64, c_dbl, c_i32, P_vp, P_i64, c_vp,
+                              c_size, c_vp]),
+    "tt_prof_enable": (c_i32, [c_i32]),
+    "tt_prof_reset": (c_i32, []),
+    "tt_prof_read": (c_i32, [P_dbl, P_dbl, P_i64, P_i64]),
+}
+
+
+def lib():
+    """The loaded library (raises RuntimeError if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing; run "
+                               "python -c 'import __graft_entry__ as g; g.build()'")
+        l = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            if hasattr(l, name):
+                f = getattr(l, name)
+                f.restype = res
+                f.argtypes = args
+        _lib = l
+    return _lib
+
+
+def last_error() -> str:
+    return lib().tt_last_error().decode()

@@ -1,0 +1,154 @@
+"""Argument marshalling for the C ABI (no arithmetic of the method here)."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as nat
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+_PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED, PREC_FP64: PREC_FP64, PREC_MIXED: PREC_MIXED}
+
+
+class TTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ttround error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != 0:
+        raise TTError(rc, nat.last_error())
+
+
+def _i64(vals):
+    vals = [int(v) for v in vals]
+    return (ctypes.c_int64 * max(len(vals), 1))(*vals)
+
+
+def _ptrs(tensors):
+    return (ctypes.c_void_p * max(len(tensors), 1))(*[t.data_ptr() for t in tensors])
+
+
+def _stream(stream, device):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_core(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 3
+            and t.is_contiguous()):
+        raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor of shape (r0, I, r1)")
+
+
+def tt_version() -> str:
+    return nat.lib().tt_version().decode()
+
+
+def tt_sketch_gaussian(dims, ells, seed, *, device=None, stream=None):
+    """Gaussian TT of Definition 3.1 drawn on the device (Philox4x32-10)."""
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    device = torch.device(device or "cuda")
+    out = [torch.empty((int(ells[n]), dims[n], int(ells[n + 1])), dtype=torch.float64, device=device)
+           for n in range(N)]
+    _check(nat.lib().tt_sketch_gaussian(N, _i64(dims), _i64(ells), ctypes.c_uint64(int(seed)), _ptrs(out),
+                                        _stream(stream, device)))
+    return out
+
+
+def clamp_ranks(dims, ells):
+    N = len(dims)
+    ell = [1] + [int(x) for x in ells[1:N]] + [1]
+    for n in range(1, N):
+        ell[n] = min(ell[n], ell[n - 1] * dims[n - 1])
+    for n in range(N - 1, 0, -1):
+        ell[n] = min(ell[n], ell[n + 1] * dims[n])
+    return ell
+
+
+def tt_round_sum_rand(summands, ells, *, tol=0.0, sketch=None, seed=0, coeffs=None, precision="fp64",
+                      workspace=None, stream=None):
+    """Algorithm 7 (sum of TTs, Randomize-then-Orthogonalize) on the GPU.
+
+    summands: list of K TTs (lists of N cores). ells: N+1 target ranks.
+    sketch: optional list of N sketch cores (l_{n-1}, I_n, l_n); None draws it
+    on the device from seed. Returns the list of output cores."""
+    K = len(summands)
+    N = len(summands[0])
+    device = summands[0][0].device
+    dims = [int(c.shape[1]) for c in summands[0]]
+    ranks = []
+    flat = []
+    for j, Y in enumerate(summands):
+        if len(Y) != N:
+            raise ValueError("all summands need the same order")
+        ranks += [int(Y[0].shape[0])] + [int(c.shape[2]) for c in Y]
+        for n, c in enumerate(Y):
+            _check_core(c, f"summand {j} core {n}")
+            if int(c.shape[1]) != dims[n]:
+                raise ValueError("mode sizes differ between summands")
+    for Y in summands:
+        flat += list(Y)
+    ell = clamp_ranks(dims, ells)
+    out = [torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float64, device=device) for n in range(N)]
+    sk_arr = None
+    if sketch is not None:
+        for n, c in enumerate(sketch):
+            _check_core(c, f"sketch core {n}")
+            if tuple(c.shape) != (ell[n], dims[n], ell[n + 1]):
+                raise ValueError(f"sketch core {n} has shape {tuple(c.shape)}, expected "
+                                 f"{(ell[n], dims[n], ell[n + 1])}")
+        sk_arr = _ptrs(sketch)
+    co = None
+    if coeffs is not None:
+        co = (ctypes.c_double * K)(*[float(c) for c in coeffs])
+    prec = _PREC[precision]
+    L = nat.lib()
+    dims_a, ranks_a, ell_a = _i64(dims), _i64(ranks), _i64(ell)
+    ws_bytes = 0
+    ws_ptr = None
+    if workspace is None:
+        ws_bytes = L.tt_round_sum_rand_workspace(N, K, dims_a, ranks_a, ell_a, float(tol), prec)
+        if ws_bytes == 0:
+            _check(L.tt_round_sum_rand(N, K, dims_a, ranks_a, _ptrs(flat), co, ell_a, sk_arr, 0, float(tol), prec,
+                                       None, None, None, 0, None) or 1)
+        workspace = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=device)
+    ws_ptr = workspace.data_ptr()
+    ws_ptr += (-ws_ptr) % 256
+    ws_bytes = workspace.numel() - (ws_ptr - workspace.data_ptr())
+    out_ranks = (ctypes.c_int64 * (N + 1))()
+    _check(L.tt_round_sum_rand(N, K, dims_a, ranks_a, _ptrs(flat), co, ell_a, sk_arr, ctypes.c_uint64(int(seed)),
+                               float(tol), prec, _ptrs(out), out_ranks, ctypes.c_void_p(ws_ptr), ws_bytes,
+                               _stream(stream, device)))
+    r = [int(x) for x in out_ranks]
+    res = []
+    for n in range(N):
+        cnt = r[n] * dims[n] * r[n + 1]
+        res.append(out[n].view(-1)[:cnt].view(r[n], dims[n], r[n + 1]))
+    return res
+
+
+def tt_round_rand(Y, ells, **kw):
+    """Algorithm 5 (single TT, Randomize-then-Orthogonalize): tt_round_sum_rand with K = 1."""
+    if kw.get("coeffs") is not None:
+        raise ValueError("tt_round_rand takes no coefficients")
+    return tt_round_sum_rand([Y], ells, **kw)
+
+
+def prof_enable(on=True):
+    _check(nat.lib().tt_prof_enable(1 if on else 0))
+
+
+def prof_reset():
+    _check(nat.lib().tt_prof_reset())
+
+
+def prof_read():
+    """(gemm_ms, gemm_flops, gemm_launches, kernel_launches) since the last reset."""
+    ms, fl = ctypes.c_double(), ctypes.c_double()
+    gl, kl = ctypes.c_int64(), ctypes.c_int64()
+    _check(nat.lib().tt_prof_read(ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(gl), ctypes.byref(kl)))
+    return ms.value, fl.value, gl.value, kl.value

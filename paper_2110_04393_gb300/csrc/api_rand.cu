@@ -1,0 +1,417 @@
+// C ABI: planner + stream-ordered execution of the randomized roundings.
+//
+// tt_round_sum_rand follows Algorithm 7 (Section 3.4):
+//   RL sweep (Algorithm 3 per summand, shared sketch), n = N..2:
+//     Z^{(j)}   = V(Y^{(j)}_n) W^{(j)}_n                 (one grouped GEMM, all j)
+//     W^{(j)}_{n-1} = H(Z^{(j)}) H(Omega_n)^T            (one grouped split-K GEMM)
+//   LR sweep, n = 1..N-1 (M_0 = the summand coefficients):
+//     X_n(:, i, :) = [M^{(j)}_{n-1} Y^{(j)}_n(:, i, :)]_j (batched over i and j)
+//     Y_n = V(X_n) [W^{(1)}_n; ...; W^{(K)}_n]           (GEMM)
+//     V(Xout_n) = Q of TSQR(Y_n)                         (thin Householder QR)
+//     [M^{(1)}_n ... M^{(K)}_n] = Q^T V(X_n)             (split-K GEMM)
+//   last core: X_N = sum_j M^{(j)}_{N-1} Y^{(j)}_N, i.e. V(X_N) times a column of ones.
+// With tol > 0 the left-orthogonal result is truncated right to left
+// (Section 3.2 with Algorithm 2's loop mirrored): per bond TSQR of H(X_n)^T,
+// the eps-rule on R, then X_n := (Q G1)^T and X_{n-1} := X_{n-1} G2.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "plan.cuh"
+#include "qr.cuh"
+
+namespace ttr {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+int plan_workspace_bytes(const BuildFn& build, size_t* bytes) {
+  Arena a;
+  a.sizing = true;
+  Schedule s;
+  TTR_TRY(build(a, s));
+  *bytes = a.used + align256(size_t(s.pbuf_need) * sizeof(double)) + align256(s.descs.size() * sizeof(GemmDesc)) + 256;
+  return TT_OK;
+}
+
+int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStream_t st) {
+  size_t need = 0;
+  Schedule probe;
+  {
+    Arena a;
+    a.sizing = true;
+    TTR_TRY(build(a, probe));
+    need = a.used + align256(size_t(probe.pbuf_need) * sizeof(double)) +
+           align256(probe.descs.size() * sizeof(GemmDesc)) + 256;
+  }
+  void* ws = workspace;
+  bool owned = false;
+  if (ws == nullptr) {
+    if (need > 0) {
+      cudaError_t e = cudaMallocAsync(&ws, need, st);
+      if (e != cudaSuccess) {
+        set_error(std::string("workspace allocation of ") + std::to_string(need) + " bytes failed: " +
+                  cudaGetErrorString(e));
+        return TT_ENOMEM;
+      }
+      owned = true;
+    }
+  } else if (ws_bytes < need) {
+    set_error("workspace too small: need " + std::to_string(need) + " bytes, got " + std::to_string(ws_bytes));
+    return TT_ENOMEM;
+  } else if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) {
+    set_error("workspace must be 256-byte aligned");
+    return TT_EINVAL;
+  }
+  Arena a;
+  a.sizing = false;
+  a.base = static_cast<char*>(ws);
+  a.cap = need;
+  Schedule s;
+  s.pbuf = a.take<double>(size_t(std::max<int64_t>(probe.pbuf_need, 1)));
+  GemmDesc* d_descs = a.take<GemmDesc>(std::max<size_t>(probe.descs.size(), 1));
+  int rc = build(a, s);
+  if (rc == TT_OK && !s.descs.empty()) {
+    cudaError_t e = cudaMemcpyAsync(d_descs, s.descs.data(), s.descs.size() * sizeof(GemmDesc),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      set_error(std::string("descriptor upload: ") + cudaGetErrorString(e));
+      rc = TT_ECUDA;
+    }
+  }
+  for (size_t i = 0; rc == TT_OK && i < s.items.size(); ++i) rc = s.items[i](st, d_descs);
+  if (owned) cudaFreeAsync(ws, st);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Validation of a TT-sum problem.
+struct SumProblem {
+  int N = 0, K = 0;
+  std::vector<int64_t> I;      // [N]
+  std::vector<int64_t> R;      // [K*(N+1)]
+  std::vector<int64_t> S;      // [N+1] sum of summand ranks per bond
+  std::vector<int64_t> off;    // [K*(N+1)] prefix of summand ranks per bond
+  std::vector<int64_t> ell;    // [N+1] clamped sketch ranks
+  std::vector<const double*> cores;
+  std::vector<double> coeffs;
+  int64_t r(int j, int n) const { return R[size_t(j) * (N + 1) + n]; }
+  int64_t o(int j, int n) const { return off[size_t(j) * (N + 1) + n]; }
+  const double* core(int j, int n) const { return cores[size_t(j) * N + (n - 1)]; }   // n is 1-based
+};
+
+static int validate_sum(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+                        const double* coeffs, const int64_t* ells, bool need_cores, SumProblem* P) {
+  if (N < 1 || K < 1 || !dims || !ranks || !ells || (need_cores && !cores)) {
+    set_error("invalid arguments: need N >= 1, K >= 1 and non-null dims/ranks/ells/cores");
+    return TT_EINVAL;
+  }
+  P->N = N;
+  P->K = K;
+  P->I.assign(dims, dims + N);
+  P->R.assign(ranks, ranks + size_t(K) * (N + 1));
+  for (int n = 0; n < N; ++n)
+    if (P->I[n] < 1) { set_error("mode sizes must be positive"); return TT_EINVAL; }
+  for (int j = 0; j < K; ++j) {
+    if (P->r(j, 0) != 1 || P->r(j, N) != 1) { set_error("summand ranks must start and end with 1"); return TT_EINVAL; }
+    for (int n = 0; n <= N; ++n)
+      if (P->r(j, n) < 1) { set_error("ranks must be positive"); return TT_EINVAL; }
+  }
+  P->S.assign(N + 1, 0);
+  P->off.assign(size_t(K) * (N + 1), 0);
+  for (int n = 0; n <= N; ++n) {
+    int64_t acc = 0;
+    for (int j = 0; j < K; ++j) {
+      P->off[size_t(j) * (N + 1) + n] = acc;
+      acc += P->r(j, n);
+    }
+    P->S[n] = acc;
+  }
+  if (need_cores) {
+    P->cores.assign(cores, cores + size_t(K) * N);
+    for (auto* c : P->cores)
+      if (!c) { set_error("null core pointer"); return TT_EINVAL; }
+  } else {
+    P->cores.assign(size_t(K) * N, nullptr);
+  }
+  P->coeffs.assign(K, 1.0);
+  if (coeffs) P->coeffs.assign(coeffs, coeffs + K);
+  // target ranks: l_0 = l_N = 1, l_n <= min(l_{n-1} I_n, I_{n+1} l_{n+1})
+  P->ell.assign(ells, ells + N + 1);
+  P->ell[0] = 1;
+  P->ell[N] = 1;
+  for (int n = 1; n < N; ++n)
+    if (P->ell[n] < 1) { set_error("target ranks must be positive"); return TT_EINVAL; }
+  for (int n = 1; n < N; ++n) P->ell[n] = std::min(P->ell[n], P->ell[n - 1] * P->I[n - 1]);
+  for (int n = N - 1; n >= 1; --n) P->ell[n] = std::min(P->ell[n], P->ell[n + 1] * P->I[n]);
+  for (int n = 1; n < N; ++n)
+    if (P->ell[n] > TSQR_KMAX) {
+      set_error("target rank " + std::to_string(P->ell[n]) + " above the supported maximum " +
+                std::to_string(TSQR_KMAX));
+      return TT_EUNSUPPORTED;
+    }
+  return TT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Right-to-left truncation of a left-orthogonal TT held in caller buffers
+// (padded layout (l_{n-1}, I_n, l_n)); decided ranks land in rk[0..N] (device).
+struct TruncBufs {
+  double* eps;      // [2]: eps, ||X||
+  int64_t* rk;      // [N+1]
+  double* Qt;       // max m*k
+  double* Rb;       // k*k
+  double* G1;
+  double* G2;
+  double* sig;
+  double* tmp;      // max core size
+};
+
+static int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int64_t>& I,
+                           const std::vector<int64_t>& ell, double tol, double* const* out, int64_t** rk_out) {
+  TruncBufs b;
+  int64_t qmax = 1, kmax = 1, cmax = 1;
+  for (int n = 2; n <= N; ++n) {
+    const int64_t m = I[n - 1] * ell[n], k = ell[n - 1];
+    qmax = std::max(qmax, m * k);
+    kmax = std::max(kmax, k);
+  }
+  for (int n = 1; n <= N; ++n) cmax = std::max(cmax, ell[n - 1] * I[n - 1] * ell[n]);
+  b.eps = ar.take<double>(2);
+  b.rk = ar.take<int64_t>(N + 1);
+  b.Qt = ar.take<double>(qmax);
+  b.Rb = ar.take<double>(kmax * kmax);
+  b.G1 = ar.take<double>(kmax * kmax);
+  b.G2 = ar.take<double>(kmax * kmax);
+  b.sig = ar.take<double>(kmax);
+  b.tmp = ar.take<double>(cmax);
+  *rk_out = b.rk;
+  std::vector<QrBufs> qb(N + 1);
+  for (int n = 2; n <= N; ++n) qb[n] = qr_reserve(ar, I[n - 1] * ell[n], int(ell[n - 1]));
+
+  {   // int64 ranks staged through a double-sized host buffer
+    std::vector<int64_t> tmp(ell.begin(), ell.end());
+    std::vector<double> raw(N + 1);
+    std::memcpy(raw.data(), tmp.data(), sizeof(int64_t) * (N + 1));
+    sc.upload(reinterpret_cast<double*>(b.rk), raw);
+  }
+  sc.add([=](cudaStream_t s) -> int {
+    return norm_eps_launch(out[N - 1], ell[N - 1] * I[N - 1], tol, N, b.eps, s);
+  });
+  for (int n = N; n >= 2; --n) {
+    const int64_t m = I[n - 1] * ell[n], k = ell[n - 1];
+    double* Xn = out[n - 1];
+    double* Xp = out[n - 2];
+    qr_plan(sc, qb[n], Xn, 1, m, b.Qt, k, 1, b.Rb);
+    sc.add([=](cudaStream_t s) -> int {
+      return svd_trunc_launch(int(k), b.Rb, b.eps, int(k), b.G1, b.G2, b.sig, b.rk + (n - 1), s);
+    });
+    // new H(X_n) = (Q G1)^T : column-major m x k view of core n
+    sc.gemm({gdesc(b.Qt, k, 1, b.G1, k, 1, Xn, 1, m, m, k, k)});
+    // V(X_{n-1}) := V(X_{n-1}) G2
+    const int64_t mp = ell[n - 2] * I[n - 2];
+    sc.gemm({gdesc(Xp, k, 1, b.G2, k, 1, b.tmp, k, 1, mp, k, k)});
+    sc.add([=](cudaStream_t s) -> int {
+      if (!Xp) return int(TT_OK);
+      TTR_CHECK_CUDA(cudaMemcpyAsync(Xp, b.tmp, sizeof(double) * mp * k, cudaMemcpyDeviceToDevice, s));
+      return int(TT_OK);
+    });
+  }
+  // compact every core to its decided ranks
+  for (int n = 1; n <= N; ++n) {
+    double* Xn = out[n - 1];
+    const int64_t r0 = ell[n - 1], In = I[n - 1], r1 = ell[n];
+    sc.add([=](cudaStream_t s) -> int {
+      if (!Xn) return int(TT_OK);
+      TTR_CHECK_CUDA(cudaMemcpyAsync(b.tmp, Xn, sizeof(double) * r0 * In * r1, cudaMemcpyDeviceToDevice, s));
+      return compact_core_launch(b.tmp, Xn, r0, In, r1, b.rk + (n - 1), b.rk + n, s);
+    });
+  }
+  return TT_OK;
+}
+
+// ---------------------------------------------------------------------------
+static int build_sum_rand_fp64(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol,
+                               double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev) {
+  const int N = P.N, K = P.K;
+  const auto& I = P.I;
+  const auto& S = P.S;
+  const auto& ell = P.ell;
+  auto In = [&](int n) { return I[n - 1]; };   // 1-based mode size
+
+  // ---- workspace
+  std::vector<double*> W(N + 1, nullptr);
+  for (int n = 1; n <= N; ++n) W[n] = ar.take<double>(S[n] * ell[n]);
+  int64_t zmax = 1, xmax = 1, ymax = 1, mmax = 1;
+  for (int n = 2; n <= N; ++n) zmax = std::max(zmax, S[n - 1] * In(n) * ell[n]);
+  for (int n = 1; n <= N; ++n) xmax = std::max(xmax, ell[n - 1] * In(n) * S[n]);
+  for (int n = 1; n < N; ++n) ymax = std::max(ymax, ell[n - 1] * In(n) * ell[n]);
+  for (int n = 0; n < N; ++n) mmax = std::max(mmax, ell[n] * S[n]);
+  double* Z = ar.take<double>(zmax);
+  double* X = ar.take<double>(xmax);
+  double* Ys = ar.take<double>(ymax);
+  double* Mb[2] = {ar.take<double>(mmax), ar.take<double>(mmax)};
+  std::vector<const double*> sk(N + 1, nullptr);
+  std::vector<double*> skw(N + 1, nullptr);
+  for (int n = 2; n <= N; ++n) {
+    if (sketch_in) {
+      sk[n] = sketch_in[n - 1];
+    } else {
+      skw[n] = ar.take<double>(ell[n - 1] * In(n) * ell[n]);
+      sk[n] = skw[n];
+    }
+  }
+  std::vector<QrBufs> qb(N + 1);
+  for (int n = 1; n < N; ++n) qb[n] = qr_reserve(ar, ell[n - 1] * In(n), int(ell[n]));
+
+  // ---- set-up: counters, W_N = ones, M_0 = coefficients, sketch
+  sc.add([=](cudaStream_t s) -> int { return fill_launch(W[N], S[N] * ell[N], 1.0, s); });
+  sc.upload(Mb[0], P.coeffs);
+  if (!sketch_in) {
+    for (int n = 2; n <= N; ++n) {
+      double* dst = skw[n];
+      const int64_t a = ell[n - 1], b = In(n), c = ell[n];
+      sc.add([=](cudaStream_t s) -> int { return sketch_launch(dst, a, b, c, n - 1, seed, s); });
+    }
+  }
+
+  // ---- right-to-left partial contractions (Algorithm 3 for every summand)
+  for (int n = N; n >= 2; --n) {
+    std::vector<GemmDesc> ga, gb;
+    for (int j = 0; j < K; ++j) {
+      const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
+      double* Zj = Z ? Z + P.o(j, n - 1) * In(n) * ell[n] : nullptr;
+      const double* Wj = W[n] ? W[n] + P.o(j, n) * ell[n] : nullptr;
+      ga.push_back(gdesc(P.core(j, n), r1, 1, Wj, ell[n], 1, Zj, ell[n], 1, r0 * In(n), ell[n], r1));
+      double* Wo = W[n - 1] ? W[n - 1] + P.o(j, n - 1) * ell[n - 1] : nullptr;
+      gb.push_back(gdesc(Zj, In(n) * ell[n], 1, sk[n], 1, In(n) * ell[n], Wo, ell[n - 1], 1, r0, ell[n - 1],
+                         In(n) * ell[n]));
+    }
+    sc.gemm(ga);
+    sc.gemm(gb);
+  }
+
+  // ---- left-to-right sweep
+  for (int n = 1; n <= N; ++n) {
+    const double* Mp = Mb[(n - 1) & 1];
+    double* Mn = Mb[n & 1];
+    std::vector<GemmDesc> gc;
+    for (int j = 0; j < K; ++j) {
+      const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
+      GemmDesc d = gdesc(Mp ? Mp + P.o(j, n - 1) : nullptr, S[n - 1], 1, P.core(j, n), In(n) * r1, 1,
+                         X ? X + P.o(j, n) : nullptr, In(n) * S[n], 1, ell[n - 1], r1, r0);
+      d.batch = int32_t(In(n));
+      d.a_bs = 0;
+      d.b_bs = r1;
+      d.c_bs = S[n];
+      gc.push_back(d);
+    }
+    sc.gemm(gc);
+    double* dst = (n < N) ? Ys : out[N - 1];
+    sc.gemm({gdesc(X, S[n], 1, W[n], ell[n], 1, dst, ell[n], 1, ell[n - 1] * In(n), ell[n], S[n])});
+    if (n == N) break;
+    const int64_t m = ell[n - 1] * In(n), k = ell[n];
+    double* Qn = out[n - 1];
+    qr_plan(sc, qb[n], Ys, k, 1, Qn, k, 1, nullptr);
+    sc.gemm({gdesc(Qn, 1, k, X, S[n], 1, Mn, S[n], 1, k, S[n], m)});
+  }
+
+  if (tol > 0.0) TTR_TRY(plan_truncation(ar, sc, N, I, ell, tol, out, rk_dev));
+  return TT_OK;
+}
+
+}  // namespace ttr
+
+using namespace ttr;
+
+extern "C" {
+
+const char* tt_version(void) { return "ttround-gb300 0.1 (sm_103a)"; }
+const char* tt_last_error(void) { return g_err.c_str(); }
+
+int tt_sketch_gaussian(int32_t N, const int64_t* dims, const int64_t* ells, uint64_t seed, double* const* out,
+                       void* stream) {
+  if (N < 1 || !dims || !ells || !out) {
+    set_error("tt_sketch_gaussian: invalid arguments");
+    return TT_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int n = 1; n <= N; ++n) {
+    if (dims[n - 1] < 1 || ells[n - 1] < 1 || ells[n] < 1 || !out[n - 1]) {
+      set_error("tt_sketch_gaussian: invalid sizes or null output");
+      return TT_EINVAL;
+    }
+  }
+  for (int n = 1; n <= N; ++n) TTR_TRY(sketch_launch(out[n - 1], ells[n - 1], dims[n - 1], ells[n], n - 1, seed, s));
+  return TT_OK;
+}
+
+static int sum_rand_common(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                           const double* const* cores, const double* coeffs, const int64_t* ells,
+                           const double* const* sketch, uint64_t seed, double tol, int32_t precision,
+                           double* const* out, int64_t* out_ranks, void* workspace, size_t ws_bytes,
+                           void* stream, size_t* size_only) {
+  SumProblem P;
+  TTR_TRY(validate_sum(N, K, dims, ranks, cores, coeffs, ells, size_only == nullptr, &P));
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
+    set_error("unknown precision mode");
+    return TT_EINVAL;
+  }
+  if (precision == TT_PREC_MIXED) {
+    set_error("mixed precision is not available in this build");
+    return TT_EUNSUPPORTED;
+  }
+  if (size_only == nullptr) {
+    if (!out || !out_ranks) { set_error("null output arrays"); return TT_EINVAL; }
+    for (int n = 0; n < N; ++n)
+      if (!out[n]) { set_error("null output core pointer"); return TT_EINVAL; }
+    if (sketch)
+      for (int n = 1; n < N; ++n)
+        if (!sketch[n]) { set_error("null sketch core pointer"); return TT_EINVAL; }
+  }
+  int64_t* rk_dev = nullptr;
+  std::vector<double*> out_v(N, nullptr);
+  if (out) out_v.assign(out, out + N);
+  BuildFn build = [&](Arena& ar, Schedule& sc) {
+    return build_sum_rand_fp64(P, sketch, seed, tol, out_v.data(), ar, sc, &rk_dev);
+  };
+  if (size_only) return plan_workspace_bytes(build, size_only);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TTR_TRY(plan_execute(build, workspace, ws_bytes, s));
+  if (tol > 0.0) {
+    std::vector<int64_t> rk(N + 1);
+    TTR_CHECK_CUDA(cudaMemcpyAsync(rk.data(), rk_dev, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, s));
+    TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+    for (int n = 0; n <= N; ++n) out_ranks[n] = rk[n];
+  } else {
+    for (int n = 0; n <= N; ++n) out_ranks[n] = P.ell[n];
+  }
+  return TT_OK;
+}
+
+int tt_round_sum_rand(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+                      const double* coeffs, const int64_t* ells, const double* const* sketch, uint64_t seed,
+                      double tol, int32_t precision, double* const* out, int64_t* out_ranks, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  return sum_rand_common(N, K, dims, ranks, cores, coeffs, ells, sketch, seed, tol, precision, out, out_ranks,
+                         workspace, workspace_bytes, stream, nullptr);
+}
+
+size_t tt_round_sum_rand_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                                   const int64_t* ells, double tol, int32_t precision) {
+  size_t bytes = 0;
+  if (sum_rand_common(N, K, dims, ranks, nullptr, nullptr, ells, nullptr, 0, tol, precision, nullptr, nullptr,
+                      nullptr, 0, nullptr, &bytes) != TT_OK)
+    return 0;
+  return bytes;
+}
+
+int tt_round_rand(int32_t N, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+                  const int64_t* ells, const double* const* sketch, uint64_t seed, double tol, int32_t precision,
+                  double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes, void* stream) {
+  return sum_rand_common(N, 1, dims, ranks, cores, nullptr, ells, sketch, seed, tol, precision, out, out_ranks,
+                         workspace, workspace_bytes, stream, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Declarations of the device kernels' host launchers (internal to the library).
+#pragma once
+#include "common.cuh"
+
+namespace ttr {
+
+// ----------------------------------------------------------------------------
+// Grouped, batched, strided FP64 GEMM:  C_b = alpha * A_b B_b + beta * C_b for
+// every descriptor and batch entry b. Element (r, c) of A_b is at
+// A + b*a_bs + r*a_rs + c*a_cs (same for B, C). With ksplit > 1 the K range is
+// split over CTAs; partial products go to P ([batch][ksplit][M][N], row-major)
+// and a second kernel reduces them into C. beta == 0 never reads C.
+struct GemmDesc {
+  const double* A;
+  const double* B;
+  double* C;
+  double* P;
+  int64_t M, N, K;
+  int64_t a_rs, a_cs, b_rs, b_cs, c_rs, c_cs;
+  int64_t a_bs, b_bs, c_bs;
+  double alpha, beta;
+  int32_t batch, ksplit;
+  int32_t mt, nt;
+  int64_t kchunk;
+  int64_t tile_begin;   // prefix over the group (set by the planner)
+  int64_t elem_begin;   // prefix of reduce elements over the group
+};
+
+constexpr int GEMM_BM = 32, GEMM_BN = 32, GEMM_BK = 16, GEMM_THREADS = 256;
+
+// Fills tile/elem prefixes, chooses ksplit and carves each split descriptor's
+// partial buffer out of pbase; returns (tiles, reduce elems) and the partial
+// doubles used (pbase may be null when only sizing).
+void gemm_prepare(std::vector<GemmDesc>& g, int64_t* tiles, int64_t* elems, int64_t* pbuf_doubles,
+                  int target_ctas, double* pbase);
+// flops: algorithmic 2*M*N*K*batch summed over the group (for live profiling).
+int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, int64_t elems, double flops, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Tall-skinny Householder QR (TSQR) of an m x k matrix A (k <= TSQR_KMAX):
+// leaves of b rows are factored in parallel, their R factors are combined up a
+// binary tree inside the same launch (the last CTA to finish a pair combines
+// it, so no CTA waits), and a second launch forms the explicit thin Q.
+constexpr int TSQR_KMAX = 96;
+struct TsqrWork {
+  double* leafV;     // P * b * k
+  double* leafTau;   // P * k
+  double* nodeV;     // inner nodes * 2k * k
+  double* nodeTau;   // inner nodes * k
+  double* nodeR;     // all nodes * k * k
+  int* counters;     // inner nodes, zero before first use (self-resetting)
+};
+struct TsqrShape {
+  int64_t m;
+  int k, b, P, L, inner;
+};
+TsqrShape tsqr_shape(int64_t m, int k);
+size_t tsqr_work_doubles(const TsqrShape& sh, size_t* ints);
+void tsqr_bind(const TsqrShape& sh, double* dbase, int* ibase, TsqrWork* w);
+// Q (m x k, strides q_rs/q_cs) may alias A. R (k x k row-major) may be null.
+// With skip_unless set the kernels do nothing unless *skip_unless != 0 (a
+// device-side fallback switch).
+int tsqr_launch(const TsqrShape& sh, const TsqrWork& w, const double* A, int64_t a_rs, int64_t a_cs,
+                double* Q, int64_t q_rs, int64_t q_cs, double* R, cudaStream_t s,
+                const int* skip_unless = nullptr);
+
+// ----------------------------------------------------------------------------
+// Small dense SVD and truncation rule for one k x k upper-triangular R
+// (k <= TSQR_KMAX). Writes G1 (k x k) and G2 (k x k), row-major, such that the
+// caller can set  new right factor = Q G1  and  left factor *= G2:
+//  - when 1/||R^{-1}||_F > 2 eps (so sigma_min(R) > eps and nothing is cut):
+//        G1 = I, G2 = R^T, rank = k;
+//  - else one-sided Jacobi SVD R = U S V^T, rank r = smallest r >= 1 with
+//        sqrt(sum_{i>r} s_i^2) <= eps, G1 = [U_r 0], G2 = [V_r S_r 0].
+// eps is read from device memory (eps_ptr), or taken as 0 when eps_ptr is null
+// (fixed rank cap rcap). The rank is written to *rank_out (device).
+int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, double* G1, double* G2,
+                     double* sigma, int64_t* rank_out, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Elementwise helpers.
+int fill_launch(double* p, int64_t n, double v, cudaStream_t s);
+int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, uint64_t seed,
+                  cudaStream_t s);
+// eps = tol * ||x||_F / sqrt(N-1) into *eps_out; x has n doubles.
+int norm_eps_launch(const double* x, int64_t n, double tol, int N, double* eps_out, cudaStream_t s);
+// Copy core (r0max, I, r1max) from src into dst compactly as (r0, I, r1) with
+// r0 = *r0p, r1 = *r1p read on the device.
+int compact_core_launch(const double* src, double* dst, int64_t r0max, int64_t I, int64_t r1max,
+                        const int64_t* r0p, const int64_t* r1p, cudaStream_t s);
+
+}  // namespace ttr

@@ -1,0 +1,130 @@
+// Elementwise kernels: constant fill, the counter-based Gaussian sketch of
+// Definition 3.1, the truncation threshold and rank-dependent core compaction.
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "prof.cuh"
+
+namespace ttr {
+
+namespace {
+
+__global__ void fill_kernel(double* p, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = v;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
+// (hi0, lo0) = M0*c0, (hi1, lo1) = M1*c2 (64-bit products),
+// c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), key += Weyl constants.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    const uint64_t p0 = uint64_t(M0) * c[0];
+    const uint64_t p1 = uint64_t(M1) * c[2];
+    const uint32_t hi0 = uint32_t(p0 >> 32), lo0 = uint32_t(p0);
+    const uint32_t hi1 = uint32_t(p1 >> 32), lo1 = uint32_t(p1);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+__device__ __forceinline__ double u52(uint32_t a, uint32_t b) {
+  const uint64_t bits = (uint64_t(a) << 20) | (uint64_t(b) >> 12);
+  return (double(bits) + 0.5) * 0x1p-52;
+}
+
+__global__ void sketch_kernel(double* out, int64_t E, int core_index, uint32_t k0, uint32_t k1, double stdv) {
+  const int64_t npairs = (E + 1) / 2;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < npairs;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    uint32_t c[4] = {uint32_t(uint64_t(p)), uint32_t(uint64_t(p) >> 32), uint32_t(core_index), 0x7474726Eu};
+    philox4x32_10(c, k0, k1);
+    const double u1 = u52(c[0], c[1]), u2 = u52(c[2], c[3]);
+    const double rad = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    out[2 * p] = rad * cs * stdv;
+    if (2 * p + 1 < E) out[2 * p + 1] = rad * sn * stdv;
+  }
+}
+
+__global__ void norm_eps_kernel(const double* x, int64_t n, double tol, int N, double* eps_out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(x[i], x[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) t += red[i];
+    eps_out[0] = tol * sqrt(t) / sqrt(double(max(N - 1, 1)));
+    eps_out[1] = sqrt(t);
+  }
+}
+
+__global__ void compact_kernel(const double* src, double* dst, int64_t r0max, int64_t I, int64_t r1max,
+                               const int64_t* r0p, const int64_t* r1p) {
+  const int64_t r0 = r0p ? *r0p : r0max, r1 = r1p ? *r1p : r1max;
+  const int64_t n = r0 * I * r1;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t b = e % r1, ai = e / r1;
+    const int64_t i = ai % I, a = ai / I;
+    dst[e] = src[(a * I + i) * r1max + b];
+  }
+}
+
+unsigned grid_for(int64_t n, int threads) {
+  return unsigned(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), int64_t(num_sms()) * 16)));
+}
+
+}  // namespace
+
+int fill_launch(double* p, int64_t n, double v, cudaStream_t s) {
+  if (n <= 0) return TT_OK;
+  fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(p, n, v);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, uint64_t seed, cudaStream_t s) {
+  const int64_t E = r0 * I * r1;
+  if (E <= 0) return TT_OK;
+  const double stdv = 1.0 / std::sqrt(double(r0) * double(I) * double(r1));
+  sketch_kernel<<<grid_for((E + 1) / 2, 256), 256, 0, s>>>(out, E, core_index, uint32_t(seed),
+                                                            uint32_t(seed >> 32), stdv);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+int norm_eps_launch(const double* x, int64_t n, double tol, int N, double* eps_out, cudaStream_t s) {
+  norm_eps_kernel<<<1, 1024, 0, s>>>(x, n, tol, N, eps_out);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+int compact_core_launch(const double* src, double* dst, int64_t r0max, int64_t I, int64_t r1max,
+                        const int64_t* r0p, const int64_t* r1p, cudaStream_t s) {
+  compact_kernel<<<grid_for(r0max * I * r1max, 256), 256, 0, s>>>(src, dst, r0max, I, r1max, r0p, r1p);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  }
+  return n;
+}
+
+}  // namespace ttr

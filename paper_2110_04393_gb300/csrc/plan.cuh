@@ -1,0 +1,65 @@
+// Host-side schedule: a list of stream-ordered launch items plus one table of
+// GEMM descriptors uploaded once per call (internal to the library).
+#pragma once
+#include <functional>
+
+#include "kernels.cuh"
+
+namespace ttr {
+
+struct Schedule {
+  std::vector<GemmDesc> descs;
+  std::vector<std::function<int(cudaStream_t, const GemmDesc*)>> items;
+  std::vector<std::vector<double>> host_keep;   // host sources of H2D copies
+  int64_t pbuf_need = 0;                        // split-K partial doubles needed by the largest group
+  double* pbuf = nullptr;                       // partial buffer (null while sizing)
+
+  void gemm(std::vector<GemmDesc> g) {
+    if (g.empty()) return;
+    int64_t tiles = 0, elems = 0, pb = 0;
+    gemm_prepare(g, &tiles, &elems, &pb, 2 * num_sms(), pbuf);
+    if (pb > pbuf_need) pbuf_need = pb;
+    const size_t off = descs.size();
+    const int n = int(g.size());
+    double flops = 0.0;
+    for (const auto& d : g) flops += 2.0 * double(d.M) * double(d.N) * double(d.K) * double(d.batch);
+    descs.insert(descs.end(), g.begin(), g.end());
+    items.push_back([=](cudaStream_t s, const GemmDesc* d) { return gemm_launch(d + off, n, tiles, elems, flops, s); });
+  }
+  void add(std::function<int(cudaStream_t)> f) {
+    items.push_back([f](cudaStream_t s, const GemmDesc*) { return f(s); });
+  }
+  // H2D copy of host values kept alive by the schedule.
+  void upload(double* dst, std::vector<double> v) {
+    host_keep.push_back(std::move(v));
+    const std::vector<double>* src = &host_keep.back();
+    const size_t bytes = src->size() * sizeof(double);
+    const double* hp = src->data();
+    add([dst, hp, bytes](cudaStream_t s) -> int {
+      if (!dst || bytes == 0) return int(TT_OK);
+      TTR_CHECK_CUDA(cudaMemcpyAsync(dst, hp, bytes, cudaMemcpyHostToDevice, s));
+      return int(TT_OK);
+    });
+  }
+};
+
+inline GemmDesc gdesc(const double* A, int64_t a_rs, int64_t a_cs, const double* B, int64_t b_rs, int64_t b_cs,
+                      double* C, int64_t c_rs, int64_t c_cs, int64_t M, int64_t N, int64_t K, double alpha = 1.0,
+                      double beta = 0.0) {
+  GemmDesc d{};
+  d.A = A; d.B = B; d.C = C;
+  d.a_rs = a_rs; d.a_cs = a_cs; d.b_rs = b_rs; d.b_cs = b_cs; d.c_rs = c_rs; d.c_cs = c_cs;
+  d.M = M; d.N = N; d.K = K;
+  d.alpha = alpha; d.beta = beta;
+  d.batch = 1; d.ksplit = 1;
+  return d;
+}
+
+// Runs a planner twice: once to size the workspace, once to bind real pointers
+// and execute. build(Arena&, Schedule&) must take arena regions in the same
+// order on both passes.
+using BuildFn = std::function<int(Arena&, Schedule&)>;
+int plan_workspace_bytes(const BuildFn& build, size_t* bytes);
+int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStream_t s);
+
+}  // namespace ttr

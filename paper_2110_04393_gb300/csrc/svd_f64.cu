@@ -1,0 +1,200 @@
+// Small dense SVD of an upper-triangular R and the eps-truncation rule of
+// Section 2.1 ("SVD(X, eps)"), used by the truncation loop of Algorithm 2 and
+// by the truncation of the left-orthogonal Randomize-then-Orthogonalize output
+// (Section 3.2).
+//
+// The threshold is absolute (Algorithm 2 passes eps = ||Y|| eps0 / sqrt(N-1)):
+// the kept rank is the smallest r >= 1 with sqrt(sum_{i>r} s_i^2) <= eps.
+//
+// Certified shortcut: if 1/||R^{-1}||_F > 2 eps then sigma_min(R) > eps, no
+// singular value can be dropped (the tail of any r < k already exceeds eps),
+// and the SVD is not needed: the step reduces to absorbing R (G1 = I, G2 = R^T).
+// Otherwise: one-sided Jacobi (Hestenes) with a round-robin pair schedule, one
+// warp per column pair.
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "prof.cuh"
+
+namespace ttr {
+
+namespace {
+
+constexpr int SVD_THREADS = 1024;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const double* __restrict__ R,
+                                                                const double* __restrict__ eps_ptr, int rcap,
+                                                                double* G1, double* G2, double* sigma,
+                                                                int64_t* rank_out) {
+  extern __shared__ double sm[];
+  const int kk = k + (k & 1);        // even number of columns for the round-robin schedule
+  double* A = sm;                    // k x kk column-major (column k is zero padding)
+  double* Vm = A + k * kk;           // kk x kk column-major
+  double* sv = Vm + kk * kk;         // kk
+  double* red = sv + kk;             // 32
+  __shared__ int s_flag, s_rot, s_rank;
+  __shared__ int order[128];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  const double eps = eps_ptr ? *eps_ptr : 0.0;
+
+  for (int idx = tid; idx < k * kk; idx += nt) {
+    const int r = idx % k, c = idx / k;
+    A[r + c * k] = (c < k) ? R[r * k + c] : 0.0;
+  }
+  __syncthreads();
+
+  // ---- certificate: sigma_min(R) >= 1/||R^{-1}||_F > 2 eps  =>  nothing is cut
+  if (eps_ptr != nullptr && rcap >= k) {
+    double part = 0.0;
+    bool bad = false;
+    for (int c = tid; c < k; c += nt) {
+      // column c of R^{-1} by back substitution, kept in Vm (column c)
+      for (int i = c; i >= 0; --i) {
+        double s = (i == c) ? 1.0 : 0.0;
+        for (int j = i + 1; j <= c; ++j) s -= A[i + j * k] * Vm[j + c * kk];
+        const double d = A[i + i * k];
+        if (d == 0.0) { bad = true; s = 0.0; } else s /= d;
+        Vm[i + c * kk] = s;
+        part = fma(s, s, part);
+      }
+    }
+    part = warp_sum(part);
+    if (tid == 0) s_flag = 0;
+    __syncthreads();
+    if (lane == 0) red[warp] = part;
+    if (bad) atomicOr(&s_flag, 1);
+    __syncthreads();
+    double tot = 0.0;
+    for (int i = 0; i < nwarp; ++i) tot += red[i];
+    const bool certified = !s_flag && isfinite(tot) && tot > 0.0 && (1.0 / sqrt(tot)) > 2.0 * eps;
+    __syncthreads();
+    if (certified) {
+      for (int idx = tid; idx < k * k; idx += nt) {
+        const int r = idx / k, c = idx % k;
+        G1[idx] = (r == c) ? 1.0 : 0.0;
+        G2[idx] = A[c + r * k];            // R^T
+      }
+      for (int i = tid; i < k; i += nt) sigma[i] = -1.0;   // not computed
+      if (tid == 0) *rank_out = k;
+      return;
+    }
+  }
+
+  // ---- one-sided Jacobi: A V = U S
+  for (int idx = tid; idx < kk * kk; idx += nt) Vm[idx] = ((idx % kk) == (idx / kk)) ? 1.0 : 0.0;
+  __syncthreads();
+  const int npairs = kk / 2;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int step = 0; step < kk - 1; ++step) {
+      for (int pr = warp; pr < npairs; pr += nwarp) {
+        const int pos_a = pr, pos_b = kk - 1 - pr;
+        int p = (pos_a == 0) ? 0 : ((pos_a - 1 + step) % (kk - 1)) + 1;
+        int q = ((pos_b - 1 + step) % (kk - 1)) + 1;
+        if (p > q) { int t = p; p = q; q = t; }
+        if (q >= k) continue;                       // padding column
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = lane; r < k; r += 32) {
+          const double x = A[r + p * k], y = A[r + q * k];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (ga == 0.0 || fabs(ga) <= 2e-15 * sqrt(al * be)) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+        const double c = 1.0 / sqrt(fma(t, t, 1.0));
+        const double s = c * t;
+        for (int r = lane; r < k; r += 32) {
+          const double x = A[r + p * k], y = A[r + q * k];
+          A[r + p * k] = c * x - s * y;
+          A[r + q * k] = s * x + c * y;
+        }
+        for (int r = lane; r < kk; r += 32) {
+          const double x = Vm[r + p * kk], y = Vm[r + q * kk];
+          Vm[r + p * kk] = c * x - s * y;
+          Vm[r + q * kk] = s * x + c * y;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    if (!s_rot) break;
+    __syncthreads();
+  }
+
+  // ---- singular values, descending order, rank
+  for (int c = warp; c < k; c += nwarp) {
+    double s = 0.0;
+    for (int r = lane; r < k; r += 32) s = fma(A[r + c * k], A[r + c * k], s);
+    s = warp_sum(s);
+    if (lane == 0) sv[c] = sqrt(s);
+  }
+  __syncthreads();
+  for (int i = tid; i < k; i += nt) {
+    int pos = 0;
+    for (int j = 0; j < k; ++j) pos += (sv[j] > sv[i]) || (sv[j] == sv[i] && j < i);
+    order[pos] = i;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int r = k;
+    double tail = 0.0;
+    // smallest r >= 1 with sqrt(sum_{i>r} s_i^2) <= eps: walk from the end
+    for (int t = k - 1; t >= 1; --t) {
+      const double st = sv[order[t]];
+      const double nt2 = tail + st * st;
+      if (sqrt(nt2) <= eps) { tail = nt2; r = t; } else break;
+    }
+    if (r > rcap) r = rcap;
+    if (r < 1) r = 1;
+    s_rank = r;
+    *rank_out = r;
+  }
+  __syncthreads();
+  const int r = s_rank;
+  for (int idx = tid; idx < k * k; idx += nt) {
+    const int row = idx / k, t = idx % k;
+    double g1 = 0.0, g2 = 0.0;
+    if (t < r) {
+      const int c = order[t];
+      const double s = sv[c];
+      g1 = (s > 0.0) ? A[row + c * k] / s : (row == t ? 1.0 : 0.0);
+      g2 = Vm[row + c * kk] * s;
+    }
+    G1[idx] = g1;
+    G2[idx] = g2;
+  }
+  for (int t = tid; t < k; t += nt) sigma[t] = sv[order[t]];
+}
+
+}  // namespace
+
+int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, double* G1, double* G2,
+                     double* sigma, int64_t* rank_out, cudaStream_t s) {
+  if (k < 1 || k > TSQR_KMAX) {
+    set_error("svd_trunc: k out of range");
+    return TT_EUNSUPPORTED;
+  }
+  const int kk = k + (k & 1);
+  const size_t smem = (size_t(k) * kk + size_t(kk) * kk + kk + 32) * sizeof(double);
+  static bool attr_done = false;
+  if (!attr_done) {
+    TTR_CHECK_CUDA(cudaFuncSetAttribute(svd_trunc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_done = true;
+  }
+  svd_trunc_kernel<<<1, SVD_THREADS, smem, s>>>(k, R, eps_ptr, rcap, G1, G2, sigma, rank_out);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+}  // namespace ttr

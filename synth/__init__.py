@@ -129,22 +129,24 @@ def workload_sum_literal(seed: int, K=20, N=50, I=100, R=10):
     return [gaussian_tt(rng_for(seed, 100 + j), dims, _uniform_ranks(N, R)) for j in range(K)]
 
 
-def workload_sum_structured(seed: int, K=20, N=50, I=100, R=10, m=2, delta=1e-10):
-    """Redundant sum in the style of TT-GMRES combinations (Section 4.2): summand j
-    is c_j times a gauge-scrambled copy of one of m base TTs of rank R, with every
-    core perturbed by relative noise delta. The sum has TT-rank about m*R plus a
-    tail of relative size about delta."""
+def workload_sum_structured(seed: int, K=20, N=50, I=100, R=10, m=2, p=2, delta=1e-10):
+    """Redundant sum in the style of TT-GMRES combinations (Section 4.2). The
+    first K - p summands are c_j times gauge-scrambled copies of m base TTs of
+    rank R (so together they have TT-rank m*R); the last p summands are
+    independent Gaussian TTs of rank R scaled by delta (relative to the base
+    norm), a genuine tail of relative size about delta. Every summand keeps
+    TT-rank R."""
     dims = [int(I)] * N
     bases = [gaussian_tt(rng_for(seed, 200 + a), dims, _uniform_ranks(N, R)) for a in range(m)]
     crng = rng_for(seed, 300)
     out = []
-    for j in range(K):
+    for j in range(K - p):
         g = rng_for(seed, 400 + j)
         Y = gauge_scramble(g, bases[j % m])
-        Y = scale_tt(Y, float(crng.standard_normal()))
-        if delta > 0:
-            Y = perturb_cores(g, Y, delta)
-        out.append(Y)
+        out.append(scale_tt(Y, float(crng.standard_normal())))
+    for j in range(p):
+        E = gaussian_tt(rng_for(seed, 600 + j), dims, _uniform_ranks(N, R))
+        out.append(scale_tt(E, delta))
     return out
 
 
