@@ -31,7 +31,8 @@ int plan_workspace_bytes(const BuildFn& build, size_t* bytes) {
   a.sizing = true;
   Schedule s;
   TTR_TRY(build(a, s));
-  *bytes = a.used + align256(size_t(s.pbuf_need) * sizeof(double)) + align256(s.descs.size() * sizeof(GemmDesc)) + 256;
+  *bytes = a.used + align256(size_t(s.pbuf_need) * sizeof(double)) + align256(s.descs.size() * sizeof(GemmDesc)) +
+           align256(size_t(std::max<int64_t>(s.cnt_need, 1)) * sizeof(int)) + 256;
   return TT_OK;
 }
 
@@ -43,7 +44,8 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
     a.sizing = true;
     TTR_TRY(build(a, probe));
     need = a.used + align256(size_t(probe.pbuf_need) * sizeof(double)) +
-           align256(probe.descs.size() * sizeof(GemmDesc)) + 256;
+           align256(probe.descs.size() * sizeof(GemmDesc)) +
+           align256(size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int)) + 256;
   }
   void* ws = workspace;
   bool owned = false;
@@ -71,7 +73,16 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
   Schedule s;
   s.pbuf = a.take<double>(size_t(std::max<int64_t>(probe.pbuf_need, 1)));
   GemmDesc* d_descs = a.take<GemmDesc>(std::max<size_t>(probe.descs.size(), 1));
-  int rc = build(a, s);
+  s.cnt = a.take<int>(size_t(std::max<int64_t>(probe.cnt_need, 1)));
+  int rc = TT_OK;
+  {
+    cudaError_t e = cudaMemsetAsync(s.cnt, 0, size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int), st);
+    if (e != cudaSuccess) {
+      set_error(std::string("counter reset: ") + cudaGetErrorString(e));
+      rc = TT_ECUDA;
+    }
+  }
+  if (rc == TT_OK) rc = build(a, s);
   if (rc == TT_OK && !s.descs.empty()) {
     cudaError_t e = cudaMemcpyAsync(d_descs, s.descs.data(), s.descs.size() * sizeof(GemmDesc),
                                     cudaMemcpyHostToDevice, st);

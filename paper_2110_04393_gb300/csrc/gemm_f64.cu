@@ -15,12 +15,11 @@ namespace ttr {
 
 namespace {
 
-__device__ __forceinline__ int find_desc(const GemmDesc* d, int n, int64_t t, bool elems) {
+__device__ __forceinline__ int find_desc(const GemmDesc* d, int n, int64_t t) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    int64_t b = elems ? d[mid].elem_begin : d[mid].tile_begin;
-    if (b <= t) lo = mid; else hi = mid - 1;
+    if (d[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -28,8 +27,9 @@ __device__ __forceinline__ int find_desc(const GemmDesc* d, int n, int64_t t, bo
 __global__ void __launch_bounds__(GEMM_THREADS) gemm_f64_kernel(const GemmDesc* __restrict__ descs, int ndesc) {
   __shared__ double As[GEMM_BK][GEMM_BM + 1];
   __shared__ double Bs[GEMM_BK][GEMM_BN + 1];
+  __shared__ int s_last;
   const int64_t t = blockIdx.x;
-  const GemmDesc& d = descs[find_desc(descs, ndesc, t, false)];
+  const GemmDesc& d = descs[find_desc(descs, ndesc, t)];
   int64_t local = t - d.tile_begin;
   const int ntile = int(local % d.nt); local /= d.nt;
   const int mtile = int(local % d.mt); local /= d.mt;
@@ -47,6 +47,8 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_f64_kernel(const GemmDesc* 
   double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
   const bool a_kfast = (d.a_cs == 1);
   const bool b_nfast = (d.b_cs == 1);
+  // threads whose 2x2 outputs all fall outside C skip the FMAs (padded tiles)
+  const bool active = (m0 + ty < d.M) && (n0 + tx < d.N);
 
   for (int64_t kb = k0; kb < k1; kb += GEMM_BK) {
 #pragma unroll
@@ -62,59 +64,82 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_f64_kernel(const GemmDesc* 
       Bs[kk2][nn] = (gn < d.N && gk2 < k1) ? B[gk2 * d.b_rs + gn * d.b_cs] : 0.0;
     }
     __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int kk = 0; kk < GEMM_BK; ++kk) {
-      double a0 = As[kk][ty], a1 = As[kk][ty + 16];
-      double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
+      for (int kk = 0; kk < GEMM_BK; ++kk) {
+        double a0 = As[kk][ty], a1 = As[kk][ty + 16];
+        double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
     }
     __syncthreads();
   }
 
+  if (d.ksplit == 1) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      int64_t gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
-      if (gm >= d.M || gn >= d.N) continue;
-      if (d.ksplit == 1) {
+      for (int j = 0; j < 2; ++j) {
+        int64_t gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+        if (gm >= d.M || gn >= d.N) continue;
         double* c = d.C + b * d.c_bs + gm * d.c_rs + gn * d.c_cs;
         double v = d.alpha * acc[i][j];
         if (d.beta != 0.0) v = fma(d.beta, *c, v);
         *c = v;
-      } else {
-        d.P[((b * d.ksplit + ks) * d.M + gm) * d.N + gn] = acc[i][j];
       }
+    return;
+  }
+  // split K: publish the partial tile, the last CTA of the tile reduces
+  const int64_t MN = d.M * d.N;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      int64_t gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < d.M && gn < d.N) d.P[(b * d.ksplit + ks) * MN + gm * d.N + gn] = acc[i][j];
     }
+  __threadfence();
+  __syncthreads();
+  const int64_t tile_id = (b * d.mt + mtile) * d.nt + ntile;
+  if (tid == 0) {
+    const int old = atomicAdd(d.cnt + tile_id, 1);
+    s_last = (old == d.ksplit - 1);
+    if (s_last) d.cnt[tile_id] = 0;
   }
-}
-
-__global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs, int ndesc, int64_t total) {
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    const GemmDesc& d = descs[find_desc(descs, ndesc, e, true)];
-    int64_t local = e - d.elem_begin;
-    const int64_t MN = d.M * d.N;
-    const int64_t b = local / MN;
-    const int64_t r = local % MN;
-    const int64_t gm = r / d.N, gn = r % d.N;
-    double s = 0.0;
-    for (int k = 0; k < d.ksplit; ++k) s += d.P[(b * d.ksplit + k) * MN + r];
-    double* c = d.C + b * d.c_bs + gm * d.c_rs + gn * d.c_cs;
-    double v = d.alpha * s;
-    if (d.beta != 0.0) v = fma(d.beta, *c, v);
-    *c = v;
-  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // sum the partials in split order; eight independent loads per output in flight
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      int64_t gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm >= d.M || gn >= d.N) continue;
+      const double* pp = d.P + b * d.ksplit * MN + gm * d.N + gn;
+      double u[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int k = 0;
+      for (; k + 8 <= d.ksplit; k += 8) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) u[q] += __ldcg(pp + (k + q) * MN);
+      }
+      for (; k < d.ksplit; ++k) u[0] += __ldcg(pp + k * MN);
+      const double sacc = ((u[0] + u[1]) + (u[2] + u[3])) + ((u[4] + u[5]) + (u[6] + u[7]));
+      double* c = d.C + b * d.c_bs + gm * d.c_rs + gn * d.c_cs;
+      double v = d.alpha * sacc;
+      if (d.beta != 0.0) v = fma(d.beta, *c, v);
+      *c = v;
+    }
 }
 
 }  // namespace
 
-void gemm_prepare(std::vector<GemmDesc>& g, int64_t* tiles, int64_t* elems, int64_t* pbuf, int target_ctas,
-                  double* pbase) {
-  int64_t t = 0, e = 0, p = 0;
+void gemm_prepare(std::vector<GemmDesc>& g, int64_t* tiles, int64_t* pbuf, int64_t* counters, int target_ctas,
+                  double* pbase, int* cbase) {
+  int64_t t = 0, p = 0, c = 0;
   for (auto& d : g) {
     d.mt = int(ceil_div(std::max<int64_t>(d.M, 1), GEMM_BM));
     d.nt = int(ceil_div(std::max<int64_t>(d.N, 1), GEMM_BN));
@@ -123,38 +148,34 @@ void gemm_prepare(std::vector<GemmDesc>& g, int64_t* tiles, int64_t* elems, int6
     if (d.K > 2 * GEMM_BK && base < target_ctas) {
       int64_t want = ceil_div(target_ctas, base);
       int64_t maxk = d.K / (2 * GEMM_BK);
-      ks = int(std::max<int64_t>(1, std::min<int64_t>({want, maxk, 64})));
+      ks = int(std::max<int64_t>(1, std::min<int64_t>({want, maxk, 32})));
     }
-    d.ksplit = ks;
     d.kchunk = ceil_div(ceil_div(std::max<int64_t>(d.K, 1), ks), GEMM_BK) * GEMM_BK;
+    ks = int(ceil_div(std::max<int64_t>(d.K, 1), d.kchunk));   // no empty split
+    d.ksplit = ks;
     d.tile_begin = t;
     t += base * ks;
-    d.elem_begin = e;
     d.P = nullptr;
+    d.cnt = nullptr;
     if (ks > 1) {
-      e += int64_t(d.batch) * d.M * d.N;
       d.P = pbase ? pbase + p : nullptr;
       p += int64_t(d.batch) * ks * d.M * d.N;
+      d.cnt = cbase ? cbase + c : nullptr;
+      c += base;
     }
   }
   *tiles = t;
-  *elems = e;
   *pbuf = p;
+  *counters = c;
 }
 
-int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, int64_t elems, double flops, cudaStream_t s) {
+int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, double flops, cudaStream_t s) {
   if (ndesc == 0 || tiles == 0) return TT_OK;
   cudaEvent_t e0;
   const bool prof = prof_gemm_begin(s, &e0);
   gemm_f64_kernel<<<unsigned(tiles), GEMM_THREADS, 0, s>>>(d_descs, ndesc);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
-  if (elems > 0) {
-    int64_t blocks = std::min<int64_t>(ceil_div(elems, 256), 4096);
-    gemm_reduce_kernel<<<unsigned(blocks), 256, 0, s>>>(d_descs, ndesc, elems);
-    TTR_CHECK_LAUNCH();
-  prof_count_launch(1);
-  }
   if (prof) prof_gemm_end(s, flops);
   return TT_OK;
 }

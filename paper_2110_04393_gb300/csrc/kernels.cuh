@@ -9,7 +9,9 @@ namespace ttr {
 // every descriptor and batch entry b. Element (r, c) of A_b is at
 // A + b*a_bs + r*a_rs + c*a_cs (same for B, C). With ksplit > 1 the K range is
 // split over CTAs; partial products go to P ([batch][ksplit][M][N], row-major)
-// and a second kernel reduces them into C. beta == 0 never reads C.
+// and the last CTA to finish a tile (arrival counter) sums them in split order
+// and writes C, so the result does not depend on scheduling. beta == 0 never
+// reads C.
 struct GemmDesc {
   const double* A;
   const double* B;
@@ -23,18 +25,19 @@ struct GemmDesc {
   int32_t mt, nt;
   int64_t kchunk;
   int64_t tile_begin;   // prefix over the group (set by the planner)
-  int64_t elem_begin;   // prefix of reduce elements over the group
+  int* cnt;             // split-K arrival counters, one per output tile (self-resetting)
 };
 
 constexpr int GEMM_BM = 32, GEMM_BN = 32, GEMM_BK = 16, GEMM_THREADS = 256;
 
-// Fills tile/elem prefixes, chooses ksplit and carves each split descriptor's
-// partial buffer out of pbase; returns (tiles, reduce elems) and the partial
-// doubles used (pbase may be null when only sizing).
-void gemm_prepare(std::vector<GemmDesc>& g, int64_t* tiles, int64_t* elems, int64_t* pbuf_doubles,
-                  int target_ctas, double* pbase);
+// Fills tile prefixes, chooses ksplit and carves each split descriptor's
+// partial buffer out of pbase and its counters out of cbase; returns the tile
+// count and the partial doubles / counters used (bases may be null when only
+// sizing).
+void gemm_prepare(std::vector<GemmDesc>& g, int64_t* tiles, int64_t* pbuf_doubles, int64_t* counters,
+                  int target_ctas, double* pbase, int* cbase);
 // flops: algorithmic 2*M*N*K*batch summed over the group (for live profiling).
-int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, int64_t elems, double flops, cudaStream_t s);
+int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, double flops, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // Tall-skinny Householder QR (TSQR) of an m x k matrix A (k <= TSQR_KMAX):

@@ -13,18 +13,21 @@ struct Schedule {
   std::vector<std::vector<double>> host_keep;   // host sources of H2D copies
   int64_t pbuf_need = 0;                        // split-K partial doubles needed by the largest group
   double* pbuf = nullptr;                       // partial buffer (null while sizing)
+  int64_t cnt_need = 0;                         // split-K counters needed by the largest group
+  int* cnt = nullptr;                           // counters (zeroed once per call, self-resetting)
 
   void gemm(std::vector<GemmDesc> g) {
     if (g.empty()) return;
-    int64_t tiles = 0, elems = 0, pb = 0;
-    gemm_prepare(g, &tiles, &elems, &pb, 2 * num_sms(), pbuf);
+    int64_t tiles = 0, pb = 0, cn = 0;
+    gemm_prepare(g, &tiles, &pb, &cn, 2 * num_sms(), pbuf, cnt);
     if (pb > pbuf_need) pbuf_need = pb;
+    if (cn > cnt_need) cnt_need = cn;
     const size_t off = descs.size();
     const int n = int(g.size());
     double flops = 0.0;
     for (const auto& d : g) flops += 2.0 * double(d.M) * double(d.N) * double(d.K) * double(d.batch);
     descs.insert(descs.end(), g.begin(), g.end());
-    items.push_back([=](cudaStream_t s, const GemmDesc* d) { return gemm_launch(d + off, n, tiles, elems, flops, s); });
+    items.push_back([=](cudaStream_t s, const GemmDesc* d) { return gemm_launch(d + off, n, tiles, flops, s); });
   }
   void add(std::function<int(cudaStream_t)> f) {
     items.push_back([f](cudaStream_t s, const GemmDesc*) { return f(s); });

@@ -51,24 +51,39 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
 
   // ---- certificate: sigma_min(R) >= 1/||R^{-1}||_F > 2 eps  =>  nothing is cut
   if (eps_ptr != nullptr && rcap >= k) {
-    double part = 0.0;
-    bool bad = false;
-    for (int c = tid; c < k; c += nt) {
-      // column c of R^{-1} by back substitution, kept in Vm (column c)
-      for (int i = c; i >= 0; --i) {
-        double s = (i == c) ? 1.0 : 0.0;
-        for (int j = i + 1; j <= c; ++j) s -= A[i + j * k] * Vm[j + c * kk];
-        const double d = A[i + i * k];
-        if (d == 0.0) { bad = true; s = 0.0; } else s /= d;
-        Vm[i + c * kk] = s;
-        part = fma(s, s, part);
+    // R^{-1} (upper) by a right-looking backward sweep over all columns at once
+    __shared__ double s_rd;
+    __shared__ int s_zero;
+    if (tid == 0) s_zero = 0;
+    for (int idx = tid; idx < kk * kk; idx += nt) Vm[idx] = ((idx % kk) == (idx / kk)) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int j = k - 1; j >= 0; --j) {
+      if (tid == 0) {
+        const double dj = A[j + j * k];
+        if (dj == 0.0 || !isfinite(dj)) { s_zero = 1; s_rd = 0.0; } else s_rd = 1.0 / dj;
       }
+      __syncthreads();
+      const double rd = s_rd;
+      for (int c = j + tid; c < k; c += nt) Vm[j + c * kk] *= rd;        // row j of X final
+      __syncthreads();
+      for (int idx = tid; idx < j * (k - j); idx += nt) {                  // rows i < j, columns c >= j
+        const int i = idx % j, c = j + idx / j;
+        Vm[i + c * kk] = fma(-A[i + j * k], Vm[j + c * kk], Vm[i + c * kk]);
+      }
+      __syncthreads();
     }
+    double part = 0.0;
+    for (int idx = tid; idx < k * k; idx += nt) {
+      const int r = idx % k, c = idx / k;
+      const double x = Vm[r + c * kk];
+      part = fma(x, x, part);
+    }
+    const bool bad = (s_zero != 0);
     part = warp_sum(part);
     if (tid == 0) s_flag = 0;
     __syncthreads();
     if (lane == 0) red[warp] = part;
-    if (bad) atomicOr(&s_flag, 1);
+    if (bad && tid == 0) atomicOr(&s_flag, 1);
     __syncthreads();
     double tot = 0.0;
     for (int i = 0; i < nwarp; ++i) tot += red[i];
