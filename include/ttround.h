@@ -122,6 +122,33 @@ int tt_round_rand(int32_t N, const int64_t* dims, const int64_t* ranks, const do
                   size_t workspace_bytes, void* stream);
 
 /*
+ * tt_round_sum_rand_noalloc -- tt_round_sum_rand for callers that cannot
+ * allocate device memory (no counterpart in the paper: it only changes where the
+ * scratch lives). Some callers may not call cudaMalloc at the point of the
+ * rounding: code being captured into a CUDA graph by a framework that forbids
+ * allocation during capture, real-time loops with a fixed memory budget, hosts
+ * that hand the library only its inputs and outputs. This entry point takes the
+ * same arguments as tt_round_sum_rand minus the workspace and uses a fixed
+ * device array of TT_NOALLOC_SCRATCH_BYTES inside the library instead; every
+ * GPU that loads the library holds that array until the process exits. It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - Problems whose scratch need (tt_round_sum_rand_workspace) exceeds
+ *     TT_NOALLOC_SCRATCH_BYTES return TT_ENOMEM with both sizes in the message.
+ *   - All calls on a device share the array and leave their contents behind;
+ *     each call zeroes what must start at zero. Calls whose device work
+ *     overlaps (several streams or host threads) race: serialize them.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current; make it before any stream capture.
+ * tt_noalloc_scratch_bytes() returns the array size.
+ */
+#define TT_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+size_t tt_noalloc_scratch_bytes(void);
+int tt_round_sum_rand_noalloc(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                              const double* const* cores, const double* coeffs, const int64_t* ells,
+                              const double* const* sketch, uint64_t seed, double tol, int32_t precision,
+                              double* const* out, int64_t* out_ranks, void* stream);
+
+/*
  * Measurement hooks (no counterpart in the paper; used by the benchmark).
  * tt_prof_enable(1) makes the library record a CUDA event pair on the caller's
  * stream around every grouped-GEMM launch (all contraction steps) and add up the

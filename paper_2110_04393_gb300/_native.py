@@ -25,6 +25,9 @@ SIGNATURES = {
     "tt_round_sum_rand_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64, c_dbl, c_i32]),
     "tt_round_rand": (c_i32, [c_i32, P_i64, P_i64, P_vp, P_i64, P_vp, c_u64, c_dbl, c_i32, P_vp, P_i64, c_vp,
                               c_size, c_vp]),
+    "tt_noalloc_scratch_bytes": (c_size, []),
+    "tt_round_sum_rand_noalloc": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl,
+                                          c_i32, P_vp, P_i64, c_vp]),
     "tt_prof_enable": (c_i32, [c_i32]),
     "tt_prof_reset": (c_i32, []),
     "tt_prof_read": (c_i32, [P_dbl, P_dbl, P_i64, P_i64]),

@@ -358,7 +358,8 @@ int tt_sketch_gaussian(int32_t N, const int64_t* dims, const int64_t* ells, uint
   return TT_OK;
 }
 
-static int sum_rand_common(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+__attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, const int64_t* dims,
+                                                         const int64_t* ranks,
                            const double* const* cores, const double* coeffs, const int64_t* ells,
                            const double* const* sketch, uint64_t seed, double tol, int32_t precision,
                            double* const* out, int64_t* out_ranks, void* workspace, size_t ws_bytes,
