@@ -38,6 +38,7 @@ def parse():
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    p.add_argument("--no-det", action="store_true", help="skip the deterministic comparison")
     return p.parse_args()
 
 
@@ -241,6 +242,32 @@ def run_ours(a):
         d2h = sum(c.numel() * 8 for c in hX)
     e2e_ms = sum(e2e_times) / len(e2e_times) if e2e_times else float("nan")
 
+    # deterministic comparison (Algorithms 1 + 2 on the formed sum), same inputs and tolerance
+    det = None
+    if not a.no_det:
+        from paper_2110_04393_gb300.costs import flops_det
+        Xd = tt.tt_round_det(Yd, tol=tol)          # warm-up
+        dts = []
+        for s in range(2):
+            flush.fill_(s & 0xFF)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Xd = tt.tt_round_det(Yd, tol=tol)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dts.append(e0.elapsed_time(e1))
+        dr = [int(Xd[0].shape[0])] + [int(c.shape[2]) for c in Xd]
+        S = [1] + [sum(R[n] for R in ranks_of(Ys)) for n in range(1, N)] + [1]
+        S[1] = min(S[1], dims[0])
+        for n in range(N - 1, 0, -1):
+            S[n] = min(S[n], dims[n] * S[n + 1])
+        dfl = flops_det(dims, S, dr)
+        dms = min(dts)
+        det = {"ms_per_step": dms, "tflops_alg": dfl / (dms * 1e-3) / 1e12, "gflop_alg": dfl / 1e9,
+               "output_ranks_max": max(dr), "rand_speedup": dms / t_ms}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -277,6 +304,8 @@ def run_ours(a):
                                   "a DFMA-loop probe measured 1.19 TFLOP/s",
                      "launches": gemm_n, "share_of_step": gemm_ms / (t_ms * a.steps) if t_ms > 0 else None},
         "clocks": clocks,
+        "variants": {"rand_" + prec: {"ms_per_step": t_ms, "tflops_alg": flops / (t_ms * 1e-3) / 1e12},
+                     "det_fp64": det},
     }
     if world == 1 and not a.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(Ys)

@@ -122,6 +122,51 @@ int tt_round_rand(int32_t N, const int64_t* dims, const int64_t* ranks, const do
                   size_t workspace_bytes, void* stream);
 
 /*
+ * tt_round_det -- deterministic TT-rounding of a sum: the formed TT-sum of
+ * Section 2.1 (coefficients in the first cores), Algorithm 1 (right-to-left
+ * orthogonalization) and Algorithm 2 (TT-SVD truncation, eps = tol ||Y|| /
+ * sqrt(N-1), so ||X - Y|| <= tol ||Y||), the comparison path of the paper.
+ * With max_rank > 0 every bond is also capped at max_rank (tol <= 0: fixed
+ * ranks only). Arguments as tt_round_sum_rand, and:
+ *   out   host array of N device pointers; core n must hold the formed core,
+ *         tt_round_det_out_capacity(...)[n-1] doubles (S_{n-1} I_n S_n with
+ *         S_n = sum_j R^{(j)}_n): it is used as working storage and receives the
+ *         result compactly as (r_{n-1}, I_n, r_n).
+ * The output ranks are decided on the device and read back (one stream sync).
+ * Errors: TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_EUNSUPPORTED (an unfolding that
+ * would have to be wide), TT_ESINGULAR (a Cholesky QR above the Householder
+ * limit could not orthogonalize a block).
+ */
+int tt_round_det(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+                 const double* coeffs, double tol, int64_t max_rank, double* const* out, int64_t* out_ranks,
+                 void* workspace, size_t workspace_bytes, void* stream);
+size_t tt_round_det_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, double tol,
+                              int64_t max_rank);
+int tt_round_det_out_capacity(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, int64_t* caps);
+
+/*
+ * tt_round_orthrand -- Algorithm 4 (Orthogonalize-then-Randomize, Section 3.1)
+ * on the formed TT-sum: Algorithm 1, then for n = 1..N-1 sketch
+ * Y_n = V(X_n) Omega_n with a Gaussian R'_n x l_n matrix, thin QR,
+ * M_n = Q^T V(X_n), H(X_{n+1}) := M_n H(X_{n+1}).
+ *   omega  host array of N device pointers, omega[n-1] = Omega_n (R'_n x l_n,
+ *          row-major; omega[N-1] unused), R'_n from tt_orthrand_omega_ranks;
+ *          or NULL to draw them on the device from seed (Philox, as
+ *          tt_sketch_gaussian does for a 1 x R'_n x l_n core with index n-1)
+ *   out    host array of N device pointers, core n holds l_{n-1} I_n l_n doubles
+ *          (clamped target ranks, returned in out_ranks).
+ * Errors: TT_EINVAL, TT_ENOMEM, TT_ECUDA.
+ */
+int tt_round_orthrand(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+                      const double* coeffs, const int64_t* ells, const double* const* omega, uint64_t seed,
+                      double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
+                      void* stream);
+size_t tt_round_orthrand_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                                   const int64_t* ells);
+/* R'_0..R'_N: ranks of the formed sum after Algorithm 1 (the row counts of Omega_n). */
+int tt_orthrand_omega_ranks(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, int64_t* rp);
+
+/*
  * tt_round_sum_rand_noalloc -- tt_round_sum_rand for callers that cannot
  * allocate device memory (no counterpart in the paper: it only changes where the
  * scratch lives). Some callers may not call cudaMalloc at the point of the

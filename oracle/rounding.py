@@ -61,14 +61,26 @@ def svd_truncated(R, eps=0.0, max_rank=None):
     return U[:, :k], s[:k], Vt[:k, :], s
 
 
+def qr_pos(A):
+    """Thin QR with a nonnegative diagonal of R: for full column rank this is
+    the unique thin QR factorization (Section 2.1 leaves the signs open; fixing
+    them makes the basis of the orthogonalized right part, and therefore the
+    sketch of Algorithm 4, independent of the QR routine)."""
+    Q, R = np.linalg.qr(A)
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d[None, :], d[:, None] * R
+
+
 def orthogonalize_rl(Y):
     """Algorithm 1: X right-orthogonal and equal to Y. For n = N..2: thin QR
-    of H(X_n)^T, H(X_n) := Q^T, V(X_{n-1}) := V(Y_{n-1}) R^T."""
+    of H(X_n)^T, H(X_n) := Q^T, V(X_{n-1}) := V(Y_{n-1}) R^T (thin QR with a
+    nonnegative diagonal of R, see qr_pos)."""
     X = [np.array(c, copy=True) for c in Y]
     N = len(X)
     for n in range(N, 1, -1):
         Xn = X[n - 1]
-        Q, R = np.linalg.qr(H(Xn).T)
+        Q, R = qr_pos(H(Xn).T)
         X[n - 1] = from_H(Q.T, Xn.shape[1])
         X[n - 2] = from_V(V(X[n - 2]) @ R.T, X[n - 2].shape[1])
     return X

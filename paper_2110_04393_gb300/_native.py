@@ -25,6 +25,14 @@ SIGNATURES = {
     "tt_round_sum_rand_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64, c_dbl, c_i32]),
     "tt_round_rand": (c_i32, [c_i32, P_i64, P_i64, P_vp, P_i64, P_vp, c_u64, c_dbl, c_i32, P_vp, P_i64, c_vp,
                               c_size, c_vp]),
+    "tt_round_det": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, c_dbl, c_i64, P_vp, P_i64, c_vp, c_size,
+                             c_vp]),
+    "tt_round_det_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, c_dbl, c_i64]),
+    "tt_round_det_out_capacity": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_i64]),
+    "tt_round_orthrand": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, P_vp, P_i64, c_vp,
+                                  c_size, c_vp]),
+    "tt_round_orthrand_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64]),
+    "tt_orthrand_omega_ranks": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_i64]),
     "tt_noalloc_scratch_bytes": (c_size, []),
     "tt_round_sum_rand_noalloc": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl,
                                           c_i32, P_vp, P_i64, c_vp]),

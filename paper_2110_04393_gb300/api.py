@@ -131,6 +131,88 @@ def tt_round_sum_rand(summands, ells, *, tol=0.0, sketch=None, seed=0, coeffs=No
     return res
 
 
+def _sum_args(summands):
+    N = len(summands[0])
+    dims = [int(c.shape[1]) for c in summands[0]]
+    ranks = []
+    for j, Y in enumerate(summands):
+        if len(Y) != N:
+            raise ValueError("all summands need the same order")
+        ranks += [int(Y[0].shape[0])] + [int(c.shape[2]) for c in Y]
+        for n, c in enumerate(Y):
+            _check_core(c, f"summand {j} core {n}")
+            if int(c.shape[1]) != dims[n]:
+                raise ValueError("mode sizes differ between summands")
+    flat = [c for Y in summands for c in Y]
+    return N, len(summands), dims, ranks, flat
+
+
+def _workspace(nbytes, device, workspace):
+    if workspace is None:
+        workspace = torch.empty(max(int(nbytes), 1) + 256, dtype=torch.uint8, device=device)
+    p = workspace.data_ptr()
+    p += (-p) % 256
+    return workspace, ctypes.c_void_p(p), workspace.numel() - (p - workspace.data_ptr())
+
+
+def tt_round_det(summands, *, tol=0.0, max_rank=0, coeffs=None, workspace=None, stream=None):
+    """Algorithms 1 + 2 (deterministic TT-SVD rounding) of the formed sum."""
+    N, K, dims, ranks, flat = _sum_args(summands)
+    device = summands[0][0].device
+    L = nat.lib()
+    dims_a, ranks_a = _i64(dims), _i64(ranks)
+    caps = (ctypes.c_int64 * N)()
+    _check(L.tt_round_det_out_capacity(N, K, dims_a, ranks_a, caps))
+    out = [torch.empty(int(caps[n]), dtype=torch.float64, device=device) for n in range(N)]
+    nb = L.tt_round_det_workspace(N, K, dims_a, ranks_a, float(tol), int(max_rank))
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    co = (ctypes.c_double * K)(*[float(c) for c in coeffs]) if coeffs is not None else None
+    out_ranks = (ctypes.c_int64 * (N + 1))()
+    _check(L.tt_round_det(N, K, dims_a, ranks_a, _ptrs(flat), co, float(tol), int(max_rank), _ptrs(out), out_ranks,
+                          wp, wb, _stream(stream, device)))
+    r = [int(x) for x in out_ranks]
+    return [out[n][:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)]
+
+
+def tt_orthrand_omega_ranks(dims, ranks_per_summand):
+    N = len(dims)
+    K = len(ranks_per_summand)
+    flat = [int(r) for R in ranks_per_summand for r in R]
+    rp = (ctypes.c_int64 * (N + 1))()
+    _check(nat.lib().tt_orthrand_omega_ranks(N, K, _i64(dims), _i64(flat), rp))
+    return [int(x) for x in rp]
+
+
+def tt_round_orthrand(summands, ells, *, omega=None, seed=0, coeffs=None, workspace=None, stream=None):
+    """Algorithm 4 (Orthogonalize-then-Randomize) of the formed sum.
+    omega: optional list of N-1 Gaussian matrices Omega_n (R'_n x l_n)."""
+    N, K, dims, ranks, flat = _sum_args(summands)
+    device = summands[0][0].device
+    ell = clamp_ranks(dims, ells)
+    L = nat.lib()
+    dims_a, ranks_a, ell_a = _i64(dims), _i64(ranks), _i64(ell)
+    om = None
+    if omega is not None:
+        rp = tt_orthrand_omega_ranks(dims, [ranks[j * (N + 1):(j + 1) * (N + 1)] for j in range(K)])
+        for n in range(1, N):
+            o = omega[n - 1]
+            if not (o.is_cuda and o.dtype == torch.float64 and o.is_contiguous() and tuple(o.shape) == (rp[n], ell[n])):
+                raise ValueError(f"omega[{n - 1}] must be a contiguous float64 CUDA ({rp[n]}, {ell[n]}) matrix")
+        om = _ptrs(list(omega) + [omega[0]])
+    out = [torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float64, device=device) for n in range(N)]
+    nb = L.tt_round_orthrand_workspace(N, K, dims_a, ranks_a, ell_a)
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    co = (ctypes.c_double * K)(*[float(c) for c in coeffs]) if coeffs is not None else None
+    out_ranks = (ctypes.c_int64 * (N + 1))()
+    _check(L.tt_round_orthrand(N, K, dims_a, ranks_a, _ptrs(flat), co, ell_a, om, ctypes.c_uint64(int(seed)),
+                               _ptrs(out), out_ranks, wp, wb, _stream(stream, device)))
+    return out
+
+
 def tt_round_rand(Y, ells, **kw):
     """Algorithm 5 (single TT, Randomize-then-Orthogonalize): tt_round_sum_rand with K = 1."""
     if kw.get("coeffs") is not None:

@@ -41,3 +41,24 @@ def bytes_sum_randorth(dims, ranks_per_summand, ells):
     sk = sum(ells[n - 1] * dims[n - 1] * ells[n] for n in range(2, N + 1))
     out = sum(ells[n] * dims[n] * ells[n + 1] for n in range(N))
     return 8.0 * (2 * inp + sk + out)
+
+
+def flops_det(dims, formed_ranks, out_ranks):
+    """Algorithm 1 + Algorithm 2 on the formed sum (Appendix A): per core the
+    right-to-left orthogonalization costs 4 m k^2 - 4 k^3/3 (Householder QR of
+    H(X_n)^T, m = I_n R_n, k = R_{n-1}) plus R_{n-2} I_{n-1} k^2 (the triangular
+    update); the left-to-right truncation costs the QR of V(X_n), the SVD of R
+    (~ 12 k^3) and the two updates 2 m k r + 2 r k I R_{n+1}."""
+    N = len(dims)
+    R = list(formed_ranks)
+    f = 0.0
+    for n in range(N, 1, -1):
+        m, k = dims[n - 1] * R[n], R[n - 1]
+        if m >= k:
+            f += 4.0 * m * k * k - 4.0 * k ** 3 / 3.0 + R[n - 2] * dims[n - 2] * k * k
+    r = out_ranks
+    for n in range(1, N):
+        m, k = R[n - 1] * dims[n - 1], R[n]
+        f += 4.0 * m * k * k - 4.0 * k ** 3 / 3.0 + 12.0 * k ** 3
+        f += 2.0 * m * k * r[n] + 2.0 * r[n] * k * dims[n] * R[n + 1]
+    return f

@@ -32,7 +32,8 @@ int plan_workspace_bytes(const BuildFn& build, size_t* bytes) {
   Schedule s;
   TTR_TRY(build(a, s));
   *bytes = a.used + align256(size_t(s.pbuf_need) * sizeof(double)) + align256(s.descs.size() * sizeof(GemmDesc)) +
-           align256(size_t(std::max<int64_t>(s.cnt_need, 1)) * sizeof(int)) + 256;
+           align256(size_t(std::max<int64_t>(s.cnt_need, 1)) * sizeof(int)) +
+           align256(std::max<size_t>(s.copies.size(), 1) * sizeof(Copy3)) + 256;
   return TT_OK;
 }
 
@@ -45,7 +46,8 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
     TTR_TRY(build(a, probe));
     need = a.used + align256(size_t(probe.pbuf_need) * sizeof(double)) +
            align256(probe.descs.size() * sizeof(GemmDesc)) +
-           align256(size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int)) + 256;
+           align256(size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int)) +
+           align256(std::max<size_t>(probe.copies.size(), 1) * sizeof(Copy3)) + 256;
   }
   void* ws = workspace;
   bool owned = false;
@@ -74,6 +76,7 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
   s.pbuf = a.take<double>(size_t(std::max<int64_t>(probe.pbuf_need, 1)));
   GemmDesc* d_descs = a.take<GemmDesc>(std::max<size_t>(probe.descs.size(), 1));
   s.cnt = a.take<int>(size_t(std::max<int64_t>(probe.cnt_need, 1)));
+  s.d_copies = a.take<Copy3>(std::max<size_t>(probe.copies.size(), 1));
   int rc = TT_OK;
   {
     cudaError_t e = cudaMemsetAsync(s.cnt, 0, size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int), st);
@@ -88,6 +91,14 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
       set_error(std::string("descriptor upload: ") + cudaGetErrorString(e));
+      rc = TT_ECUDA;
+    }
+  }
+  if (rc == TT_OK && !s.copies.empty()) {
+    cudaError_t e = cudaMemcpyAsync(s.d_copies, s.copies.data(), s.copies.size() * sizeof(Copy3),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      set_error(std::string("copy descriptor upload: ") + cudaGetErrorString(e));
       rc = TT_ECUDA;
     }
   }
@@ -157,9 +168,9 @@ static int validate_sum(int32_t N, int32_t K, const int64_t* dims, const int64_t
   for (int n = 1; n < N; ++n) P->ell[n] = std::min(P->ell[n], P->ell[n - 1] * P->I[n - 1]);
   for (int n = N - 1; n >= 1; --n) P->ell[n] = std::min(P->ell[n], P->ell[n + 1] * P->I[n]);
   for (int n = 1; n < N; ++n)
-    if (P->ell[n] > TSQR_KMAX) {
+    if (P->ell[n] > TT_MAX_RANK) {
       set_error("target rank " + std::to_string(P->ell[n]) + " above the supported maximum " +
-                std::to_string(TSQR_KMAX));
+                std::to_string(TT_MAX_RANK));
       return TT_EUNSUPPORTED;
     }
   return TT_OK;
@@ -198,8 +209,10 @@ static int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int
   b.sig = ar.take<double>(kmax);
   b.tmp = ar.take<double>(cmax);
   *rk_out = b.rk;
-  std::vector<QrBufs> qb(N + 1);
-  for (int n = 2; n <= N; ++n) qb[n] = qr_reserve(ar, I[n - 1] * ell[n], int(ell[n - 1]));
+  std::vector<std::pair<int64_t, int>> shapes;
+  for (int n = 2; n <= N; ++n) shapes.push_back({I[n - 1] * ell[n], int(ell[n - 1])});
+  const QrPool pool = qr_pool_reserve(ar, shapes);
+  double* sbig = ar.take<double>(std::max<size_t>(svd_scratch_doubles(int(kmax)), 1));
 
   {   // int64 ranks staged through a double-sized host buffer
     std::vector<int64_t> tmp(ell.begin(), ell.end());
@@ -214,9 +227,9 @@ static int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int
     const int64_t m = I[n - 1] * ell[n], k = ell[n - 1];
     double* Xn = out[n - 1];
     double* Xp = out[n - 2];
-    qr_plan(sc, qb[n], Xn, 1, m, b.Qt, k, 1, b.Rb);
+    qr_plan(sc, qr_view(pool, m, int(k)), Xn, 1, m, b.Qt, k, 1, b.Rb);
     sc.add([=](cudaStream_t s) -> int {
-      return svd_trunc_launch(int(k), b.Rb, b.eps, int(k), b.G1, b.G2, b.sig, b.rk + (n - 1), s);
+      return svd_trunc_launch(int(k), b.Rb, b.eps, int(k), b.G1, b.G2, b.sig, b.rk + (n - 1), s, sbig);
     });
     // new H(X_n) = (Q G1)^T : column-major m x k view of core n
     sc.gemm({gdesc(b.Qt, k, 1, b.G1, k, 1, Xn, 1, m, m, k, k)});
@@ -273,8 +286,9 @@ static int build_sum_rand_fp64(const SumProblem& P, const double* const* sketch_
       sk[n] = skw[n];
     }
   }
-  std::vector<QrBufs> qb(N + 1);
-  for (int n = 1; n < N; ++n) qb[n] = qr_reserve(ar, ell[n - 1] * In(n), int(ell[n]));
+  std::vector<std::pair<int64_t, int>> shapes;
+  for (int n = 1; n < N; ++n) shapes.push_back({ell[n - 1] * In(n), int(ell[n])});
+  const QrPool pool = qr_pool_reserve(ar, shapes);
 
   // ---- set-up: counters, W_N = ones, M_0 = coefficients, sketch
   sc.add([=](cudaStream_t s) -> int { return fill_launch(W[N], S[N] * ell[N], 1.0, s); });
@@ -324,7 +338,7 @@ static int build_sum_rand_fp64(const SumProblem& P, const double* const* sketch_
     if (n == N) break;
     const int64_t m = ell[n - 1] * In(n), k = ell[n];
     double* Qn = out[n - 1];
-    qr_plan(sc, qb[n], Ys, k, 1, Qn, k, 1, nullptr);
+    qr_plan(sc, qr_view(pool, m, int(k)), Ys, k, 1, Qn, k, 1, nullptr);
     sc.gemm({gdesc(Qn, 1, k, X, S[n], 1, Mn, S[n], 1, k, S[n], m)});
   }
 

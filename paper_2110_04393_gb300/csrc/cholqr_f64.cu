@@ -1,25 +1,30 @@
-// Thin QR by Cholesky QR with an automatic shift (Fukaya, Kannan, Nakatsukasa,
+// Thin QR by Cholesky QR with automatic shifts (Fukaya, Kannan, Nakatsukasa,
 // Zhang, Kawamura, "Shifted Cholesky QR for computing the QR factorization of
-// ill-conditioned matrices", SIAM J. Sci. Comput. 42 (2020)):
-//   pass 0: G = A^T A; Cholesky G = R1^T R1. If it breaks down, retry with
-//           G + s I, s = 11 (m k + k (k+1)) u ||A||_F^2 (shifted pass).
-//   pass 1: Q1 = A R1^{-1}; G = Q1^T Q1 = R2^T R2.
-//   pass 2: Q2 = Q1 R2^{-1}; unshifted chain: Q2 is the result, check Q2^T Q2 = I;
-//           shifted chain: G = Q2^T Q2 = R3^T R3.
-//   pass 3: (shifted chain only) Q = Q2 R3^{-1}, check Q^T Q = I.
-//   R = R3 R2 R1 (accumulated when asked for).
-// Orthogonality and residual are of order u for cond(A) up to about 1/u.
+// ill-conditioned matrices", SIAM J. Sci. Comput. 42 (2020)). A chain of
+// passes; pass 0 factors G = A^T A, every later pass multiplies the current
+// block by the previous inverse factor and factors its Gram matrix:
+//   * a factorization that breaks down is retried with G + s I,
+//     s = 11 (m k + k (k+1)) u ||.||_F^2 (a shifted pass);
+//   * once two consecutive factorizations were unshifted, the next pass writes
+//     the final Q and checks Q^T Q = I to 64 k u.
+// So a well-conditioned A takes CholeskyQR2 (3 passes), cond(A) up to 1/u takes
+// shifted CholeskyQR3 (4 passes), and an exactly rank-deficient A (zero singular
+// values met when a target rank exceeds the true rank) takes up to two shifts:
+// its null directions come out as orthonormal round-off directions, as with
+// Householder. R = R_last ... R_1 is accumulated when asked for. Six passes are
+// launched; passes after the final one exit at once.
 //
 // GB300 design: FP64 issues at 2 DFMA/clk/SM with long latency, so a
 // Householder column step (reduction, sqrt, divide, barriers) is latency bound
 // and a TSQR tree stacks several of them. Here each pass is one launch over
 // ~one CTA per SM: every CTA multiplies its row block by the previous inverse
 // factor, stores it, and forms its partial Gram matrix; the last CTA to arrive
-// (arrival counter, no waiting) sums the partials in block order and runs the
-// k x k Cholesky with the inverse formed alongside. If a pivot fails or the
-// final Q^T Q misses the identity by more than 64 k u, a device flag is raised
-// and the Householder TSQR (which reads that flag and otherwise exits at once)
-// recomputes Q and R. No host synchronization is involved.
+// (arrival counters, two levels, no waiting) sums the partials in block order
+// and runs the k x k Cholesky with the inverse formed alongside (in shared
+// memory for k <= 96, in global scratch above). If the final check fails, a
+// device flag is raised: for k <= 96 the Householder TSQR (which reads that
+// flag and otherwise exits at once) recomputes Q and R; above, the flag is
+// reported to the caller. No host synchronization is involved.
 #include <algorithm>
 
 #include "plan.cuh"
@@ -32,26 +37,24 @@ namespace {
 
 constexpr int CQ_THREADS = 256;
 constexpr int CQ_GROUP = 16;
-enum { CQ_NONE = 0, CQ_CHOL_AUTO = 1, CQ_CHOL = 2, CQ_CHECK = 3 };
+constexpr int CQ_SMEM_K = 96;   // above this the k x k factors live in global scratch
+
+constexpr int CQ_MAX_PASSES = 6;
 
 struct CqrPass {
   int64_t m;
-  int k, b, P;
-  const double* src;
-  int64_t s_rs, s_cs;
-  const double* Rin;        // k x k upper (row-major) applied on the right, or null
-  double* dst_sh;           // destination when the chain is shifted
-  int64_t dsh_rs, dsh_cs;
-  double* dst_un;           // destination when the chain is unshifted
-  int64_t dun_rs, dun_cs;
-  int mode_sh, mode_un;
-  int only_if_shifted;
-  double* Gpart;            // P x k x k
-  int* counter;
-  double* Rinv;             // k x k out (may alias Rin)
+  int k, b, P, pass;
+  const double* A;          // input
+  int64_t a_rs, a_cs;
+  double* buf[2];           // m x k ping-pong blocks (row-major)
+  double* Q;                // final Q
+  int64_t q_rs, q_cs;
+  double* Gpart;            // (P + groups) x k x k
+  int* counter;             // [0] final arrival, [1 + g] group arrivals
+  double* Rinv;             // k x k (upper, row-major)
   double* Racc;             // k x k accumulated R, or null
-  int first;
-  int* status;              // [0] failure, [1] shifted chain
+  double* big;              // 3 k x k global scratch when k > CQ_SMEM_K (else null)
+  int* status;              // [0] failure, [1] unshifted run, [2] done, [3] factorizations so far
 };
 
 // In-place right-looking Cholesky of G (k x k row-major, lower part) with
@@ -100,30 +103,35 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   __shared__ double s_rd;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int k = a.k, b = a.b;
-  const int shifted = __ldcg(a.status + 1);
-  if (a.only_if_shifted && !shifted) return;
-  double* dst = shifted ? a.dst_sh : a.dst_un;
-  const int64_t d_rs = shifted ? a.dsh_rs : a.dun_rs, d_cs = shifted ? a.dsh_cs : a.dun_cs;
-  const int mode = shifted ? a.mode_sh : a.mode_un;
+  if (__ldcg(a.status + 2)) return;                         // chain already finished
+  const int unshifted_run = __ldcg(a.status + 1);
+  const bool final_pass = (a.pass > 0) && (unshifted_run >= 2 || a.pass == CQ_MAX_PASSES - 1);
+  const double* src = (a.pass <= 1) ? a.A : a.buf[(a.pass - 2) & 1];
+  const int64_t s_rs = (a.pass <= 1) ? a.a_rs : k, s_cs = (a.pass <= 1) ? a.a_cs : 1;
+  double* dst = (a.pass == 0) ? nullptr : (final_pass ? a.Q : a.buf[(a.pass - 1) & 1]);
+  const int64_t d_rs = final_pass ? a.q_rs : k, d_cs = final_pass ? a.q_cs : 1;
+  const bool big = (a.big != nullptr);
 
-  // ---- row block: T = src rows (times Rin), stored to dst, partial Gram
+  // ---- row block: T = src rows (times R^{-1} of the previous pass), stored, partial Gram
   double* T = sm;                 // b x k
   double* T2 = T + b * k;         // b x k
-  double* Rs = T2 + b * k;        // k x k
+  double* Rs = T2 + b * k;        // k x k (shared when small)
+  const double* Rin = (a.pass == 0) ? nullptr : a.Rinv;
   const int64_t r0 = int64_t(blockIdx.x) * b;
   for (int idx = tid; idx < b * k; idx += nt) {
     const int r = idx / k, c = idx % k;
     const int64_t gr = r0 + r;
-    T[idx] = (gr < a.m) ? a.src[gr * a.s_rs + c * a.s_cs] : 0.0;
+    T[idx] = (gr < a.m) ? src[gr * s_rs + c * s_cs] : 0.0;
   }
-  if (a.Rin)
-    for (int idx = tid; idx < k * k; idx += nt) Rs[idx] = __ldcg(a.Rin + idx);
+  if (Rin && !big)
+    for (int idx = tid; idx < k * k; idx += nt) Rs[idx] = __ldcg(Rin + idx);
   __syncthreads();
-  if (a.Rin) {
+  if (Rin) {
+    const double* Rr = big ? Rin : Rs;
     for (int idx = tid; idx < b * k; idx += nt) {
       const int r = idx / k, c = idx % k;
       double s = 0.0;
-      for (int j = 0; j <= c; ++j) s = fma(T[r * k + j], Rs[j * k + c], s);
+      for (int j = 0; j <= c; ++j) s = fma(T[r * k + j], big ? __ldcg(Rr + j * k + c) : Rr[j * k + c], s);
       T2[idx] = s;
     }
     __syncthreads();
@@ -135,7 +143,6 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
       const int64_t gr = r0 + r;
       if (gr < a.m) dst[gr * d_rs + c * d_cs] = T[idx];
     }
-  if (mode == CQ_NONE) return;
   double* Gp = a.Gpart + int64_t(blockIdx.x) * k * k;
   for (int idx = tid; idx < k * k; idx += nt) {
     const int i = idx / k, j = idx % k;
@@ -185,10 +192,10 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   if (!s_last) return;
   __threadfence();
 
-  // ---- last group: G = sum of group partials in order, then Cholesky / check
-  double* G = sm;                 // k x k
-  double* X = G + k * k;          // k x k
-  double* G0 = X + k * k;         // k x k (copy for the shifted retry / R accumulation)
+  // ---- last group: G = sum of group partials in order, then check or factor
+  double* G = big ? a.big : sm;                 // k x k
+  double* X = G + k * k;                        // k x k
+  double* G0 = X + k * k;                       // k x k
   for (int idx = tid; idx < k * k; idx += nt) {
     const double* base = a.Gpart + int64_t(a.P) * k * k + idx;
     double u[4] = {0, 0, 0, 0};
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
     G0[idx] = sv;
   }
   __syncthreads();
-  if (mode == CQ_CHECK) {
+  if (final_pass) {
     __shared__ int bad;
     if (tid == 0) bad = 0;
     __syncthreads();
@@ -213,27 +220,37 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
       if (!(fabs(dv) <= tol)) bad = 1;
     }
     __syncthreads();
-    if (tid == 0 && bad) atomicExch(a.status, 1);
+    if (tid == 0) {
+      if (bad) atomicExch(a.status, 1);
+      atomicExch(a.status + 2, 1);
+    }
     return;
   }
   bool ok = chol_with_inverse(G, X, k, &s_rd);
-  if (!ok && mode == CQ_CHOL_AUTO) {
+  bool shifted = false;
+  if (!ok) {
     __shared__ double s_shift;
     if (tid == 0) {
       double tr = 0.0;
       for (int i = 0; i < k; ++i) tr += G0[i * k + i];
       s_shift = 11.0 * (double(a.m) * k + double(k) * (k + 1)) * 0x1p-53 * tr;
-      atomicExch(a.status + 1, 1);
     }
     __syncthreads();
     for (int idx = tid; idx < k * k; idx += nt) G[idx] = G0[idx] + (((idx / k) == (idx % k)) ? s_shift : 0.0);
     __syncthreads();
     ok = chol_with_inverse(G, X, k, &s_rd);
+    shifted = true;
   }
-  if (!ok) {
-    if (tid == 0) atomicExch(a.status, 1);
-    for (int idx = tid; idx < k * k; idx += nt) a.Rinv[idx] = ((idx / k) == (idx % k)) ? 1.0 : 0.0;
+  if (!ok) {                                    // not even the shifted Gram is positive definite
+    if (tid == 0) {
+      atomicExch(a.status, 1);
+      atomicExch(a.status + 2, 1);
+    }
     return;
+  }
+  if (tid == 0) {
+    a.status[1] = shifted ? 0 : unshifted_run + 1;
+    a.status[3] += 1;
   }
   // Rinv = L^{-T} (upper)
   for (int idx = tid; idx < k * k; idx += nt) {
@@ -241,7 +258,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
     a.Rinv[idx] = (c >= r) ? X[c * k + r] : 0.0;
   }
   if (a.Racc) {
-    if (!a.first) {
+    if (a.pass > 0) {
       for (int idx = tid; idx < k * k; idx += nt) G0[idx] = a.Racc[idx];
       __syncthreads();
       for (int idx = tid; idx < k * k; idx += nt) {
@@ -260,7 +277,8 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
 }
 
 int cqr_launch(const CqrPass& p, cudaStream_t s) {
-  const size_t smem = std::max<size_t>(size_t(2) * p.b * p.k + size_t(p.k) * p.k, size_t(3) * p.k * p.k) *
+  const size_t kk = size_t(p.k) * p.k;
+  const size_t smem = (p.big ? size_t(2) * p.b * p.k : std::max<size_t>(size_t(2) * p.b * p.k + kk, 3 * kk)) *
                       sizeof(double);
   static bool attr = false;
   if (!attr) {
@@ -275,25 +293,71 @@ int cqr_launch(const CqrPass& p, cudaStream_t s) {
 
 }  // namespace
 
-QrBufs qr_reserve(Arena& ar, int64_t m, int k) {
+namespace {
+void qr_shape(int64_t m, int k, int* rows, int* P, int* nstat) {
+  const bool big = k > CQ_SMEM_K;
+  const int64_t budget = 28000 - (big ? 0 : int64_t(k) * k);                 // doubles of shared memory
+  const int64_t bmax = std::max<int64_t>(1, budget / (2 * int64_t(k)));
+  *rows = int(std::min<int64_t>(bmax, std::max<int64_t>(4, ceil_div(m, num_sms()))));
+  *P = int(ceil_div(m, *rows));
+  *nstat = 4 + 1 + (*P + 15) / 16;      // [0..3] chain state, then arrival counters
+}
+}  // namespace
+
+QrPool qr_pool_reserve(Arena& ar, const std::vector<std::pair<int64_t, int>>& shapes) {
+  size_t gp = 1, kk = 1, mk = 1, bigk = 0, st = 1, tw = 1, ti = 1;
+  for (auto& sh : shapes) {
+    const int64_t m = sh.first;
+    const int k = sh.second;
+    int rows, P, ns;
+    qr_shape(m, k, &rows, &P, &ns);
+    gp = std::max<size_t>(gp, size_t(P + (P + 15) / 16) * k * k);
+    kk = std::max<size_t>(kk, size_t(k) * k);
+    mk = std::max<size_t>(mk, size_t(m) * k);
+    if (k > CQ_SMEM_K) bigk = std::max<size_t>(bigk, 3 * size_t(k) * k);
+    st = std::max<size_t>(st, size_t(ns));
+    if (k <= TSQR_KMAX) {
+      size_t ii = 0;
+      tw = std::max(tw, tsqr_work_doubles(tsqr_shape(m, k), &ii));
+      ti = std::max(ti, ii);
+    }
+  }
+  QrPool p;
+  p.Gpart = ar.take<double>(gp);
+  p.Rinv = ar.take<double>(kk);
+  p.Q1 = ar.take<double>(mk);
+  p.Q2 = ar.take<double>(mk);
+  p.big = bigk ? ar.take<double>(bigk) : nullptr;
+  p.status = ar.take<int>(st);
+  p.tw = ar.take<double>(tw);
+  p.ti = ar.take<int>(ti);
+  return p;
+}
+
+QrBufs qr_view(const QrPool& p, int64_t m, int k) {
   QrBufs b;
   b.m = m;
   b.k = k;
-  const int64_t bmax = std::max<int64_t>(4, (28000 - int64_t(k) * k) / (2 * int64_t(k)));   // shared memory cap
-  b.rows = int(std::min<int64_t>(bmax, std::max<int64_t>(4, ceil_div(m, num_sms()))));
-  b.P = int(ceil_div(m, b.rows));
-  b.Gpart = ar.take<double>(int64_t(b.P + (b.P + 15) / 16) * k * k);   // partials + group partials
-  b.Rinv = ar.take<double>(int64_t(k) * k);
-  b.Q1 = ar.take<double>(m * k);
-  b.Q2 = ar.take<double>(m * k);
-  b.status = ar.take<int>(3 + (b.P + 15) / 16);   // fail, shifted, counter, group counters
-  b.sh = tsqr_shape(m, k);
-  size_t ii = 0;
-  const size_t dd = tsqr_work_doubles(b.sh, &ii);
-  b.tw = ar.take<double>(std::max<size_t>(dd, 1));
-  b.ti = ar.take<int>(ii);
-  b.ti_n = ii;
+  qr_shape(m, k, &b.rows, &b.P, &b.nstat);
+  b.Gpart = p.Gpart;
+  b.Rinv = p.Rinv;
+  b.Q1 = p.Q1;
+  b.Q2 = p.Q2;
+  b.big = (k > CQ_SMEM_K) ? p.big : nullptr;
+  b.status = p.status;
+  if (k <= TSQR_KMAX) {
+    b.sh = tsqr_shape(m, k);
+    size_t ii = 0;
+    tsqr_work_doubles(b.sh, &ii);
+    b.tw = p.tw;
+    b.ti = p.ti;
+    b.ti_n = ii;
+  }
   return b;
+}
+
+QrBufs qr_reserve(Arena& ar, int64_t m, int k) {
+  return qr_view(qr_pool_reserve(ar, {{m, k}}), m, k);
 }
 
 void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q, int64_t q_rs,
@@ -301,7 +365,7 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
   const QrBufs bb = b;
   sc.add([bb](cudaStream_t s) -> int {
     if (!bb.status) return int(TT_OK);
-    TTR_CHECK_CUDA(cudaMemsetAsync(bb.status, 0, (3 + (bb.P + 15) / 16) * sizeof(int), s));
+    TTR_CHECK_CUDA(cudaMemsetAsync(bb.status, 0, bb.nstat * sizeof(int), s));
     if (bb.ti && bb.ti_n) TTR_CHECK_CUDA(cudaMemsetAsync(bb.ti, 0, bb.ti_n * sizeof(int), s));
     return int(TT_OK);
   });
@@ -310,45 +374,33 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
   base.k = b.k;
   base.b = b.rows;
   base.P = b.P;
+  base.A = A;
+  base.a_rs = a_rs;
+  base.a_cs = a_cs;
+  base.buf[0] = b.Q1;
+  base.buf[1] = b.Q2;
+  base.Q = Q;
+  base.q_rs = q_rs;
+  base.q_cs = q_cs;
   base.Gpart = b.Gpart;
-  base.counter = b.status ? b.status + 2 : nullptr;
+  base.counter = b.status ? b.status + 4 : nullptr;
   base.Rinv = b.Rinv;
   base.Racc = R;
+  base.big = b.big;
   base.status = b.status;
-  const int k = b.k;
-  // pass 0: Gram of A, Cholesky (shift on breakdown)
-  CqrPass p0 = base;
-  p0.src = A; p0.s_rs = a_rs; p0.s_cs = a_cs;
-  p0.mode_sh = p0.mode_un = CQ_CHOL_AUTO;
-  p0.first = 1;
-  // pass 1: Q1 = A R1^{-1}, Gram, Cholesky
-  CqrPass p1 = base;
-  p1.src = A; p1.s_rs = a_rs; p1.s_cs = a_cs; p1.Rin = b.Rinv;
-  p1.dst_sh = p1.dst_un = b.Q1; p1.dsh_rs = p1.dun_rs = k; p1.dsh_cs = p1.dun_cs = 1;
-  p1.mode_sh = p1.mode_un = CQ_CHOL;
-  // pass 2: Q2 = Q1 R2^{-1}; final (check) unless the chain was shifted
-  CqrPass p2 = base;
-  p2.src = b.Q1; p2.s_rs = k; p2.s_cs = 1; p2.Rin = b.Rinv;
-  p2.dst_sh = b.Q2; p2.dsh_rs = k; p2.dsh_cs = 1;
-  p2.dst_un = Q; p2.dun_rs = q_rs; p2.dun_cs = q_cs;
-  p2.mode_sh = CQ_CHOL;
-  p2.mode_un = CQ_CHECK;
-  // pass 3: shifted chain only
-  CqrPass p3 = base;
-  p3.src = b.Q2; p3.s_rs = k; p3.s_cs = 1; p3.Rin = b.Rinv;
-  p3.dst_sh = p3.dst_un = Q; p3.dsh_rs = p3.dun_rs = q_rs; p3.dsh_cs = p3.dun_cs = q_cs;
-  p3.mode_sh = p3.mode_un = CQ_CHECK;
-  p3.only_if_shifted = 1;
-  for (const CqrPass* p : {&p0, &p1, &p2, &p3}) {
-    const CqrPass pp = *p;
+  for (int p = 0; p < CQ_MAX_PASSES; ++p) {
+    CqrPass pp = base;
+    pp.pass = p;
     sc.add([pp](cudaStream_t s) -> int { return cqr_launch(pp, s); });
   }
-  // Householder fallback, run only when the device flag is raised
-  sc.add([bb, A, a_rs, a_cs, Q, q_rs, q_cs, R](cudaStream_t s) -> int {
-    TsqrWork w;
-    tsqr_bind(bb.sh, bb.tw, bb.ti, &w);
-    return tsqr_launch(bb.sh, w, A, a_rs, a_cs, Q, q_rs, q_cs, R, s, bb.status);
-  });
+  if (b.k <= TSQR_KMAX) {
+    // Householder fallback, run only when the device flag is raised
+    sc.add([bb, A, a_rs, a_cs, Q, q_rs, q_cs, R](cudaStream_t s) -> int {
+      TsqrWork w;
+      tsqr_bind(bb.sh, bb.tw, bb.ti, &w);
+      return tsqr_launch(bb.sh, w, A, a_rs, a_cs, Q, q_rs, q_cs, R, s, bb.status);
+    });
+  }
 }
 
 }  // namespace ttr

@@ -44,7 +44,8 @@ int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, double flops,
 // leaves of b rows are factored in parallel, their R factors are combined up a
 // binary tree inside the same launch (the last CTA to finish a pair combines
 // it, so no CTA waits), and a second launch forms the explicit thin Q.
-constexpr int TSQR_KMAX = 96;
+constexpr int TSQR_KMAX = 96;   // Householder fallback limit; Cholesky QR has none
+constexpr int TT_MAX_RANK = 1024;   // largest target rank / formed rank handled
 struct TsqrWork {
   double* leafV;     // P * b * k
   double* leafTau;   // P * k
@@ -77,11 +78,25 @@ int tsqr_launch(const TsqrShape& sh, const TsqrWork& w, const double* A, int64_t
 //        sqrt(sum_{i>r} s_i^2) <= eps, G1 = [U_r 0], G2 = [V_r S_r 0].
 // eps is read from device memory (eps_ptr), or taken as 0 when eps_ptr is null
 // (fixed rank cap rcap). The rank is written to *rank_out (device).
+// k > 96 needs global scratch of svd_scratch_doubles(k) doubles (else may be null).
+size_t svd_scratch_doubles(int k);
 int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, double* G1, double* G2,
-                     double* sigma, int64_t* rank_out, cudaStream_t s);
+                     double* sigma, int64_t* rank_out, cudaStream_t s, double* big = nullptr);
 
 // ----------------------------------------------------------------------------
 // Elementwise helpers.
+struct Copy3 {
+  const double* src;
+  double* dst;
+  int64_t n0, n1, n2;        // extents
+  int64_t s0, s1, s2;        // source strides
+  int64_t d0, d1, d2;        // destination strides
+  double scale;
+  int64_t begin;             // prefix of n0*n1*n2 over the batch (set by the planner)
+};
+int copy3_launch(const Copy3* d_descs, int n, int64_t total, cudaStream_t s);
+// dst[0] := 1 if src[0] != 0 (device flags)
+int or_flag_launch(int* dst, const int* src, cudaStream_t s);
 int fill_launch(double* p, int64_t n, double v, cudaStream_t s);
 int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, uint64_t seed,
                   cudaStream_t s);

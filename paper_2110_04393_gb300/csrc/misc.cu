@@ -128,3 +128,49 @@ int num_sms() {
 }
 
 }  // namespace ttr
+
+// ---------------------------------------------------------------------------
+// Batched strided 3-D copies dst[a, i, b] = scale * src[a, i, b] (one launch for
+// all summand blocks of a formed TT-sum core, Section 2.1).
+namespace ttr {
+namespace {
+__global__ void copy3_kernel(const Copy3* __restrict__ d, int n, int64_t total) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (d[mid].begin <= e) lo = mid; else hi = mid - 1;
+    }
+    const Copy3& c = d[lo];
+    int64_t l = e - c.begin;
+    const int64_t z = l % c.n2; l /= c.n2;
+    const int64_t y = l % c.n1;
+    const int64_t x = l / c.n1;
+    c.dst[x * c.d0 + y * c.d1 + z * c.d2] = c.scale * c.src[x * c.s0 + y * c.s1 + z * c.s2];
+  }
+}
+}  // namespace
+
+int copy3_launch(const Copy3* d_descs, int n, int64_t total, cudaStream_t s) {
+  if (n == 0 || total == 0) return TT_OK;
+  copy3_kernel<<<grid_for(total, 256), 256, 0, s>>>(d_descs, n, total);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+}  // namespace ttr
+
+namespace ttr {
+namespace {
+__global__ void or_flag_kernel(int* dst, const int* src) {
+  if (threadIdx.x == 0 && src[0]) dst[0] = 1;
+}
+}  // namespace
+int or_flag_launch(int* dst, const int* src, cudaStream_t s) {
+  if (!dst || !src) return TT_OK;
+  or_flag_kernel<<<1, 32, 0, s>>>(dst, src);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+}  // namespace ttr

@@ -32,6 +32,20 @@ struct Schedule {
   void add(std::function<int(cudaStream_t)> f) {
     items.push_back([f](cudaStream_t s, const GemmDesc*) { return f(s); });
   }
+  // Copy descriptors live in the same uploaded table as raw bytes after the GEMM
+  // descriptors would complicate alignment; they get their own device region.
+  std::vector<Copy3> copies;
+  Copy3* d_copies = nullptr;     // bound by plan_execute
+  void copy3(std::vector<Copy3> g) {
+    if (g.empty()) return;
+    int64_t t = 0;
+    for (auto& c : g) { c.begin = t; t += c.n0 * c.n1 * c.n2; }
+    const size_t off = copies.size();
+    const int n = int(g.size());
+    copies.insert(copies.end(), g.begin(), g.end());
+    Copy3** base = &d_copies;
+    items.push_back([=](cudaStream_t s, const GemmDesc*) { return copy3_launch(*base + off, n, t, s); });
+  }
   // H2D copy of host values kept alive by the schedule.
   void upload(double* dst, std::vector<double> v) {
     host_keep.push_back(std::move(v));

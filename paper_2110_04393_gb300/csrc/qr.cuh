@@ -14,15 +14,33 @@ struct QrBufs {
   double* Rinv = nullptr;   // k x k inverse Cholesky factor
   double* Q1 = nullptr;     // m x k
   double* Q2 = nullptr;     // m x k
-  int* status = nullptr;    // [0] 1 = fall back to Householder, [1] shifted chain, [2] arrival counter
+  double* big = nullptr;    // 3 k x k global scratch for k > 96
+  int* status = nullptr;    // [0] failure (Householder fallback for k <= 96), [1] unshifted run,
+                            // [2] done, [3] factorizations, then arrival counters
+  int nstat = 0;
   TsqrShape sh{};
   double* tw = nullptr;
   int* ti = nullptr;
   size_t ti_n = 0;
 };
 
+// Scratch shared by QR factorizations that run one after another on a stream:
+// reserve once for every (m, k) shape, then take a view per factorization.
+struct QrPool {
+  double* Gpart = nullptr;
+  double* Rinv = nullptr;
+  double* Q1 = nullptr;
+  double* Q2 = nullptr;
+  double* big = nullptr;
+  int* status = nullptr;
+  double* tw = nullptr;
+  int* ti = nullptr;
+};
+QrPool qr_pool_reserve(Arena& ar, const std::vector<std::pair<int64_t, int>>& shapes);
+QrBufs qr_view(const QrPool& p, int64_t m, int k);
 QrBufs qr_reserve(Arena& ar, int64_t m, int k);
-// Q must not alias A (the fallback re-reads A).
+// Q must not alias A (the fallback re-reads A). After the schedule ran,
+// status[0] != 0 means no orthonormal Q was produced (only possible for k > 96).
 void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q, int64_t q_rs,
              int64_t q_cs, double* R);
 

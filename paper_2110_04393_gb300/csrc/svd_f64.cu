@@ -21,6 +21,7 @@ namespace ttr {
 namespace {
 
 constexpr int SVD_THREADS = 1024;
+constexpr int SVD_SMEM_K = 96;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -30,15 +31,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const double* __restrict__ R,
                                                                 const double* __restrict__ eps_ptr, int rcap,
                                                                 double* G1, double* G2, double* sigma,
-                                                                int64_t* rank_out) {
+                                                                int64_t* rank_out, double* big) {
   extern __shared__ double sm[];
   const int kk = k + (k & 1);        // even number of columns for the round-robin schedule
-  double* A = sm;                    // k x kk column-major (column k is zero padding)
+  double* base = big ? big : sm;     // global scratch above SVD_SMEM_K
+  double* A = base;                  // k x kk column-major (column k is zero padding)
   double* Vm = A + k * kk;           // kk x kk column-major
   double* sv = Vm + kk * kk;         // kk
   double* red = sv + kk;             // 32
   __shared__ int s_flag, s_rot, s_rank;
-  __shared__ int order[128];
+  __shared__ int order_s[128];
+  int* order = big ? reinterpret_cast<int*>(red + 32) : order_s;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   const double eps = eps_ptr ? *eps_ptr : 0.0;
@@ -193,20 +196,27 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
 
 }  // namespace
 
+size_t svd_scratch_doubles(int k) {
+  if (k <= SVD_SMEM_K) return 0;
+  const size_t kk = size_t(k + (k & 1));
+  return size_t(k) * kk + kk * kk + kk + 32 + kk;   // + order (ints stored in doubles)
+}
+
 int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, double* G1, double* G2,
-                     double* sigma, int64_t* rank_out, cudaStream_t s) {
-  if (k < 1 || k > TSQR_KMAX) {
-    set_error("svd_trunc: k out of range");
+                     double* sigma, int64_t* rank_out, cudaStream_t s, double* big) {
+  if (k < 1 || (k > SVD_SMEM_K && big == nullptr)) {
+    set_error("svd_trunc: k out of range or missing scratch");
     return TT_EUNSUPPORTED;
   }
   const int kk = k + (k & 1);
-  const size_t smem = (size_t(k) * kk + size_t(kk) * kk + kk + 32) * sizeof(double);
+  const size_t smem = (k > SVD_SMEM_K) ? 0 : (size_t(k) * kk + size_t(kk) * kk + kk + 32) * sizeof(double);
   static bool attr_done = false;
   if (!attr_done) {
     TTR_CHECK_CUDA(cudaFuncSetAttribute(svd_trunc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_done = true;
   }
-  svd_trunc_kernel<<<1, SVD_THREADS, smem, s>>>(k, R, eps_ptr, rcap, G1, G2, sigma, rank_out);
+  svd_trunc_kernel<<<1, SVD_THREADS, smem, s>>>(k, R, eps_ptr, rcap, G1, G2, sigma, rank_out,
+                                                k > SVD_SMEM_K ? big : nullptr);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
   return TT_OK;

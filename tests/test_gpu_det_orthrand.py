@@ -1,0 +1,84 @@
+"""Parity of the CUDA deterministic rounding (Algorithms 1 + 2 on the formed
+sum) and of Orthogonalize-then-Randomize (Algorithm 4) with the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests._gpu import to_dev, to_host, const_ranks
+
+import paper_2110_04393_gb300 as tt
+
+pytestmark = pytest.mark.gpu
+FP64_TOL = 1e-10
+
+
+def rel_diff(Xg, Xo):
+    return O.diff_norm(Xg, Xo) / O.norm(Xo)
+
+
+@pytest.mark.parametrize("case", ["small_tol", "fixed_rank", "wide_ends", "big_k"])
+def test_det_parity(case):
+    if case == "small_tol":
+        dims, rs, tol, mr = [7, 9, 8, 6, 7], [3, 4, 2], 1e-3, 0
+    elif case == "fixed_rank":
+        dims, rs, tol, mr = [10, 12, 11, 10], [4, 5], 0.0, 3
+    elif case == "wide_ends":        # S_1 = 12 > I_1 = 5 and I_N R'_N < S_{N-1}: both folds
+        dims, rs, tol, mr = [5, 8, 9, 4], [4, 5, 3], 1e-6, 0
+    else:                            # formed rank 120 > 96: Cholesky QR with global scratch
+        dims, rs, tol, mr = [60, 40, 40, 60], [30, 30, 30, 30], 1e-2, 0
+    N = len(dims)
+    Ys = [synth.gaussian_tt(synth.rng_for(80, j), dims, const_ranks(N, r)) for j, r in enumerate(rs)]
+    coeffs = list(synth.rng_for(81).standard_normal(len(Ys)))
+    Xg = to_host(tt.tt_round_det([to_dev(Y) for Y in Ys], tol=tol, max_rank=mr, coeffs=coeffs))
+    Ysum = O.block_sum(Ys, coeffs)
+    Xo = O.tt_round_det(Ysum, tol, max_rank=mr if mr > 0 else None)
+    assert O.ranks_of(Xg) == O.ranks_of(Xo)
+    assert rel_diff(Xg, Xo) <= FP64_TOL
+    if tol > 0:
+        assert O.diff_norm(Xg, Ysum) <= tol * O.norm(Ysum) * (1 + 1e-8)
+
+
+def test_det_structured_truncates_to_true_rank():
+    Ys = synth.workload_sum_structured(4, K=6, N=6, I=12, R=3, m=2, p=1, delta=1e-9)
+    Xg = to_host(tt.tt_round_det([to_dev(Y) for Y in Ys], tol=1e-6))
+    Xo = O.tt_round_det(O.block_sum(Ys), 1e-6)
+    assert O.ranks_of(Xg) == O.ranks_of(Xo)
+    assert max(O.ranks_of(Xg)) <= 6
+    assert rel_diff(Xg, Xo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("case", ["single", "sum"])
+def test_orthrand_parity(case):
+    if case == "single":
+        dims = [12, 15, 13, 14]
+        Ys = [synth.gaussian_tt(synth.rng_for(90), dims, [1, 8, 10, 8, 1])]
+        ell = [1, 5, 6, 5, 1]
+    else:
+        dims = [9, 10, 11, 10, 9]
+        Ys = [synth.gaussian_tt(synth.rng_for(91, j), dims, const_ranks(5, r)) for j, r in enumerate([3, 4, 2])]
+        ell = [1, 6, 7, 7, 6, 1]
+    N = len(dims)
+    rp = tt.tt_orthrand_omega_ranks(dims, [[1] + [c.shape[2] for c in Y] for Y in Ys])
+    Ysum = O.block_sum(Ys)
+    assert rp == O.ranks_of(O.orthogonalize_rl(Ysum))
+    rng = synth.rng_for(92)
+    Om = [None] + [synth.gaussian_matrix(rng, rp[n], ell[n]) for n in range(1, N)]
+    Xg = to_host(tt.tt_round_orthrand([to_dev(Y) for Y in Ys], ell,
+                                      omega=[to_dev([o])[0] for o in Om[1:]]))
+    Xo = O.round_orthrand(Ysum, Om)
+    assert rel_diff(Xg, Xo) <= FP64_TOL
+
+
+def test_rand_vs_det_same_accuracy_order_on_low_rank_sum():
+    """X + X (exact rank R): randomized rounding with l > R and deterministic
+    rounding both recover 2X to round-off."""
+    dims = [14] * 7
+    Y = synth.gaussian_tt(synth.rng_for(93), dims, const_ranks(7, 4))
+    Yd = to_dev(Y)
+    Xd = to_host(tt.tt_round_det([Yd, Yd], tol=1e-10))
+    Xr = to_host(tt.tt_round_sum_rand([Yd, Yd], const_ranks(7, 7), seed=3, tol=1e-10))
+    ref = synth.scale_tt(Y, 2.0)
+    assert O.ranks_of(Xd) == const_ranks(7, 4) and O.ranks_of(Xr) == const_ranks(7, 4)
+    assert O.diff_norm(Xd, ref) <= 1e-12 * O.norm(ref)
+    assert O.diff_norm(Xr, ref) <= 1e-12 * O.norm(ref)

@@ -45,9 +45,9 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert rc == 1 and "ranks" in lib.tt_last_error().decode()
     rc = lib.tt_round_sum_rand(0, 1, dims, bad_ranks, None, None, ells, None, 0, 0.0, 0, None, None, None, 0, None)
     assert rc == 1
-    big = i64([1, 200, 200, 1])
+    big = i64([1, 2000, 2000, 1])
     ranks = i64([1, 3, 3, 1])
-    sz = lib.tt_round_sum_rand_workspace(3, 1, i64([1000, 1000, 1000]), ranks, big, 0.0, 0)
+    sz = lib.tt_round_sum_rand_workspace(3, 1, i64([5000, 5000, 5000]), ranks, big, 0.0, 0)
     assert sz == 0 and "maximum" in lib.tt_last_error().decode()
     sz = lib.tt_round_sum_rand_workspace(3, 1, dims, ranks, ells, 0.0, 0)
     assert sz > 0

@@ -320,3 +320,14 @@ def test_hilbert_tt_randomized_matches_deterministic():
 
 def test_clamp_ranks():
     assert O.clamp_ranks([2, 3, 100, 2], [1, 50, 50, 50, 1]) == [1, 2, 6, 2, 1]
+
+
+def test_qr_pos_is_the_unique_positive_diagonal_qr():
+    """For full column rank, R of the positive-diagonal thin QR is the
+    transposed Cholesky factor of A^T A (uniqueness of that factorization)."""
+    from oracle.rounding import qr_pos
+    A = synth.rng_for(120).standard_normal((40, 7))
+    Q, R = qr_pos(A)
+    assert np.all(np.diag(R) > 0)
+    np.testing.assert_allclose(R, np.linalg.cholesky(A.T @ A).T, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(Q @ R, A, atol=1e-13)
