@@ -101,7 +101,7 @@ int tt_sketch_gaussian(int32_t N, const int64_t* dims, const int64_t* ells, uint
  *                 compactly as (r_{n-1}, I_n, r_n)
  *   out_ranks     host, N+1, receives r_0..r_N
  * Errors: TT_EINVAL (bad sizes/ranks/pointers), TT_EUNSUPPORTED (a target rank
- * above 96 or other limits of this build), TT_ENOMEM, TT_ECUDA.
+ * above 1024), TT_ENOMEM, TT_ECUDA.
  */
 int tt_round_sum_rand(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
                       const double* const* cores, const double* coeffs, const int64_t* ells,
@@ -165,6 +165,32 @@ size_t tt_round_orthrand_workspace(int32_t N, int32_t K, const int64_t* dims, co
                                    const int64_t* ells);
 /* R'_0..R'_N: ranks of the formed sum after Algorithm 1 (the row counts of Omega_n). */
 int tt_orthrand_omega_ranks(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, int64_t* rp);
+
+/*
+ * tt_round_twosided -- Algorithm 6 (Two-Sided-Randomization, generalized
+ * Nystrom, Section 3.3) for a sum of K TT-tensors without forming the block
+ * cores: left-to-right contractions with a Gaussian TT L of ranks l_n,
+ * right-to-left contractions (Algorithm 3) with a Gaussian TT R of ranks
+ * rho_n > l_n, per bond the SVD of W^L_n W^R_n and the factors
+ * L_n = W^R_n V S^{+1/2}, R_n = S^{+1/2} U^T W^L_n, then
+ * X_n = R_{n-1} x_1 Y_n x_3 L_n summed over the summands.
+ *   rhos         host, N+1 right sketch ranks, or NULL for ceil(1.5 l_n)
+ *                (Section 4.1); clamped like ells; must stay >= l_n
+ *   sketch_left  host array of N device pointers (l_{n-1} x I_n x l_n) or NULL
+ *   sketch_right host array of N device pointers (rho_{n-1} x I_n x rho_n) or NULL
+ *                (NULL: drawn on the device as tt_sketch_gaussian does, the left
+ *                one from seed and the right one from seed + 1)
+ *   out          host array of N device pointers, core n holds l_{n-1} I_n l_n
+ * The result is not orthogonal (Section 3.3). Errors: TT_EINVAL, TT_ENOMEM,
+ * TT_ECUDA.
+ */
+int tt_round_twosided(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+                      const double* coeffs, const int64_t* ells, const int64_t* rhos,
+                      const double* const* sketch_left, const double* const* sketch_right, uint64_t seed,
+                      double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
+                      void* stream);
+size_t tt_round_twosided_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                                   const int64_t* ells, const int64_t* rhos);
 
 /*
  * tt_round_sum_rand_noalloc -- tt_round_sum_rand for callers that cannot

@@ -213,6 +213,36 @@ def tt_round_orthrand(summands, ells, *, omega=None, seed=0, coeffs=None, worksp
     return out
 
 
+def tt_round_twosided(summands, ells, *, rhos=None, sketch_left=None, sketch_right=None, seed=0, coeffs=None,
+                      workspace=None, stream=None):
+    """Algorithm 6 (Two-Sided-Randomization) of a sum without forming it."""
+    import math
+    N, K, dims, ranks, flat = _sum_args(summands)
+    device = summands[0][0].device
+    ell = clamp_ranks(dims, ells)
+    rr = clamp_ranks(dims, rhos if rhos is not None else [int(math.ceil(1.5 * x)) for x in ell])
+    L = nat.lib()
+    dims_a, ranks_a, ell_a, rho_a = _i64(dims), _i64(ranks), _i64(ell), _i64(rr)
+    for sk, rk, name in ((sketch_left, ell, "sketch_left"), (sketch_right, rr, "sketch_right")):
+        if sk is not None:
+            for n, c in enumerate(sk):
+                _check_core(c, f"{name} core {n}")
+                if tuple(c.shape) != (rk[n], dims[n], rk[n + 1]):
+                    raise ValueError(f"{name} core {n} has shape {tuple(c.shape)}")
+    out = [torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float64, device=device) for n in range(N)]
+    nb = L.tt_round_twosided_workspace(N, K, dims_a, ranks_a, ell_a, rho_a)
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    co = (ctypes.c_double * K)(*[float(c) for c in coeffs]) if coeffs is not None else None
+    out_ranks = (ctypes.c_int64 * (N + 1))()
+    _check(L.tt_round_twosided(N, K, dims_a, ranks_a, _ptrs(flat), co, ell_a, rho_a,
+                               _ptrs(sketch_left) if sketch_left is not None else None,
+                               _ptrs(sketch_right) if sketch_right is not None else None,
+                               ctypes.c_uint64(int(seed)), _ptrs(out), out_ranks, wp, wb, _stream(stream, device)))
+    return out
+
+
 def tt_round_rand(Y, ells, **kw):
     """Algorithm 5 (single TT, Randomize-then-Orthogonalize): tt_round_sum_rand with K = 1."""
     if kw.get("coeffs") is not None:

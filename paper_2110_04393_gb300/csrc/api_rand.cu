@@ -20,6 +20,7 @@
 
 #include "plan.cuh"
 #include "qr.cuh"
+#include "problem.cuh"
 
 namespace ttr {
 
@@ -107,23 +108,17 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
   return rc;
 }
 
-// ---------------------------------------------------------------------------
-// Validation of a TT-sum problem.
-struct SumProblem {
-  int N = 0, K = 0;
-  std::vector<int64_t> I;      // [N]
-  std::vector<int64_t> R;      // [K*(N+1)]
-  std::vector<int64_t> S;      // [N+1] sum of summand ranks per bond
-  std::vector<int64_t> off;    // [K*(N+1)] prefix of summand ranks per bond
-  std::vector<int64_t> ell;    // [N+1] clamped sketch ranks
-  std::vector<const double*> cores;
-  std::vector<double> coeffs;
-  int64_t r(int j, int n) const { return R[size_t(j) * (N + 1) + n]; }
-  int64_t o(int j, int n) const { return off[size_t(j) * (N + 1) + n]; }
-  const double* core(int j, int n) const { return cores[size_t(j) * N + (n - 1)]; }   // n is 1-based
-};
+std::vector<int64_t> clamp_rank_vector(const std::vector<int64_t>& I, const int64_t* r) {
+  const int N = int(I.size());
+  std::vector<int64_t> ell(r, r + N + 1);
+  ell[0] = 1;
+  ell[N] = 1;
+  for (int n = 1; n < N; ++n) ell[n] = std::min(std::max<int64_t>(ell[n], 1), ell[n - 1] * I[n - 1]);
+  for (int n = N - 1; n >= 1; --n) ell[n] = std::min(ell[n], ell[n + 1] * I[n]);
+  return ell;
+}
 
-static int validate_sum(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+int validate_sum(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
                         const double* coeffs, const int64_t* ells, bool need_cores, SumProblem* P) {
   if (N < 1 || K < 1 || !dims || !ranks || !ells || (need_cores && !cores)) {
     set_error("invalid arguments: need N >= 1, K >= 1 and non-null dims/ranks/ells/cores");

@@ -1,0 +1,229 @@
+// Two-Sided-Randomization (Algorithm 6, Section 3.3, generalized Nystrom) for a
+// sum of K TT-tensors, without forming the block cores.
+//
+// Block form: the sketches of the formed sum are the summands' sketches side by
+// side (W^L_n = [W^{L,(1)}_n ... W^{L,(K)}_n], l_n x S_n) and stacked
+// (W^R_n = [W^{R,(1)}_n; ...], S_n x rho_n), as in the derivation of Section 3.4.
+//   left-to-right: W^{L,(j)}_1 = c_j V(L_1)^T V(Y^(j)_1);
+//                  T = W^{L,(j)}_{n-1} H(Y^(j)_n), W^{L,(j)}_n = V(L_n)^T V(T);
+//   right-to-left: Algorithm 3 with the rho sketch (as in the sum rounding);
+//   per bond:      A_n = W^L_n W^R_n (l_n x rho_n) = V_R S (Q U_R)^T from the thin QR
+//                  A_n^T = Q R and the SVD R = U_R S V_R^T; then
+//                  L_n = W^R_n (Q U_R) S^{+1/2}  (S_n x l_n),
+//                  R_n = S^{+1/2} V_R^T W^L_n     (l_n x S_n), S^+ dropping
+//                  s_i <= max(l, rho) 2^-52 s_1;
+//   distribution:  X_n(:, i, :) = sum_j R^(j)_{n-1} Y^(j)_n(:, i, :) L^(j)_n with
+//                  R_0 = the coefficients and L_N = ones.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "problem.cuh"
+#include "prof.cuh"
+#include "qr.cuh"
+
+namespace ttr {
+
+namespace {
+
+// M[:, c] *= (s_c > thr) ? s_c^p : 0 for c < cols, thr = tol_rel * s_0 (sigma sorted descending).
+__global__ void colscale_kernel(double* M, int64_t rows, int64_t cols, int64_t ld, const double* sig, double p,
+                                double tol_rel) {
+  const double thr = tol_rel * sig[0];
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < rows * cols;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / cols, c = e % cols;
+    const double s = sig[c];
+    M[r * ld + c] *= (s > thr) ? pow(s, p) : 0.0;
+  }
+}
+
+int colscale_launch(double* M, int64_t rows, int64_t cols, int64_t ld, const double* sig, double p, double tol_rel,
+                    cudaStream_t s) {
+  const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows * cols, 256), 2048)));
+  colscale_kernel<<<g, 256, 0, s>>>(M, rows, cols, ld, sig, p, tol_rel);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const double* const* skL,
+                   const double* const* skR, uint64_t seed, double* const* out, Arena& ar, Schedule& sc) {
+  const int N = P.N, K = P.K;
+  const auto& S = P.S;
+  const auto& ell = P.ell;
+  auto In = [&](int n) { return P.I[n - 1]; };
+
+  std::vector<double*> WL(N + 1, nullptr), WR(N + 1, nullptr), Lf(N + 1, nullptr), Rf(N + 1, nullptr);
+  for (int n = 1; n < N; ++n) WL[n] = ar.take<double>(ell[n] * S[n]);
+  for (int n = 1; n <= N; ++n) WR[n] = ar.take<double>(S[n] * rho[n]);
+  for (int n = 1; n <= N; ++n) Lf[n] = ar.take<double>(S[n] * ell[n]);
+  for (int n = 0; n < N; ++n) Rf[n] = ar.take<double>(ell[n] * S[n]);
+  int64_t tmax = 1, zmax = 1, kmax = 1, amax = 1;
+  for (int n = 2; n < N; ++n) tmax = std::max(tmax, ell[n - 1] * In(n) * S[n]);
+  for (int n = 1; n <= N; ++n) zmax = std::max(zmax, S[n - 1] * In(n) * std::max(rho[n], ell[n]));
+  for (int n = 1; n < N; ++n) {
+    kmax = std::max(kmax, ell[n]);
+    amax = std::max(amax, ell[n] * rho[n]);
+  }
+  double* T = ar.take<double>(tmax);
+  double* Z = ar.take<double>(zmax);
+  double* Am = ar.take<double>(amax);
+  double* Qt = ar.take<double>(amax);
+  double* Rb = ar.take<double>(kmax * kmax);
+  double* G1 = ar.take<double>(kmax * kmax);
+  double* G2 = ar.take<double>(kmax * kmax);
+  double* sig = ar.take<double>(kmax);
+  double* sbig = ar.take<double>(std::max<size_t>(svd_scratch_doubles(int(kmax)), 1));
+  int64_t* rdummy = ar.take<int64_t>(1);
+  std::vector<std::pair<int64_t, int>> shapes;
+  for (int n = 1; n < N; ++n) shapes.push_back({rho[n], int(ell[n])});
+  const QrPool pool = qr_pool_reserve(ar, shapes);
+  std::vector<const double*> L(N + 1, nullptr), Rs(N + 1, nullptr);
+  for (int n = 1; n <= N; ++n) {
+    if (skL) {
+      L[n] = skL[n - 1];
+    } else {
+      double* d = ar.take<double>(ell[n - 1] * In(n) * ell[n]);
+      L[n] = d;
+      const int64_t a = ell[n - 1], b = In(n), c = ell[n];
+      sc.add([=](cudaStream_t s) -> int { return sketch_launch(d, a, b, c, n - 1, seed, s); });
+    }
+    if (skR) {
+      Rs[n] = skR[n - 1];
+    } else {
+      double* d = ar.take<double>(rho[n - 1] * In(n) * rho[n]);
+      Rs[n] = d;
+      const int64_t a = rho[n - 1], b = In(n), c = rho[n];
+      sc.add([=](cudaStream_t s) -> int { return sketch_launch(d, a, b, c, n - 1, seed + 1, s); });
+    }
+  }
+  sc.add([=](cudaStream_t s) -> int {
+    TTR_TRY(fill_launch(WR[N], S[N] * rho[N], 1.0, s));
+    return fill_launch(Lf[N], S[N] * ell[N], 1.0, s);
+  });
+  sc.upload(Rf[0], P.coeffs);
+
+  // ---- left-to-right partial contractions with L
+  for (int n = 1; n < N; ++n) {
+    std::vector<GemmDesc> ga, gb;
+    for (int j = 0; j < K; ++j) {
+      const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
+      double* Wo = WL[n] ? WL[n] + P.o(j, n) : nullptr;
+      if (n == 1) {
+        ga.push_back(gdesc(L[1], 1, ell[1], P.core(j, 1), r1, 1, Wo, S[1], 1, ell[1], r1, In(1), P.coeffs[j]));
+      } else {
+        double* Tj = T ? T + ell[n - 1] * In(n) * P.o(j, n) : nullptr;
+        const double* Wi = WL[n - 1] ? WL[n - 1] + P.o(j, n - 1) : nullptr;
+        ga.push_back(gdesc(Wi, S[n - 1], 1, P.core(j, n), In(n) * r1, 1, Tj, In(n) * r1, 1, ell[n - 1], In(n) * r1,
+                           r0));
+        gb.push_back(gdesc(L[n], 1, ell[n], Tj, r1, 1, Wo, S[n], 1, ell[n], r1, ell[n - 1] * In(n)));
+      }
+    }
+    sc.gemm(ga);
+    sc.gemm(gb);
+  }
+  // ---- right-to-left partial contractions with R (Algorithm 3 for every summand)
+  for (int n = N; n >= 2; --n) {
+    std::vector<GemmDesc> ga, gb;
+    for (int j = 0; j < K; ++j) {
+      const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
+      double* Zj = Z ? Z + P.o(j, n - 1) * In(n) * rho[n] : nullptr;
+      const double* Wj = WR[n] ? WR[n] + P.o(j, n) * rho[n] : nullptr;
+      ga.push_back(gdesc(P.core(j, n), r1, 1, Wj, rho[n], 1, Zj, rho[n], 1, r0 * In(n), rho[n], r1));
+      double* Wo = WR[n - 1] ? WR[n - 1] + P.o(j, n - 1) * rho[n - 1] : nullptr;
+      gb.push_back(gdesc(Zj, In(n) * rho[n], 1, Rs[n], 1, In(n) * rho[n], Wo, rho[n - 1], 1, r0, rho[n - 1],
+                         In(n) * rho[n]));
+    }
+    sc.gemm(ga);
+    sc.gemm(gb);
+  }
+  // ---- per bond: SVD of W^L_n W^R_n and the factors L_n, R_n
+  const double eps52 = std::ldexp(1.0, -52);
+  for (int n = 1; n < N; ++n) {
+    const int64_t l = ell[n], r = rho[n];
+    sc.gemm({gdesc(WL[n], S[n], 1, WR[n], r, 1, Am, r, 1, l, r, S[n])});
+    // thin QR of A^T (r x l, a strided view of A)
+    qr_plan(sc, qr_view(pool, r, int(l)), Am, 1, r, Qt, l, 1, Rb);
+    sc.add([=](cudaStream_t s) -> int {
+      return svd_trunc_launch(int(l), Rb, nullptr, int(l), G1, G2, sig, rdummy, s, sbig);
+    });
+    const double tol_rel = double(std::max(l, r)) * eps52;
+    // P1 = Q U_R S^{+1/2} into Am (r x l)
+    sc.gemm({gdesc(Qt, l, 1, G1, l, 1, Am, l, 1, r, l, l)});
+    sc.add([=](cudaStream_t s) -> int {
+      TTR_TRY(colscale_launch(Am, r, l, l, sig, -0.5, tol_rel, s));
+      return colscale_launch(G2, l, l, l, sig, -1.5, tol_rel, s);    // V_R S^{+1/2} = G2 S^{-3/2}
+    });
+    sc.gemm({gdesc(WR[n], r, 1, Am, l, 1, Lf[n], l, 1, S[n], l, r)});         // L_n = W^R_n P1
+    sc.gemm({gdesc(G2, 1, l, WL[n], S[n], 1, Rf[n], S[n], 1, l, S[n], l)});  // R_n = P2^T W^L_n
+  }
+  // ---- distribution of the factors into the cores
+  for (int n = 1; n <= N; ++n) {
+    std::vector<GemmDesc> ga;
+    for (int j = 0; j < K; ++j) {
+      const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
+      double* Zj = Z ? Z + P.o(j, n - 1) * In(n) * ell[n] : nullptr;
+      const double* Lj = Lf[n] ? Lf[n] + P.o(j, n) * ell[n] : nullptr;
+      ga.push_back(gdesc(P.core(j, n), r1, 1, Lj, ell[n], 1, Zj, ell[n], 1, r0 * In(n), ell[n], r1));
+    }
+    sc.gemm(ga);
+    sc.gemm({gdesc(Rf[n - 1], S[n - 1], 1, Z, In(n) * ell[n], 1, out[n - 1], In(n) * ell[n], 1, ell[n - 1],
+                   In(n) * ell[n], S[n - 1])});
+  }
+  return TT_OK;
+}
+
+}  // namespace
+}  // namespace ttr
+
+using namespace ttr;
+
+extern "C" {
+
+static int twosided_common(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                           const double* const* cores, const double* coeffs, const int64_t* ells,
+                           const int64_t* rhos, const double* const* skL, const double* const* skR, uint64_t seed,
+                           double* const* out, int64_t* out_ranks, void* workspace, size_t ws_bytes, void* stream,
+                           size_t* size_only) {
+  SumProblem P;
+  TTR_TRY(validate_sum(N, K, dims, ranks, cores, coeffs, ells, size_only == nullptr, &P));
+  if (N < 2) { set_error("two-sided rounding needs N >= 2"); return TT_EINVAL; }
+  std::vector<int64_t> rr(N + 1);
+  for (int n = 0; n <= N; ++n) rr[n] = rhos ? rhos[n] : int64_t(std::ceil(1.5 * double(P.ell[n])));
+  std::vector<int64_t> rho = clamp_rank_vector(P.I, rr.data());
+  for (int n = 1; n < N; ++n)
+    if (rho[n] < P.ell[n]) {
+      set_error("two-sided rounding needs rho_n >= l_n (after clamping)");
+      return TT_EINVAL;
+    }
+  if (!size_only && (!out || !out_ranks)) { set_error("null outputs"); return TT_EINVAL; }
+  std::vector<double*> outv(N, nullptr);
+  if (out) outv.assign(out, out + N);
+  BuildFn build = [&](Arena& ar, Schedule& sc) { return build_twosided(P, rho, skL, skR, seed, outv.data(), ar, sc); };
+  if (size_only) return plan_workspace_bytes(build, size_only);
+  TTR_TRY(plan_execute(build, workspace, ws_bytes, static_cast<cudaStream_t>(stream)));
+  for (int n = 0; n <= N; ++n) out_ranks[n] = P.ell[n];
+  return TT_OK;
+}
+
+int tt_round_twosided(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+                      const double* coeffs, const int64_t* ells, const int64_t* rhos,
+                      const double* const* sketch_left, const double* const* sketch_right, uint64_t seed,
+                      double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
+                      void* stream) {
+  return twosided_common(N, K, dims, ranks, cores, coeffs, ells, rhos, sketch_left, sketch_right, seed, out,
+                         out_ranks, workspace, workspace_bytes, stream, nullptr);
+}
+
+size_t tt_round_twosided_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                                   const int64_t* ells, const int64_t* rhos) {
+  size_t b = 0;
+  if (twosided_common(N, K, dims, ranks, nullptr, nullptr, ells, rhos, nullptr, nullptr, 0, nullptr, nullptr,
+                      nullptr, 0, nullptr, &b) != TT_OK)
+    return 0;
+  return b;
+}
+
+}  // extern "C"

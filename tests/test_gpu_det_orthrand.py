@@ -82,3 +82,32 @@ def test_rand_vs_det_same_accuracy_order_on_low_rank_sum():
     assert O.ranks_of(Xd) == const_ranks(7, 4) and O.ranks_of(Xr) == const_ranks(7, 4)
     assert O.diff_norm(Xd, ref) <= 1e-12 * O.norm(ref)
     assert O.diff_norm(Xr, ref) <= 1e-12 * O.norm(ref)
+
+
+@pytest.mark.parametrize("case", ["single", "sum"])
+def test_twosided_parity(case):
+    """Algorithm 6 in block-sum form == Algorithm 6 on the formed sum (oracle)."""
+    if case == "single":
+        dims = [11, 13, 12, 10]
+        Ys = [synth.gaussian_tt(synth.rng_for(100), dims, [1, 7, 9, 6, 1])]
+        ell = [1, 4, 5, 4, 1]
+    else:
+        dims = [9, 10, 12, 10, 9]
+        Ys = [synth.gaussian_tt(synth.rng_for(101, j), dims, const_ranks(5, r)) for j, r in enumerate([3, 4, 2, 3])]
+        ell = [1, 5, 6, 6, 5, 1]
+    N = len(dims)
+    rho = O.clamp_ranks(dims, [int(np.ceil(1.5 * x)) for x in ell])
+    Lsk = synth.gaussian_tt(synth.rng_for(102), dims, ell)
+    Rsk = synth.gaussian_tt(synth.rng_for(103), dims, rho)
+    coeffs = list(synth.rng_for(104).standard_normal(len(Ys)))
+    Xg = to_host(tt.tt_round_twosided([to_dev(Y) for Y in Ys], ell, rhos=rho, sketch_left=to_dev(Lsk),
+                                      sketch_right=to_dev(Rsk), coeffs=coeffs))
+    Xo = O.round_sum_twosided(Ys, Lsk, Rsk, coeffs)
+    assert rel_diff(Xg, Xo) <= FP64_TOL
+
+
+def test_twosided_exact_recovery_seeded():
+    dims = [8] * 6
+    Y = synth.gaussian_tt(synth.rng_for(105), dims, const_ranks(6, 3))
+    Xg = to_host(tt.tt_round_twosided([to_dev(Y)], const_ranks(6, 4), seed=9))
+    assert O.diff_norm(Xg, Y) <= 1e-10 * O.norm(Y)
