@@ -108,6 +108,20 @@ int tt_round_sum_rand(int32_t N, int32_t K, const int64_t* dims, const int64_t* 
                       const double* const* sketch, uint64_t seed, double tol, int32_t precision,
                       double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
                       void* stream);
+/*
+ * TT_PREC_MIXED (no counterpart in the paper): the three long contractions of
+ * every bond -- H(Z) H(Omega_n)^T of Algorithm 3, the sketch V(X_n) W_n and the
+ * projection Q^T V(X_n) -- run on the tcgen05 tensor cores as split float64
+ * products: each operand is cut, per 64-wide K-chunk and per row / column, into
+ * s bf16 digits of 7 bits whose pairwise products are exact in the fp32 tensor
+ * accumulator, and the kept pairs (p + q <= s + 1) are recombined exactly in
+ * integers. The relative error per product is about 2^(10 - 7 s). QR, the
+ * small SVD and the remaining short contractions stay float64.
+ * tt_mixed_digits(tol, N) returns the s used: products accurate to 1e-3 tol / N
+ * (the errors of the N-step contraction recursion compound and enter the kept
+ * subspace of redundant sums), 1e-7 / N in fixed-rank mode; 1 <= s <= 8.
+ */
+int tt_mixed_digits(double tol, int32_t N);
 size_t tt_round_sum_rand_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
                                    const int64_t* ells, double tol, int32_t precision);
 
@@ -218,6 +232,44 @@ int tt_round_sum_rand_noalloc(int32_t N, int32_t K, const int64_t* dims, const i
                               const double* const* cores, const double* coeffs, const int64_t* ells,
                               const double* const* sketch, uint64_t seed, double tol, int32_t precision,
                               double* const* out, int64_t* out_ranks, void* stream);
+
+/*
+ * tt_gemm_emulated_f64 -- the matrix product that the mixed-precision path
+ * runs for its contractions (no counterpart in the paper, which works in FP64
+ * throughout), exported so that it can be checked on its own:
+ *   C = alpha * A B + beta * C,
+ * A an M x K view (element (r, k) at A[r*a_rs + k*a_cs]), B a K x N view
+ * (B[k*b_rs + c*b_cs]), C an M x N view (C[r*c_rs + c*c_cs]); all float64
+ * device arrays; C must not overlap A or B.
+ * Each operand is cut into `digits` (1..8) balanced 7-bit digits relative to
+ * the largest exponent of its row (A) or column (B); digit products run on the
+ * tensor cores (bf16 in, fp32 accumulation, exact), their sums are kept exactly
+ * in integers and rounded once to float64. The error of C[r][c] is below
+ * K 2^{4 - 7 digits} max_k |A[r][k]| max_k |B[k][c]| plus the final rounding
+ * (typically about sqrt(K) times smaller), so digits = 8 is FP64-class.
+ * Bit-wise deterministic. Subnormal inputs count as zero; a row of A or a
+ * column of B holding Inf or NaN gives NaN outputs (as does a tensor-core wait
+ * that gave up).
+ * workspace: NULL (allocated on the stream) or a device block of at least the
+ * size reported in the error message of a call with workspace NULL and
+ * ws_bytes != 0 (that call returns TT_EINVAL and does nothing else).
+ * Errors: TT_EINVAL (sizes, digits, K > 2^20, null operands), TT_ENOMEM,
+ * TT_ECUDA. M == 0 or N == 0 does nothing.
+ */
+int tt_gemm_emulated_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t a_rs,
+                         int64_t a_cs, const double* B, int64_t b_rs, int64_t b_cs, double beta, double* C,
+                         int64_t c_rs, int64_t c_cs, int32_t digits, void* workspace, size_t ws_bytes,
+                         void* stream);
+
+/*
+ * tt_selftest_tcgen05_bf16 -- diagnostic of the tensor-core unit (no
+ * counterpart in the paper): D = A B^T with A (M x K) and B (N x K) bf16
+ * row-major device arrays, D (M x N) fp32 row-major, accumulated in tensor
+ * memory by tcgen05.mma. N in [16, 256] and a multiple of 16, K a multiple of
+ * 64. *err (device int, zeroed by the caller) becomes 1 if a bounded wait gave up.
+ */
+int tt_selftest_tcgen05_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* D, int* err,
+                             void* stream);
 
 /*
  * Measurement hooks (no counterpart in the paper; used by the benchmark).

@@ -23,6 +23,7 @@ SIGNATURES = {
     "tt_round_sum_rand": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl, c_i32,
                                   P_vp, P_i64, c_vp, c_size, c_vp]),
     "tt_round_sum_rand_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64, c_dbl, c_i32]),
+    "tt_mixed_digits": (c_i32, [c_dbl, c_i32]),
     "tt_round_rand": (c_i32, [c_i32, P_i64, P_i64, P_vp, P_i64, P_vp, c_u64, c_dbl, c_i32, P_vp, P_i64, c_vp,
                               c_size, c_vp]),
     "tt_round_det": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, c_dbl, c_i64, P_vp, P_i64, c_vp, c_size,
@@ -39,6 +40,9 @@ SIGNATURES = {
     "tt_noalloc_scratch_bytes": (c_size, []),
     "tt_round_sum_rand_noalloc": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl,
                                           c_i32, P_vp, P_i64, c_vp]),
+    "tt_gemm_emulated_f64": (c_i32, [c_i64, c_i64, c_i64, c_dbl, c_vp, c_i64, c_i64, c_vp, c_i64, c_i64, c_dbl,
+                                     c_vp, c_i64, c_i64, c_i32, c_vp, c_size, c_vp]),
+    "tt_selftest_tcgen05_bf16": (c_i32, [c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tt_prof_enable": (c_i32, [c_i32]),
     "tt_prof_reset": (c_i32, []),
     "tt_prof_read": (c_i32, [P_dbl, P_dbl, P_i64, P_i64]),

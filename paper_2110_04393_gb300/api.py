@@ -59,6 +59,26 @@ def tt_sketch_gaussian(dims, ells, seed, *, device=None, stream=None):
     return out
 
 
+def tt_gemm_emulated_f64(A, B, C=None, *, alpha=1.0, beta=0.0, digits=8, stream=None):
+    """C = alpha A B + beta C by the emulated FP64 tensor-core product (2-D float64
+    CUDA tensors with any strides; C is created when None)."""
+    for t, nm in ((A, "A"), (B, "B")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2):
+            raise ValueError(f"{nm}: expected a 2-D float64 CUDA tensor")
+    M, K = A.shape
+    K2, N = B.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float64, device=A.device)
+    elif not (C.is_cuda and C.dtype == torch.float64 and tuple(C.shape) == (M, N)):
+        raise ValueError("C: expected a float64 CUDA tensor of shape (M, N)")
+    _check(nat.lib().tt_gemm_emulated_f64(M, N, K, float(alpha), A.data_ptr(), A.stride(0), A.stride(1),
+                                          B.data_ptr(), B.stride(0), B.stride(1), float(beta), C.data_ptr(),
+                                          C.stride(0), C.stride(1), int(digits), None, 0, _stream(stream, A.device)))
+    return C
+
+
 def clamp_ranks(dims, ells):
     N = len(dims)
     ell = [1] + [int(x) for x in ells[1:N]] + [1]

@@ -27,14 +27,24 @@ namespace ttr {
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 
+// Arena regions plus the schedule's own regions (partials, descriptors,
+// counters, copy descriptors, error flag, emulated-GEMM accumulators and
+// exponent tags), each 256-byte aligned.
+static size_t schedule_bytes(const Arena& a, const Schedule& s) {
+  return a.used + align256(size_t(std::max<int64_t>(s.pbuf_need, 1)) * sizeof(double)) +
+         align256(std::max<size_t>(s.descs.size(), 1) * sizeof(GemmDesc)) +
+         align256(size_t(std::max<int64_t>(s.cnt_need, 1)) * sizeof(int)) +
+         align256(std::max<size_t>(s.copies.size(), 1) * sizeof(Copy3)) + align256(sizeof(int)) +
+         align256(size_t(std::max<int64_t>(s.acc_need, 1)) * sizeof(long long)) +
+         align256(size_t(std::max<int64_t>(s.ex_need, 1)) * sizeof(int)) + 512;
+}
+
 int plan_workspace_bytes(const BuildFn& build, size_t* bytes) {
   Arena a;
   a.sizing = true;
   Schedule s;
   TTR_TRY(build(a, s));
-  *bytes = a.used + align256(size_t(s.pbuf_need) * sizeof(double)) + align256(s.descs.size() * sizeof(GemmDesc)) +
-           align256(size_t(std::max<int64_t>(s.cnt_need, 1)) * sizeof(int)) +
-           align256(std::max<size_t>(s.copies.size(), 1) * sizeof(Copy3)) + 256;
+  *bytes = schedule_bytes(a, s);
   return TT_OK;
 }
 
@@ -45,10 +55,7 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
     Arena a;
     a.sizing = true;
     TTR_TRY(build(a, probe));
-    need = a.used + align256(size_t(probe.pbuf_need) * sizeof(double)) +
-           align256(probe.descs.size() * sizeof(GemmDesc)) +
-           align256(size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int)) +
-           align256(std::max<size_t>(probe.copies.size(), 1) * sizeof(Copy3)) + 256;
+    need = schedule_bytes(a, probe);
   }
   void* ws = workspace;
   bool owned = false;
@@ -78,9 +85,16 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
   GemmDesc* d_descs = a.take<GemmDesc>(std::max<size_t>(probe.descs.size(), 1));
   s.cnt = a.take<int>(size_t(std::max<int64_t>(probe.cnt_need, 1)));
   s.d_copies = a.take<Copy3>(std::max<size_t>(probe.copies.size(), 1));
+  s.tc_err = a.take<int>(1);
+  s.acc = a.take<long long>(size_t(std::max<int64_t>(probe.acc_need, 1)));
+  s.ex = a.take<int>(size_t(std::max<int64_t>(probe.ex_need, 1)));
   int rc = TT_OK;
   {
     cudaError_t e = cudaMemsetAsync(s.cnt, 0, size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.tc_err, 0, sizeof(int), st);
+    if (e == cudaSuccess && probe.acc_need > 0)
+      e = cudaMemsetAsync(s.acc, 0, size_t(probe.acc_need) * sizeof(long long), st);
+    if (e == cudaSuccess && probe.ex_need > 0) e = cudaMemsetAsync(s.ex, 0, size_t(probe.ex_need) * sizeof(int), st);
     if (e != cudaSuccess) {
       set_error(std::string("counter reset: ") + cudaGetErrorString(e));
       rc = TT_ECUDA;
@@ -251,8 +265,23 @@ static int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int
 }
 
 // ---------------------------------------------------------------------------
-static int build_sum_rand_fp64(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol,
-                               double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev) {
+// bf16 digits of the Algorithm 3 contractions in the mixed path (14 bits).
+constexpr int kSketchDigits = 2;
+
+static int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol,
+                          int digits, double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev) {
+  // digits == 0: every contraction in FP64. Else every contraction runs on the
+  // tensor cores (emulated GEMM): the core updates and projections with
+  // `digits` bf16 digits, the partial contractions of Algorithm 3 with
+  // kSketchDigits (their rounding errors only change the sketch: the sketched
+  // core stays in the range of the unfolding).
+  const int dw = digits > 0 ? kSketchDigits : 0;
+  auto big = [&](std::vector<GemmDesc> g) {
+    if (digits > 0) sc.gemm_tc(std::move(g), digits); else sc.gemm(std::move(g));
+  };
+  auto sketchy = [&](std::vector<GemmDesc> g) {
+    if (dw > 0) sc.gemm_tc(std::move(g), dw); else sc.gemm(std::move(g));
+  };
   const int N = P.N, K = P.K;
   const auto& I = P.I;
   const auto& S = P.S;
@@ -296,20 +325,20 @@ static int build_sum_rand_fp64(const SumProblem& P, const double* const* sketch_
     }
   }
 
-  // ---- right-to-left partial contractions (Algorithm 3 for every summand)
+  // ---- right-to-left partial contractions (Algorithm 3 for every summand).
+  // The sketch is shared, so the second product of all summands is one GEMM of
+  // the stacked H(Z^(j)) (S_{n-1} x I_n l_n) with H(Omega_n)^T.
   for (int n = N; n >= 2; --n) {
-    std::vector<GemmDesc> ga, gb;
+    std::vector<GemmDesc> ga;
     for (int j = 0; j < K; ++j) {
       const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
       double* Zj = Z ? Z + P.o(j, n - 1) * In(n) * ell[n] : nullptr;
       const double* Wj = W[n] ? W[n] + P.o(j, n) * ell[n] : nullptr;
       ga.push_back(gdesc(P.core(j, n), r1, 1, Wj, ell[n], 1, Zj, ell[n], 1, r0 * In(n), ell[n], r1));
-      double* Wo = W[n - 1] ? W[n - 1] + P.o(j, n - 1) * ell[n - 1] : nullptr;
-      gb.push_back(gdesc(Zj, In(n) * ell[n], 1, sk[n], 1, In(n) * ell[n], Wo, ell[n - 1], 1, r0, ell[n - 1],
-                         In(n) * ell[n]));
     }
-    sc.gemm(ga);
-    sc.gemm(gb);
+    sketchy(ga);
+    sketchy({gdesc(Z, In(n) * ell[n], 1, sk[n], 1, In(n) * ell[n], W[n - 1], ell[n - 1], 1, S[n - 1], ell[n - 1],
+                   In(n) * ell[n])});
   }
 
   // ---- left-to-right sweep
@@ -319,22 +348,31 @@ static int build_sum_rand_fp64(const SumProblem& P, const double* const* sketch_
     std::vector<GemmDesc> gc;
     for (int j = 0; j < K; ++j) {
       const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
-      GemmDesc d = gdesc(Mp ? Mp + P.o(j, n - 1) : nullptr, S[n - 1], 1, P.core(j, n), In(n) * r1, 1,
-                         X ? X + P.o(j, n) : nullptr, In(n) * S[n], 1, ell[n - 1], r1, r0);
-      d.batch = int32_t(In(n));
-      d.a_bs = 0;
-      d.b_bs = r1;
-      d.c_bs = S[n];
-      gc.push_back(d);
+      if (digits > 0) {
+        // one product per summand: rows (i, c) of H(Y^(j)_n)^T, columns a
+        GemmDesc d = gdesc(P.core(j, n), 1, In(n) * r1, Mp ? Mp + P.o(j, n - 1) : nullptr, 1, S[n - 1],
+                           X ? X + P.o(j, n) : nullptr, S[n], In(n) * S[n], In(n) * r1, ell[n - 1], r0);
+        d.c_rdiv = r1;
+        d.c_rs2 = 1;
+        gc.push_back(d);
+      } else {
+        GemmDesc d = gdesc(Mp ? Mp + P.o(j, n - 1) : nullptr, S[n - 1], 1, P.core(j, n), In(n) * r1, 1,
+                           X ? X + P.o(j, n) : nullptr, In(n) * S[n], 1, ell[n - 1], r1, r0);
+        d.batch = int32_t(In(n));
+        d.a_bs = 0;
+        d.b_bs = r1;
+        d.c_bs = S[n];
+        gc.push_back(d);
+      }
     }
-    sc.gemm(gc);
+    if (digits > 0) sc.gemm_tc(gc, digits); else sc.gemm(gc);
     double* dst = (n < N) ? Ys : out[N - 1];
-    sc.gemm({gdesc(X, S[n], 1, W[n], ell[n], 1, dst, ell[n], 1, ell[n - 1] * In(n), ell[n], S[n])});
+    big({gdesc(X, S[n], 1, W[n], ell[n], 1, dst, ell[n], 1, ell[n - 1] * In(n), ell[n], S[n])});
     if (n == N) break;
     const int64_t m = ell[n - 1] * In(n), k = ell[n];
     double* Qn = out[n - 1];
     qr_plan(sc, qr_view(pool, m, int(k)), Ys, k, 1, Qn, k, 1, nullptr);
-    sc.gemm({gdesc(Qn, 1, k, X, S[n], 1, Mn, S[n], 1, k, S[n], m)});
+    big({gdesc(Qn, 1, k, X, S[n], 1, Mn, S[n], 1, k, S[n], m)});
   }
 
   if (tol > 0.0) TTR_TRY(plan_truncation(ar, sc, N, I, ell, tol, out, rk_dev));
@@ -367,6 +405,17 @@ int tt_sketch_gaussian(int32_t N, const int64_t* dims, const int64_t* ells, uint
   return TT_OK;
 }
 
+// Digits of the mixed path. Errors of the Algorithm 3 contractions compound over
+// the N-step recursion and enter the kept subspace directly when the sum is
+// redundant, so the per-product target is 1e-3 tol / N (1e-7 / N in fixed-rank
+// mode, an FP32-class target).
+static int mixed_digits(double tol, int N) {
+  const double base = tol > 0.0 ? 1e-3 * tol : 1e-7;
+  return tc_digits_for_accuracy(base / double(std::max(N, 1)));
+}
+
+int tt_mixed_digits(double tol, int32_t N) { return mixed_digits(tol, N); }
+
 __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, const int64_t* dims,
                                                          const int64_t* ranks,
                            const double* const* cores, const double* coeffs, const int64_t* ells,
@@ -379,10 +428,7 @@ __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, 
     set_error("unknown precision mode");
     return TT_EINVAL;
   }
-  if (precision == TT_PREC_MIXED) {
-    set_error("mixed precision is not available in this build");
-    return TT_EUNSUPPORTED;
-  }
+  const int digits = (precision == TT_PREC_MIXED) ? mixed_digits(tol, N) : 0;
   if (size_only == nullptr) {
     if (!out || !out_ranks) { set_error("null output arrays"); return TT_EINVAL; }
     for (int n = 0; n < N; ++n)
@@ -395,7 +441,7 @@ __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, 
   std::vector<double*> out_v(N, nullptr);
   if (out) out_v.assign(out, out + N);
   BuildFn build = [&](Arena& ar, Schedule& sc) {
-    return build_sum_rand_fp64(P, sketch, seed, tol, out_v.data(), ar, sc, &rk_dev);
+    return build_sum_rand(P, sketch, seed, tol, digits, out_v.data(), ar, sc, &rk_dev);
   };
   if (size_only) return plan_workspace_bytes(build, size_only);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -126,18 +126,17 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
   }
   // ---- right-to-left partial contractions with R (Algorithm 3 for every summand)
   for (int n = N; n >= 2; --n) {
-    std::vector<GemmDesc> ga, gb;
+    std::vector<GemmDesc> ga;
     for (int j = 0; j < K; ++j) {
       const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
       double* Zj = Z ? Z + P.o(j, n - 1) * In(n) * rho[n] : nullptr;
       const double* Wj = WR[n] ? WR[n] + P.o(j, n) * rho[n] : nullptr;
       ga.push_back(gdesc(P.core(j, n), r1, 1, Wj, rho[n], 1, Zj, rho[n], 1, r0 * In(n), rho[n], r1));
-      double* Wo = WR[n - 1] ? WR[n - 1] + P.o(j, n - 1) * rho[n - 1] : nullptr;
-      gb.push_back(gdesc(Zj, In(n) * rho[n], 1, Rs[n], 1, In(n) * rho[n], Wo, rho[n - 1], 1, r0, rho[n - 1],
-                         In(n) * rho[n]));
     }
     sc.gemm(ga);
-    sc.gemm(gb);
+    // shared sketch: one GEMM of the stacked H(Z^(j)) with H(R_n)^T
+    sc.gemm({gdesc(Z, In(n) * rho[n], 1, Rs[n], 1, In(n) * rho[n], WR[n - 1], rho[n - 1], 1, S[n - 1], rho[n - 1],
+                   In(n) * rho[n])});
   }
   // ---- per bond: SVD of W^L_n W^R_n and the factors L_n, R_n
   const double eps52 = std::ldexp(1.0, -52);

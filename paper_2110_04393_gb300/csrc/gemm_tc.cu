@@ -1,0 +1,556 @@
+// Emulated FP64 GEMM on the tcgen05 tensor cores (the contractions of the mixed
+// path): C = alpha * A B + beta * C with float64 inputs and outputs, computed
+// from bf16 "digit" slices whose products and sums are exact.
+//
+// Splitting (no FP64 arithmetic anywhere). A first launch reduces, for every
+// row r of A and column c of B, the largest float64 exponent over the whole K
+// range (integer atomics on the exponent bits). With E_r = that exponent + 2
+// every a_rk satisfies |a_rk| < 2^{E_r - 1}, so F = |a_rk| 2^{63 - E_r} is an
+// integer below 2^62 (taken from the mantissa bits with shifts). Adding the
+// constant 64 in every 7-bit digit position (plus half a unit of the last
+// kept digit) and reading the digits back gives balanced digits
+// d_1 .. d_s in [-64, 64] with F = sum_p d_p 2^{63 - 7p} + rounding error
+// below 2^{62 - 7s}: a_rk ~ 2^{E_r} sum_p d_p 2^{-7p}. Every digit is exact in
+// bf16. Columns of B are split the same way (E_c).
+//
+// Products. Digit pairs with p + q <= s + 1 are kept; pairs of one level
+// L = p + q accumulate (tcgen05.mma, fp32 in TMEM) into the TMEM region of that
+// level. Per 64-wide K-chunk a level sum is an integer of magnitude at most
+// 8 * 64 * 64^2 = 2^21, so fp32 holds it exactly. After each chunk the levels
+// are read back, converted to integers exactly (magic-number addition) and
+// added into two int64 accumulators per output, H = sum_{L<=5} D_L 2^{7(5-L)}
+// and Lo = sum_{L>=6} D_L 2^{7(9-L)}. Then
+//   C_rc ~ 2^{E_r + E_c - 63} (H 2^28 + Lo),
+// a 128-bit integer times a power of two, which is rounded to float64 once
+// with integer operations. Split-K partials are combined by integer atomics in
+// L2, so the result does not depend on the order of arrival (bit-wise
+// deterministic). The error per product is about 2^{1 - 7s} relative to
+// max_k |a_rk| max_k |b_kc|; s = 8 keeps 56 bits (FP64 class). Rows of A or
+// columns of B that hold Inf or NaN give NaN outputs; subnormals count as zero.
+//
+// Tile: 128 rows (one TMEM lane each) x 32 columns, 256 threads (8 warps).
+// Operand chunks of 128 x 64 and 32 x 64 digits per plane are staged in shared
+// memory in the canonical K-major layout of tc_sm103.cuh.
+#include <algorithm>
+#include <cmath>
+
+#include <string>
+
+#include "plan.cuh"
+#include "prof.cuh"
+#include "tc_sm103.cuh"
+
+namespace ttr {
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 32, TC_BK = 64, TC_THREADS = 256;
+constexpr int EX_OUT = 32, EX_IN = 256;   // exponent pass block: 32 rows x 256 K
+constexpr uint32_t kPolls = 1u << 24;
+constexpr int kExBias = 4096;             // stored exponent = e + kExBias, low 16 bits
+constexpr int kExNonFinite = 0x7FFF;      // stored for Inf / NaN (above every finite code)
+constexpr int kNonFinite = 1 << 20;       // decoded exponent of a row / column holding Inf or NaN
+
+__device__ __forceinline__ int dexp(double x) {        // biased exponent, or -1 for zero / subnormal
+  const uint64_t b = uint64_t(__double_as_longlong(x));
+  const int e = int((b >> 52) & 0x7FF);
+  return e == 0 ? -1 : (e == 0x7FF ? kExNonFinite : e - 1023 + kExBias);
+}
+
+// Balanced digits of x relative to 2^E (|x| < 2^{E-1}); d[p] for p < s.
+__device__ __forceinline__ void digits(double x, int E, int s, int* d) {
+  const uint64_t b = uint64_t(__double_as_longlong(x));
+  const int e = int((b >> 52) & 0x7FF);
+  uint64_t F = 0;
+  if (e != 0) {
+    const uint64_t mant = (b & ((uint64_t(1) << 52) - 1)) | (uint64_t(1) << 52);
+    const int sh = (e - 1023) - E + 11;        // F = mant 2^{sh}, sh <= 9
+    if (sh >= 0) F = mant << sh;
+    else if (sh > -64) F = mant >> (-sh);
+  }
+  // + 64 in every digit position and half a unit of digit s
+  uint64_t C = uint64_t(1) << (62 - 7 * s);
+#pragma unroll
+  for (int p = 1; p <= 8; ++p)
+    if (p <= s) C += uint64_t(64) << (63 - 7 * p);
+  const uint64_t G = F + C;
+  const int sg = -int(b >> 63);               // 0 or -1
+#pragma unroll
+  for (int p = 1; p <= 8; ++p) {
+    if (p > s) break;
+    const int v = (p == 1) ? int(G >> 56) - 64 : int((G >> (63 - 7 * p)) & 127u) - 64;
+    d[p - 1] = (v ^ sg) - sg;                 // apply the sign
+  }
+}
+
+// exact float value of a small integer (|v| < 2^22) without a conversion unit
+__device__ __forceinline__ float int_to_float_small(int v) {
+  return __fsub_rn(__int_as_float(0x4B400000 + v), 12582912.0f);
+}
+// exact integer value of an fp32 holding an integer with |x| < 2^22
+__device__ __forceinline__ int float_to_int_small(float x) {
+  return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000;
+}
+
+// Rounds T 2^{e2} to float64, T = H 2^28 + Lo (128-bit), with integer operations.
+__device__ __forceinline__ double round_i128(long long H, long long Lo, int e2) {
+  const uint64_t tl = uint64_t(H) << 28;
+  const long long th = H >> 36;
+  uint64_t ml = tl + uint64_t(Lo);
+  const long long nh = th + (Lo >> 63) + (ml < tl ? 1 : 0);
+  const bool neg = nh < 0;
+  uint64_t mh = uint64_t(nh);
+  if (neg) {
+    ml = ~ml + 1;
+    mh = ~mh + (ml == 0 ? 1 : 0);
+  }
+  if (mh == 0 && ml == 0) return 0.0;
+  const int lz = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);
+  if (lz >= 64) {
+    mh = ml << (lz - 64);
+    ml = 0;
+  } else if (lz > 0) {
+    mh = (mh << lz) | (ml >> (64 - lz));
+    ml <<= lz;
+  }
+  int msb = 127 - lz;
+  uint64_t mant = mh >> 11;
+  const uint64_t rest = mh & 0x7FF;
+  const bool rnd = (rest >> 10) & 1;
+  const bool sticky = (rest & 0x3FF) != 0 || ml != 0;
+  if (rnd && (sticky || (mant & 1))) {
+    ++mant;
+    if (mant >> 53) { mant >>= 1; ++msb; }
+  }
+  const int E = msb + e2;
+  const uint64_t sgn = uint64_t(neg) << 63;
+  const uint64_t frac = mant & ((uint64_t(1) << 52) - 1);
+  if (E > 1023) return __longlong_as_double((long long)(sgn | (uint64_t(0x7FF) << 52)));
+  if (E < -1022) {
+    // below the normal range (not expected in practice): one correctly rounded multiply
+    if (E < -1022 - 600) return __longlong_as_double((long long)sgn);
+    const double x = __longlong_as_double((long long)(sgn | (uint64_t(E + 600 + 1023) << 52) | frac));
+    return x * 0x1p-600;
+  }
+  return __longlong_as_double((long long)(sgn | (uint64_t(E + 1023) << 52) | frac));
+}
+
+struct TcArgs {
+  const GemmDesc* descs;
+  int ndesc;
+  int s;          // digits per operand
+  int epoch;      // tag of this launch's exponents (tags of older launches lose the max)
+};
+
+__device__ __forceinline__ int find_desc(const GemmDesc* descs, int ndesc, int64_t t, bool exp_pass) {
+  int lo = 0, hi = ndesc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int64_t b = exp_pass ? descs[mid].exp_begin : descs[mid].tile_begin;
+    if (b <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---- pass 1: largest exponent per row of A and per column of B over all of K
+__global__ void __launch_bounds__(256) tc_exponent_kernel(TcArgs args) {
+  const int64_t t = blockIdx.x;
+  const GemmDesc& d = args.descs[find_desc(args.descs, args.ndesc, t, true)];
+  int64_t local = t - d.exp_begin;
+  // block counts as in gemm_tc_prepare (at least one block per side)
+  const int64_t kb = max((d.K + EX_IN - 1) / EX_IN, int64_t(1));
+  const int64_t ob_a = max((d.M + EX_OUT - 1) / EX_OUT, int64_t(1));
+  const int64_t ob_b = max((d.N + EX_OUT - 1) / EX_OUT, int64_t(1));
+  const int64_t per_batch = (ob_a + ob_b) * kb;
+  const int64_t bidx = local / per_batch;
+  local -= bidx * per_batch;
+  const bool sideA = local < ob_a * kb;
+  if (!sideA) local -= ob_a * kb;
+  const int64_t ob = local / kb, ib = local % kb;
+  const double* base;
+  int64_t outer, os, is;
+  int* out;
+  if (sideA) {
+    base = d.A + bidx * d.a_bs; outer = d.M; os = d.a_rs; is = d.a_cs; out = d.ex_row + bidx * d.M;
+  } else {
+    base = d.B + bidx * d.b_bs; outer = d.N; os = d.b_cs; is = d.b_rs; out = d.ex_col + bidx * d.N;
+  }
+  const int64_t o0 = ob * EX_OUT, k0 = ib * EX_IN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tag = args.epoch << 16;
+  if (is == 1) {
+    // inner index contiguous: a warp reads along K for four rows
+    for (int j = 0; j < 4; ++j) {
+      const int64_t o = o0 + warp + 8 * j;
+      int m = -1;
+      if (o < outer) {
+        const double* p = base + o * os;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int64_t k = k0 + lane + 32 * u;
+          if (k < d.K) m = max(m, dexp(__ldg(p + k)));
+        }
+      }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+      if (lane == 0 && m >= 0) atomicMax(out + o, tag | m);
+    }
+  } else {
+    // outer index contiguous (or neither): lanes along the rows, warps along K
+    __shared__ int red[8][32];
+    const int64_t o = o0 + lane;
+    int m = -1;
+    if (o < outer) {
+      const double* p = base + o * os;
+      for (int u = 0; u < EX_IN / 8; ++u) {
+        const int64_t k = k0 + warp + 8 * u;
+        if (k < d.K) m = max(m, dexp(__ldg(p + k * is)));
+      }
+    }
+    red[warp][lane] = m;
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int w = 1; w < 8; ++w) m = max(m, red[w][lane]);
+      if (o < outer && m >= 0) atomicMax(out + o, tag | m);
+    }
+  }
+}
+
+__device__ __forceinline__ int decode_exp(int v, int epoch) {
+  if ((v >> 16) != epoch) return 0;                     // no nonzero entry
+  if ((v & 0xFFFF) == kExNonFinite) return kNonFinite;
+  return (v & 0xFFFF) - kExBias + 2;                    // E with |x| < 2^{E-1}
+}
+
+// ---- pass 2: digit products on the tensor cores
+__global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int s = args.s;
+  uint8_t* As = smem;                                  // s x (128 x 64 bf16) = s x 16 KB
+  uint8_t* Bs = smem + s * 16384;                      // s x (32 x 64 bf16)  = s x 4 KB
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail, s_last;
+  __shared__ int Er[TC_BM], Ec[TC_BN];
+
+  const int64_t t = blockIdx.x;
+  const GemmDesc d = args.descs[find_desc(args.descs, args.ndesc, t, false)];
+  int64_t local = t - d.tile_begin;
+  const int ntile = int(local % d.nt); local /= d.nt;
+  const int mtile = int(local % d.mt); local /= d.mt;
+  const int ks = int(local % d.ksplit);
+  const int64_t bidx = local / d.ksplit;
+  const double* A = d.A + bidx * d.a_bs;
+  const double* B = d.B + bidx * d.b_bs;
+  const int64_t m0 = int64_t(mtile) * TC_BM, n0 = int64_t(ntile) * TC_BN;
+  const int64_t k_begin = int64_t(ks) * d.kchunk;
+  const int64_t k_end = min(d.K, k_begin + d.kchunk);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ncols = tc::tmem_cols_for(s * TC_BN);
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, ncols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    s_fail = 0;
+  }
+  for (int i = tid; i < TC_BM + TC_BN; i += TC_THREADS) {
+    if (i < TC_BM) {
+      const int64_t r = m0 + i;
+      Er[i] = r < d.M ? decode_exp(__ldcg(d.ex_row + bidx * d.M + r), args.epoch) : 0;
+    } else {
+      const int64_t c = n0 + (i - TC_BM);
+      Ec[i - TC_BM] = c < d.N ? decode_exp(__ldcg(d.ex_col + bidx * d.N + c), args.epoch) : 0;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base;
+  const uint32_t idesc = tc::idesc_bf16_f32(TC_BM, TC_BN);
+
+  // staging roles: a warp fills core matrices (8 rows x 8 k); lane -> row lane/4, k pair lane%4
+  const int cr = lane >> 2, ck = (lane & 3) * 2;
+  // epilogue roles: TMEM lane quadrant q (warp % 4), column half ch
+  const int q = warp & 3, ch = warp >> 2;
+  long long accH[16], accL[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) { accH[j] = 0; accL[j] = 0; }
+  uint32_t phase = 0;
+
+  for (int64_t kc = k_begin; kc < k_end; kc += TC_BK) {
+    // ---- A: 128 x 64 -> s planes; warp w: row groups 2w, 2w+1, all 8 k groups
+#pragma unroll 2
+    for (int cm = 0; cm < 16; ++cm) {
+      const int rg = 2 * warp + (cm >> 3), kg = cm & 7;
+      const int rr = rg * 8 + cr, kk = kg * 8 + ck;
+      const int64_t r = m0 + rr, k = kc + kk;
+      double x0 = 0.0, x1 = 0.0;
+      if (r < d.M) {
+        const double* p = A + r * d.a_rs + k * d.a_cs;
+        if (k < k_end) x0 = __ldg(p);
+        if (k + 1 < k_end) x1 = __ldg(p + d.a_cs);
+      }
+      int d0[8], d1[8];
+      digits(x0, Er[rr], s, d0);
+      digits(x1, Er[rr], s, d1);
+      const uint32_t off = tc::canon_off(rr, kk);
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        if (p >= s) break;
+        const __nv_bfloat162 h = __floats2bfloat162_rn(int_to_float_small(d0[p]), int_to_float_small(d1[p]));
+        *reinterpret_cast<__nv_bfloat162*>(As + p * 16384 + off) = h;
+      }
+    }
+    // ---- B: 32 x 64 (columns x k) -> s planes; warp w: column group w/2, k groups 4(w%2)..+3
+#pragma unroll
+    for (int cm = 0; cm < 4; ++cm) {
+      const int cg = warp >> 1, kg = (warp & 1) * 4 + cm;
+      const int cc = cg * 8 + cr, kk = kg * 8 + ck;
+      const int64_t c = n0 + cc, k = kc + kk;
+      double x0 = 0.0, x1 = 0.0;
+      if (c < d.N) {
+        const double* p = B + k * d.b_rs + c * d.b_cs;
+        if (k < k_end) x0 = __ldg(p);
+        if (k + 1 < k_end) x1 = __ldg(p + d.b_rs);
+      }
+      int d0[8], d1[8];
+      digits(x0, Ec[cc], s, d0);
+      digits(x1, Ec[cc], s, d1);
+      const uint32_t off = tc::canon_off(cc, kk);
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        if (p >= s) break;
+        const __nv_bfloat162 h = __floats2bfloat162_rn(int_to_float_small(d0[p]), int_to_float_small(d1[p]));
+        *reinterpret_cast<__nv_bfloat162*>(Bs + p * 4096 + off) = h;
+      }
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    // ---- one thread issues every kept digit-pair product of this chunk
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
+      for (int L = 2; L <= s + 1; ++L) {
+        bool first = true;
+        for (int p = 1; p <= s; ++p) {
+          const int qq = L - p;
+          if (qq < 1 || qq > s) continue;
+          for (int st = 0; st < 4; ++st) {
+            tc::mma_bf16(taddr + uint32_t((L - 2) * TC_BN),
+                         tc::smem_desc(a0 + (p - 1) * 16384 + 256 * st, 128, 1024),
+                         tc::smem_desc(b0 + (qq - 1) * 4096 + 256 * st, 128, 1024), idesc, first ? 0u : 1u);
+            first = false;
+          }
+        }
+      }
+      tc::mma_commit(&bar);
+    }
+    if (!tc::mbar_wait_bounded(&bar, phase, kPolls)) atomicExch(&s_fail, 1);
+    phase ^= 1;
+    tc::fence_after_sync();
+    __syncthreads();
+    if (s_fail) break;
+    // ---- exact level sums -> int64 accumulators (TMEM lane q*32+lane, columns ch*16..+16)
+#pragma unroll
+    for (int L = 2; L <= 9; ++L) {
+      if (L > s + 1) break;
+      float v[16];
+      tc::tmem_ld16(taddr + (uint32_t(q * 32) << 16) + uint32_t((L - 2) * TC_BN + ch * 16), v);
+      if (L <= 5) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) accH[j] += (long long)float_to_int_small(v[j]) << (7 * (5 - L));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) accL[j] += (long long)float_to_int_small(v[j]) << (7 * (9 - L));
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+
+  const int rr = q * 32 + lane;
+  const int64_t row = m0 + rr;
+  const int64_t c0 = n0 + ch * 16;
+  const int64_t row_off = d.c_rdiv > 0 ? (row / d.c_rdiv) * d.c_rs + (row % d.c_rdiv) * d.c_rs2 : row * d.c_rs;
+  auto store = [&](int j, double v) {
+    double* cp = d.C + bidx * d.c_bs + row_off + (c0 + j) * d.c_cs;
+    if (Er[rr] == kNonFinite || Ec[ch * 16 + j] == kNonFinite) v = __longlong_as_double(0x7FF8000000000000LL);
+    if (d.alpha != 1.0) v *= d.alpha;
+    if (d.beta != 0.0) v = fma(d.beta, *cp, v);
+    *cp = v;
+  };
+  if (!s_fail) {
+    if (d.ksplit == 1) {
+      if (row < d.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < d.N) store(j, round_i128(accH[j], accL[j], Er[rr] + Ec[ch * 16 + j] - 63));
+      }
+    } else {
+      // integer partials meet in L2; the last CTA of the tile rounds and writes C
+      const int64_t tile_id = (bidx * d.mt + mtile) * d.nt + ntile;
+      unsigned long long* acc = reinterpret_cast<unsigned long long*>(d.acc) + tile_id * (2 * TC_BM * TC_BN);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int cc = ch * 16 + j;
+        if (accH[j]) atomicAdd(acc + cc * TC_BM + rr, (unsigned long long)accH[j]);
+        if (accL[j]) atomicAdd(acc + TC_BM * TC_BN + cc * TC_BM + rr, (unsigned long long)accL[j]);
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        const int old = atomicAdd(d.cnt + tile_id, 1);
+        s_last = (old == d.ksplit - 1);
+        if (s_last) d.cnt[tile_id] = 0;
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+#pragma unroll 4
+        for (int j = 0; j < 16; ++j) {
+          const int cc = ch * 16 + j;
+          unsigned long long* ph = acc + cc * TC_BM + rr;
+          unsigned long long* pl = acc + TC_BM * TC_BN + cc * TC_BM + rr;
+          const long long H = (long long)__ldcg(ph), Lo = (long long)__ldcg(pl);
+          *ph = 0;
+          *pl = 0;
+          if (row < d.M && c0 + j < d.N) store(j, round_i128(H, Lo, Er[rr] + Ec[cc] - 63));
+        }
+      }
+    }
+  } else {
+    // a wait gave up: let the in-flight MMAs drain (bounded) before freeing TMEM,
+    // raise the flag and leave NaN in this CTA's outputs
+    tc::mbar_wait_bounded(&bar, phase ^ 1, kPolls);
+    if (tid == 0) atomicExch(err, 1);
+    if (row < d.M)
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j < d.N)
+          d.C[bidx * d.c_bs + row_off + (c0 + j) * d.c_cs] = __longlong_as_double(0x7FF8000000000000LL);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, ncols);
+}
+
+}  // namespace
+
+int tc_digits_for_accuracy(double rel) {
+  // relative product error ~ 2^{1 - 7 s} times a spread and sqrt(K) factor ~ 2^9
+  int s = 1;
+  while (s < 8 && std::ldexp(1.0, -7 * s + 10) > rel) ++s;
+  return s;
+}
+
+void gemm_tc_prepare(std::vector<GemmDesc>& g, int target_ctas, TcPlan* plan, long long* acc_base, int* ex_base,
+                     int* cbase) {
+  int64_t t = 0, eb = 0, acc = 0, ex = 0, c = 0;
+  int64_t tiles_total = 0;
+  for (auto& d : g) {
+    // keep the long side on the 128-row tile
+    if (d.M < TC_BM && d.N > d.M && d.c_rdiv == 0) {
+      std::swap(d.M, d.N);
+      std::swap(d.A, d.B);
+      const int64_t ars = d.a_rs, acs = d.a_cs, abs_ = d.a_bs;
+      d.a_rs = d.b_cs; d.a_cs = d.b_rs; d.a_bs = d.b_bs;
+      d.b_rs = acs; d.b_cs = ars; d.b_bs = abs_;
+      std::swap(d.c_rs, d.c_cs);
+    }
+    d.mt = int(ceil_div(std::max<int64_t>(d.M, 1), TC_BM));
+    d.nt = int(ceil_div(std::max<int64_t>(d.N, 1), TC_BN));
+    tiles_total += int64_t(d.batch) * d.mt * d.nt;
+  }
+  for (auto& d : g) {
+    const int64_t chunks = std::max<int64_t>(1, ceil_div(std::max<int64_t>(d.K, 1), TC_BK));
+    // split K only while the grid is below one CTA per SM
+    const int64_t want = std::max<int64_t>(1, target_ctas / std::max<int64_t>(tiles_total, 1));
+    const int64_t split = std::min(chunks, want);
+    const int64_t cps = ceil_div(chunks, split);
+    d.kchunk = cps * TC_BK;
+    d.ksplit = int(ceil_div(chunks, cps));
+    const int64_t base = int64_t(d.batch) * d.mt * d.nt;
+    d.tile_begin = t;
+    t += base * d.ksplit;
+    d.exp_begin = eb;
+    const int64_t kb = ceil_div(std::max<int64_t>(d.K, 1), EX_IN);
+    eb += int64_t(d.batch) *
+          (ceil_div(std::max<int64_t>(d.M, 1), EX_OUT) + ceil_div(std::max<int64_t>(d.N, 1), EX_OUT)) * kb;
+    d.ex_row = ex_base ? ex_base + ex : nullptr;
+    ex += int64_t(d.batch) * d.M;
+    d.ex_col = ex_base ? ex_base + ex : nullptr;
+    ex += int64_t(d.batch) * d.N;
+    d.P = nullptr;
+    d.acc = nullptr;
+    d.cnt = nullptr;
+    if (d.ksplit > 1) {
+      d.acc = acc_base ? acc_base + acc : nullptr;
+      acc += base * 2 * TC_BM * TC_BN;
+      d.cnt = cbase ? cbase + c : nullptr;
+      c += base;
+    }
+  }
+  plan->tiles = t;
+  plan->exp_blocks = eb;
+  plan->acc_words = acc;
+  plan->ex_ints = ex;
+  plan->counters = c;
+}
+
+int gemm_tc_launch(const GemmDesc* d_descs, int ndesc, const TcPlan& plan, int s, int epoch, double flops, int* err,
+                   cudaStream_t st) {
+  if (ndesc == 0 || plan.tiles == 0) return TT_OK;
+  if (s < 1 || s > 8 || epoch < 1 || epoch > 32767) {
+    set_error("emulated GEMM: digits must be 1..8 and at most 32767 launches per plan");
+    return TT_EINVAL;
+  }
+  const size_t smem = size_t(s) * (16384 + 4096);
+  static bool attr = false;
+  if (!attr) {
+    TTR_CHECK_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 164 * 1024));
+    attr = true;
+  }
+  TcArgs a{d_descs, ndesc, s, epoch};
+  tc_exponent_kernel<<<unsigned(plan.exp_blocks), 256, 0, st>>>(a);
+  TTR_CHECK_LAUNCH();
+  cudaEvent_t e0;
+  const bool prof = prof_gemm_begin(st, &e0);
+  gemm_tc_kernel<<<unsigned(plan.tiles), TC_THREADS, smem, st>>>(a, err);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(2);
+  if (prof) prof_gemm_end(st, flops);
+  return TT_OK;
+}
+
+}  // namespace ttr
+
+// ---------------------------------------------------------------------------
+using namespace ttr;
+
+extern "C" int tt_gemm_emulated_f64(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t a_rs,
+                                    int64_t a_cs, const double* B, int64_t b_rs, int64_t b_cs, double beta,
+                                    double* C, int64_t c_rs, int64_t c_cs, int32_t digits, void* workspace,
+                                    size_t ws_bytes, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || digits < 1 || digits > 8 || (M > 0 && N > 0 && !C) ||
+      (M > 0 && N > 0 && K > 0 && (!A || !B)) || K > (int64_t(1) << 20)) {
+    set_error("tt_gemm_emulated_f64: need M, N, K >= 0 (K <= 2^20), digits in 1..8 and non-null operands");
+    return TT_EINVAL;
+  }
+  if (M == 0 || N == 0) return TT_OK;
+  GemmDesc d = gdesc(A, a_rs, a_cs, B, b_rs, b_cs, C, c_rs, c_cs, M, N, K, alpha, beta);
+  BuildFn build = [&](Arena&, Schedule& sc) -> int {
+    sc.gemm_tc({d}, digits);
+    return TT_OK;
+  };
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (workspace == nullptr && ws_bytes != 0) {
+    size_t need = 0;
+    TTR_TRY(plan_workspace_bytes(build, &need));
+    set_error("tt_gemm_emulated_f64: workspace needs " + std::to_string(need) + " bytes");
+    return TT_EINVAL;
+  }
+  return plan_execute(build, workspace, ws_bytes, s);
+}

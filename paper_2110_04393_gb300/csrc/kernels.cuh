@@ -26,6 +26,13 @@ struct GemmDesc {
   int64_t kchunk;
   int64_t tile_begin;   // prefix over the group (set by the planner)
   int* cnt;             // split-K arrival counters, one per output tile (self-resetting)
+  // emulated-FP64 tensor-core GEMM only (set by gemm_tc_prepare)
+  int* ex_row;          // per row of A: tagged largest exponent over K
+  int* ex_col;          // per column of B: tagged largest exponent over K
+  long long* acc;       // split-K integer accumulators (zero before use, self-resetting)
+  int64_t exp_begin;    // prefix of the exponent-pass blocks
+  int64_t c_rdiv;       // > 0: row r of C sits at (r / c_rdiv) c_rs + (r % c_rdiv) c_rs2
+  int64_t c_rs2;
 };
 
 constexpr int GEMM_BM = 32, GEMM_BN = 32, GEMM_BK = 16, GEMM_THREADS = 256;
@@ -38,6 +45,22 @@ void gemm_prepare(std::vector<GemmDesc>& g, int64_t* tiles, int64_t* pbuf_double
                   int target_ctas, double* pbase, int* cbase);
 // flops: algorithmic 2*M*N*K*batch summed over the group (for live profiling).
 int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, double flops, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Emulated FP64 GEMM on the tcgen05 tensor cores (same descriptors; see
+// gemm_tc.cu): s = bf16 digits per operand (1..8). One launch group is an
+// exponent pass plus the product pass. The exponent region (ex_ints) must be
+// zero before the first group of a plan; each group of the plan gets its own
+// epoch 1, 2, ... The accumulator region (acc_words) must be zero before the
+// first group and is left zero. *err (device) becomes 1 if a bounded wait gave up.
+struct TcPlan {
+  int64_t tiles = 0, exp_blocks = 0, acc_words = 0, ex_ints = 0, counters = 0;
+};
+int tc_digits_for_accuracy(double rel);
+void gemm_tc_prepare(std::vector<GemmDesc>& g, int target_ctas, TcPlan* plan, long long* acc_base, int* ex_base,
+                     int* cbase);
+int gemm_tc_launch(const GemmDesc* d_descs, int ndesc, const TcPlan& plan, int s, int epoch, double flops, int* err,
+                   cudaStream_t st);
 
 // ----------------------------------------------------------------------------
 // Tall-skinny Householder QR (TSQR) of an m x k matrix A (k <= TSQR_KMAX):

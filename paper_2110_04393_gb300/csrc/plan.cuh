@@ -29,6 +29,30 @@ struct Schedule {
     descs.insert(descs.end(), g.begin(), g.end());
     items.push_back([=](cudaStream_t s, const GemmDesc* d) { return gemm_launch(d + off, n, tiles, flops, s); });
   }
+  int* tc_err = nullptr;                        // device flag of the tensor-core GEMMs
+  int64_t acc_need = 0, ex_need = 0;            // emulated-GEMM accumulators / exponent tags (largest group)
+  long long* acc = nullptr;                     // zeroed once per call, left zero by every group
+  int* ex = nullptr;                            // zeroed once per call, tagged by epoch
+  int tc_epoch = 0;
+  // Group run by the emulated FP64 GEMM on the tensor cores (s digits).
+  void gemm_tc(std::vector<GemmDesc> g, int s) {
+    if (g.empty()) return;
+    double flops = 0.0;
+    for (const auto& d : g) flops += 2.0 * double(d.M) * double(d.N) * double(d.K) * double(d.batch);
+    TcPlan tp;
+    gemm_tc_prepare(g, num_sms(), &tp, acc, ex, cnt);
+    if (tp.acc_words > acc_need) acc_need = tp.acc_words;
+    if (tp.ex_ints > ex_need) ex_need = tp.ex_ints;
+    if (tp.counters > cnt_need) cnt_need = tp.counters;
+    const int epoch = ++tc_epoch;
+    const size_t off = descs.size();
+    const int n = int(g.size());
+    descs.insert(descs.end(), g.begin(), g.end());
+    int** errp = &tc_err;
+    items.push_back([=](cudaStream_t st, const GemmDesc* d) {
+      return gemm_tc_launch(d + off, n, tp, s, epoch, flops, *errp, st);
+    });
+  }
   void add(std::function<int(cudaStream_t)> f) {
     items.push_back([f](cudaStream_t s, const GemmDesc*) { return f(s); });
   }

@@ -75,3 +75,15 @@ def test_cost_model_matches_paper_table():
     assert abs(per_core - paper) <= 1e-9 * paper
     # with s = 1 it is the table's Rand-then-Orth row; Contr is its first part
     assert gold["Contr"] == [0, 2, 2, 0]
+
+
+def test_mixed_digits_policy(lib):
+    """Digits of the split tensor-core products: 2^(10 - 7 s) <= 1e-3 tol / N."""
+    for tol in (1e-2, 1e-5, 1e-8, 1e-12):
+        for N in (4, 50):
+            s = lib.tt_mixed_digits(tol, N)
+            target = 1e-3 * tol / N
+            assert 1 <= s <= 8
+            assert s == 8 or 2.0 ** (10 - 7 * s) <= target
+            assert s == 1 or 2.0 ** (10 - 7 * (s - 1)) > target
+    assert lib.tt_mixed_digits(1e-8, 50) == 8
