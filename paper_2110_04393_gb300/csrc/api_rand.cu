@@ -28,15 +28,16 @@ static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 
 // Arena regions plus the schedule's own regions (partials, descriptors,
-// counters, copy descriptors, error flag, emulated-GEMM accumulators and
-// exponent tags), each 256-byte aligned.
+// counters, copy descriptors, error flag, emulated-GEMM accumulators,
+// exponent tags and digit planes), each 256-byte aligned.
 static size_t schedule_bytes(const Arena& a, const Schedule& s) {
   return a.used + align256(size_t(std::max<int64_t>(s.pbuf_need, 1)) * sizeof(double)) +
          align256(std::max<size_t>(s.descs.size(), 1) * sizeof(GemmDesc)) +
          align256(size_t(std::max<int64_t>(s.cnt_need, 1)) * sizeof(int)) +
          align256(std::max<size_t>(s.copies.size(), 1) * sizeof(Copy3)) + align256(sizeof(int)) +
          align256(size_t(std::max<int64_t>(s.acc_need, 1)) * sizeof(long long)) +
-         align256(size_t(std::max<int64_t>(s.ex_need, 1)) * sizeof(int)) + 512;
+         align256(size_t(std::max<int64_t>(s.ex_need, 1)) * sizeof(int)) +
+         align256(size_t(std::max<int64_t>(s.plane_need, 1))) + 512;
 }
 
 int plan_workspace_bytes(const BuildFn& build, size_t* bytes) {
@@ -88,6 +89,7 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
   s.tc_err = a.take<int>(1);
   s.acc = a.take<long long>(size_t(std::max<int64_t>(probe.acc_need, 1)));
   s.ex = a.take<int>(size_t(std::max<int64_t>(probe.ex_need, 1)));
+  s.planes = a.take<uint8_t>(size_t(std::max<int64_t>(probe.plane_need, 1)));
   int rc = TT_OK;
   {
     cudaError_t e = cudaMemsetAsync(s.cnt, 0, size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int), st);

@@ -3,6 +3,9 @@
 // ill-conditioned matrices", SIAM J. Sci. Comput. 42 (2020)). A chain of
 // passes; pass 0 factors G = A^T A, every later pass multiplies the current
 // block by the previous inverse factor and factors its Gram matrix:
+//   * when only Q is wanted and a later Gram is I + E with ||E||_F <= 1e-8,
+//     the next pass multiplies by I - E/2 and ends the chain (Q^T Q - I is
+//     then O(||E||^2), below the rounding level), saving a factorization;
 //   * a factorization that breaks down is retried with G + s I,
 //     s = 11 (m k + k (k+1)) u ||.||_F^2 (a shifted pass);
 //   * once two consecutive factorizations were unshifted, the next pass writes
@@ -49,62 +52,93 @@ struct CqrPass {
   double* buf[2];           // m x k ping-pong blocks (row-major)
   double* Q;                // final Q
   int64_t q_rs, q_cs;
-  double* Gpart;            // (P + groups) x k x k
+  double* Gpart;            // (P + groups) x k (k + 1) / 2 (packed upper triangles)
   int* counter;             // [0] final arrival, [1 + g] group arrivals
   double* Rinv;             // k x k (upper, row-major)
   double* Racc;             // k x k accumulated R, or null
   double* big;              // 3 k x k global scratch when k > CQ_SMEM_K (else null)
-  int* status;              // [0] failure, [1] unshifted run, [2] done, [3] factorizations so far
+  int* status;              // [0] failure, [1] unshifted run, [2] done, [3] factorizations so far,
+                            // [4] the next pass multiplies by a first-order correction and ends the chain
 };
 
 // In-place right-looking Cholesky of G (k x k row-major, lower part) with
-// X := L^{-1} formed alongside; returns false on a non-positive pivot.
-__device__ bool chol_with_inverse(double* G, double* X, int k, double* s_rd) {
+// X := L^{-1} formed alongside; returns false on a non-positive pivot. FP64
+// issues a dependent operation only every ~65 cycles on GB300 and a reciprocal
+// square root takes ~430, so the 30-odd pivots are the critical path: every
+// step packs all of its trailing updates (the lower triangle of G below the
+// pivot and the rows of X below it) densely over threads 1.., while thread 0
+// only updates the next diagonal entry and takes its reciprocal square root.
+// Two block barriers per step. colj: k doubles of scratch.
+__device__ bool chol_with_inverse(double* G, double* X, double* colj, int k, double* s_rd, int* s_bad) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  __shared__ int s_bad;
-  for (int idx = tid; idx < k * k; idx += nt) X[idx] = ((idx / k) == (idx % k)) ? 1.0 : 0.0;
-  if (tid == 0) s_bad = 0;
+  for (int e = tid; e < k * k; e += nt) X[e] = (e % (k + 1) == 0) ? 1.0 : 0.0;
+  if (tid == 0) {
+    const double d = G[0];
+    const bool bad = !(d > 0.0) || !isfinite(d);
+    *s_bad = bad ? 1 : 0;
+    *s_rd = bad ? 1.0 : rsqrt(d);
+  }
   __syncthreads();
   for (int j = 0; j < k; ++j) {
-    if (tid == 0) {
-      const double d = G[j * k + j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        s_bad = 1;
-        *s_rd = 1.0;
-      } else {
-        const double r = rsqrt(d);
-        G[j * k + j] = d * r;
-        *s_rd = r;
-      }
-    }
-    __syncthreads();
-    if (s_bad) return false;
+    if (*s_bad) return false;
     const double rd = *s_rd;
-    for (int i = j + 1 + tid; i < k; i += nt) G[i * k + j] *= rd;
-    for (int c = tid; c <= j; c += nt) X[j * k + c] *= rd;
-    __syncthreads();
-    const int h = k - j - 1;
-    for (int idx = tid; idx < h * h; idx += nt) {
-      const int i = j + 1 + idx / h, l = j + 1 + idx % h;
-      if (l <= i) G[i * k + l] = fma(-G[i * k + j], G[l * k + j], G[i * k + l]);
+    const int n = k - j - 1;                      // rows / columns below the pivot
+    // column j of L (scaled), the diagonal, and row j of X
+    for (int e = tid; e <= n + j; e += nt) {
+      if (e < n) colj[j + 1 + e] = G[(j + 1 + e) * k + j] * rd;
+      else X[j * k + (e - n)] *= rd;
     }
-    for (int idx = tid; idx < h * (j + 1); idx += nt) {
-      const int i = j + 1 + idx / (j + 1), c = idx % (j + 1);
-      X[i * k + c] = fma(-G[i * k + j], X[j * k + c], X[i * k + c]);
+    if (tid == 0) G[j * k + j] *= rd;
+    __syncthreads();
+    const int ng = n * (n + 1) / 2, nx = n * (j + 1);
+    if (tid == 0) {
+      if (n > 0) {
+        const double d = fma(-colj[j + 1], colj[j + 1], G[(j + 1) * k + j + 1]);
+        G[(j + 1) * k + j + 1] = d;
+        const bool bad = !(d > 0.0) || !isfinite(d);
+        *s_bad = bad ? 1 : 0;
+        *s_rd = bad ? 1.0 : rsqrt(d);
+      }
+    } else {
+      // entry 0 of the packed lower triangle is the next diagonal (thread 0's)
+      for (int e = tid; e < ng + nx; e += nt - 1) {
+        if (e < ng) {
+          int ip = int((sqrtf(8.0f * float(e) + 1.0f) - 1.0f) * 0.5f);
+          while (ip * (ip + 1) / 2 > e) --ip;
+          while ((ip + 1) * (ip + 2) / 2 <= e) ++ip;
+          const int i = j + 1 + ip, l = j + 1 + (e - ip * (ip + 1) / 2);
+          G[i * k + l] = fma(-colj[i], colj[l], G[i * k + l]);
+        } else {
+          const int e2 = e - ng;
+          const int i = j + 1 + e2 / (j + 1), c = e2 % (j + 1);
+          X[i * k + c] = fma(-colj[i], X[j * k + c], X[i * k + c]);
+        }
+      }
+      for (int i = j + tid; i < k; i += nt - 1) G[i * k + j] = colj[i];   // rows j+1.. of column j
     }
     __syncthreads();
   }
   return true;
 }
 
+// Position (i, j), i <= j, of entry p of the row-wise packed upper triangle.
+__device__ __forceinline__ void tri_ij(int p, int k, int* i, int* j) {
+  int r = 0;
+  while (p >= k - r) { p -= k - r; ++r; }
+  *i = r;
+  *j = r + p;
+}
+
 __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   extern __shared__ double sm[];
-  __shared__ int s_last;
+  __shared__ int s_last, s_bad;
   __shared__ double s_rd;
+  __shared__ double s_col[CQ_SMEM_K];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int k = a.k, b = a.b;
   if (__ldcg(a.status + 2)) return;                         // chain already finished
   const int unshifted_run = __ldcg(a.status + 1);
+  const bool first_order = __ldcg(a.status + 4) != 0;
   const bool final_pass = (a.pass > 0) && (unshifted_run >= 2 || a.pass == CQ_MAX_PASSES - 1);
   const double* src = (a.pass <= 1) ? a.A : a.buf[(a.pass - 2) & 1];
   const int64_t s_rs = (a.pass <= 1) ? a.a_rs : k, s_cs = (a.pass <= 1) ? a.a_cs : 1;
@@ -118,39 +152,63 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   double* Rs = T2 + b * k;        // k x k (shared when small)
   const double* Rin = (a.pass == 0) ? nullptr : a.Rinv;
   const int64_t r0 = int64_t(blockIdx.x) * b;
-  for (int idx = tid; idx < b * k; idx += nt) {
-    const int r = idx / k, c = idx % k;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int r = warp; r < b; r += nw) {
     const int64_t gr = r0 + r;
-    T[idx] = (gr < a.m) ? src[gr * s_rs + c * s_cs] : 0.0;
+    for (int c = lane; c < k; c += 32) T[r * k + c] = (gr < a.m) ? src[gr * s_rs + c * s_cs] : 0.0;
   }
   if (Rin && !big)
-    for (int idx = tid; idx < k * k; idx += nt) Rs[idx] = __ldcg(Rin + idx);
+    for (int i = warp; i < k; i += nw)
+      for (int c = lane; c < k; c += 32) Rs[i * k + c] = __ldcg(Rin + i * k + c);
   __syncthreads();
   if (Rin) {
+    // T2 = T R^{-1} (R^{-1} upper): item (row, column pair c1 = cp, c2 = k-1-cp)
+    // so every item costs k + 1 fused multiply-adds
+    // (a first-order correction I - E/2 is a full matrix: all k terms)
     const double* Rr = big ? Rin : Rs;
-    for (int idx = tid; idx < b * k; idx += nt) {
-      const int r = idx / k, c = idx % k;
-      double s = 0.0;
-      for (int j = 0; j <= c; ++j) s = fma(T[r * k + j], big ? __ldcg(Rr + j * k + c) : Rr[j * k + c], s);
-      T2[idx] = s;
+    const int ncp = (k + 1) / 2;
+    for (int it = tid; it < b * ncp; it += nt) {
+      const int r = it / ncp, cp = it - r * ncp;
+      const int c1 = cp, c2 = k - 1 - cp;
+      const int j1 = first_order ? k - 1 : c1, j2 = first_order ? k - 1 : c2;
+      double s1 = 0.0, s2 = 0.0;
+      for (int j = 0; j <= j2; ++j) {
+        const double tj = T[r * k + j];
+        if (j <= j1) s1 = fma(tj, big ? __ldcg(Rr + j * k + c1) : Rr[j * k + c1], s1);
+        s2 = fma(tj, big ? __ldcg(Rr + j * k + c2) : Rr[j * k + c2], s2);
+      }
+      T2[r * k + c1] = s1;
+      T2[r * k + c2] = s2;
     }
     __syncthreads();
     T = T2;
   }
   if (dst)
-    for (int idx = tid; idx < b * k; idx += nt) {
-      const int r = idx / k, c = idx % k;
+    for (int r = warp; r < b; r += nw) {
       const int64_t gr = r0 + r;
-      if (gr < a.m) dst[gr * d_rs + c * d_cs] = T[idx];
+      if (gr < a.m)
+        for (int c = lane; c < k; c += 32) dst[gr * d_rs + c * d_cs] = T[r * k + c];
     }
-  double* Gp = a.Gpart + int64_t(blockIdx.x) * k * k;
-  for (int idx = tid; idx < k * k; idx += nt) {
-    const int i = idx / k, j = idx % k;
-    if (j < i) continue;
-    double s = 0.0;
-    for (int r = 0; r < b; ++r) s = fma(T[r * k + i], T[r * k + j], s);
-    Gp[i * k + j] = s;
-    Gp[j * k + i] = s;
+  if (final_pass && first_order) {
+    // Q = Q1 (I - E/2) with ||E||_F <= 1e-8 has Q^T Q = I + O(||E||^2): no check needed
+    if (tid == 0) atomicExch(a.status + 2, 1);
+    return;
+  }
+  // partial Gram, upper triangle packed row-wise (npair entries)
+  const int npair = k * (k + 1) / 2;
+  double* Gp = a.Gpart + int64_t(blockIdx.x) * npair;
+  for (int p = tid; p < npair; p += 2 * nt) {
+    int i1, j1, i2 = 0, j2 = 0;
+    tri_ij(p, k, &i1, &j1);
+    const bool two = p + nt < npair;
+    if (two) tri_ij(p + nt, k, &i2, &j2);
+    double g1 = 0.0, g2 = 0.0;
+    for (int r = 0; r < b; ++r) {
+      g1 = fma(T[r * k + i1], T[r * k + j1], g1);
+      if (two) g2 = fma(T[r * k + i2], T[r * k + j2], g2);
+    }
+    Gp[p] = g1;
+    if (two) Gp[p + nt] = g2;
   }
   // two-level arrival: the last CTA of each group of CQ_GROUP sums the group's
   // partials (block order) into a group partial; the last group sums those.
@@ -168,17 +226,16 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   if (!s_last) return;
   __threadfence();
   {
-    double* Gg = a.Gpart + int64_t(a.P + grp) * k * k;
-    const double* base = a.Gpart + int64_t(grp) * CQ_GROUP * k * k;
-    for (int idx = tid; idx < k * k; idx += nt) {
-      double u[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      int p = 0;
-      for (; p + 8 <= gsize; p += 8) {
+    double* Gg = a.Gpart + int64_t(a.P + grp) * npair;
+    const double* base = a.Gpart + int64_t(grp) * CQ_GROUP * npair;
+    for (int p = tid; p < npair; p += nt) {
+      double u[CQ_GROUP];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) u[q] += __ldcg(base + int64_t(p + q) * k * k + idx);
-      }
-      for (; p < gsize; ++p) u[0] += __ldcg(base + int64_t(p) * k * k + idx);
-      Gg[idx] = ((u[0] + u[1]) + (u[2] + u[3])) + ((u[4] + u[5]) + (u[6] + u[7]));
+      for (int q = 0; q < CQ_GROUP; ++q) u[q] = q < gsize ? __ldcg(base + int64_t(q) * npair + p) : 0.0;
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < CQ_GROUP; ++q) acc += u[q];
+      Gg[p] = acc;
     }
   }
   __threadfence();
@@ -196,18 +253,25 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   double* G = big ? a.big : sm;                 // k x k
   double* X = G + k * k;                        // k x k
   double* G0 = X + k * k;                       // k x k
-  for (int idx = tid; idx < k * k; idx += nt) {
-    const double* base = a.Gpart + int64_t(a.P) * k * k + idx;
-    double u[4] = {0, 0, 0, 0};
+  double* colj = big ? G0 + k * k : s_col;      // k
+  for (int p = tid; p < npair; p += nt) {
+    const double* base = a.Gpart + int64_t(a.P) * npair + p;
+    double acc = 0.0;
     int g = 0;
-    for (; g + 4 <= ngrp; g += 4) {
+    for (; g + 8 <= ngrp; g += 8) {
+      double u[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) u[q] += __ldcg(base + int64_t(g + q) * k * k);
+      for (int q = 0; q < 8; ++q) u[q] = __ldcg(base + int64_t(g + q) * npair);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc += u[q];
     }
-    for (; g < ngrp; ++g) u[0] += __ldcg(base + int64_t(g) * k * k);
-    const double sv = (u[0] + u[1]) + (u[2] + u[3]);
-    G[idx] = sv;
-    G0[idx] = sv;
+    for (; g < ngrp; ++g) acc += __ldcg(base + int64_t(g) * npair);
+    int i, j;
+    tri_ij(p, k, &i, &j);
+    G[i * k + j] = acc;
+    G[j * k + i] = acc;
+    G0[i * k + j] = acc;
+    G0[j * k + i] = acc;
   }
   __syncthreads();
   if (final_pass) {
@@ -226,7 +290,34 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
     }
     return;
   }
-  bool ok = chol_with_inverse(G, X, k, &s_rd);
+  if (a.pass > 0 && a.Racc == nullptr) {
+    // Only Q is wanted and the block is already orthonormal to ||E||_F <= 1e-8,
+    // E = G - I: the last pass multiplies by I - E/2 instead of factoring again
+    __shared__ double s_red[CQ_THREADS / 32];
+    double e2 = 0.0;
+    for (int idx = tid; idx < k * k; idx += nt) {
+      const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
+      e2 = fma(dv, dv, e2);
+    }
+    for (int off = 16; off; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+    if ((tid & 31) == 0) s_red[tid >> 5] = e2;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) tot += s_red[w];
+    if (tot <= 1e-16) {                           // ||E||_F <= 1e-8 (false for NaN)
+      for (int idx = tid; idx < k * k; idx += nt) {
+        const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
+        a.Rinv[idx] = ((idx % (k + 1) == 0) ? 1.0 : 0.0) - 0.5 * dv;
+      }
+      if (tid == 0) {
+        a.status[4] = 1;
+        a.status[1] = 2;
+        a.status[3] += 1;
+      }
+      return;
+    }
+  }
+  bool ok = chol_with_inverse(G, X, colj, k, &s_rd, &s_bad);
   bool shifted = false;
   if (!ok) {
     __shared__ double s_shift;
@@ -238,7 +329,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
     __syncthreads();
     for (int idx = tid; idx < k * k; idx += nt) G[idx] = G0[idx] + (((idx / k) == (idx % k)) ? s_shift : 0.0);
     __syncthreads();
-    ok = chol_with_inverse(G, X, k, &s_rd);
+    ok = chol_with_inverse(G, X, colj, k, &s_rd, &s_bad);
     shifted = true;
   }
   if (!ok) {                                    // not even the shifted Gram is positive definite
@@ -300,7 +391,7 @@ void qr_shape(int64_t m, int k, int* rows, int* P, int* nstat) {
   const int64_t bmax = std::max<int64_t>(1, budget / (2 * int64_t(k)));
   *rows = int(std::min<int64_t>(bmax, std::max<int64_t>(4, ceil_div(m, num_sms()))));
   *P = int(ceil_div(m, *rows));
-  *nstat = 4 + 1 + (*P + 15) / 16;      // [0..3] chain state, then arrival counters
+  *nstat = 5 + 1 + (*P + 15) / 16;      // [0..4] chain state, then arrival counters
 }
 }  // namespace
 
@@ -314,7 +405,7 @@ QrPool qr_pool_reserve(Arena& ar, const std::vector<std::pair<int64_t, int>>& sh
     gp = std::max<size_t>(gp, size_t(P + (P + 15) / 16) * k * k);
     kk = std::max<size_t>(kk, size_t(k) * k);
     mk = std::max<size_t>(mk, size_t(m) * k);
-    if (k > CQ_SMEM_K) bigk = std::max<size_t>(bigk, 3 * size_t(k) * k);
+    if (k > CQ_SMEM_K) bigk = std::max<size_t>(bigk, 3 * size_t(k) * k + size_t(k));
     st = std::max<size_t>(st, size_t(ns));
     if (k <= TSQR_KMAX) {
       size_t ii = 0;
@@ -383,7 +474,7 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
   base.q_rs = q_rs;
   base.q_cs = q_cs;
   base.Gpart = b.Gpart;
-  base.counter = b.status ? b.status + 4 : nullptr;
+  base.counter = b.status ? b.status + 5 : nullptr;
   base.Rinv = b.Rinv;
   base.Racc = R;
   base.big = b.big;

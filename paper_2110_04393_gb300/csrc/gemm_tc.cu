@@ -2,20 +2,23 @@
 // path): C = alpha * A B + beta * C with float64 inputs and outputs, computed
 // from bf16 "digit" slices whose products and sums are exact.
 //
-// Splitting (no FP64 arithmetic anywhere). A first launch reduces, for every
-// row r of A and column c of B, the largest float64 exponent over the whole K
-// range (integer atomics on the exponent bits). With E_r = that exponent + 2
-// every a_rk satisfies |a_rk| < 2^{E_r - 1}, so F = |a_rk| 2^{63 - E_r} is an
-// integer below 2^62 (taken from the mantissa bits with shifts). Adding the
-// constant 64 in every 7-bit digit position (plus half a unit of the last
-// kept digit) and reading the digits back gives balanced digits
+// Three launches, no FP64 arithmetic anywhere. (1) Exponents: for every row r
+// of A and column c of B, the largest float64 exponent over the whole K range
+// (integer atomics on the exponent bits). With E_r = that exponent + 2 every
+// a_rk satisfies |a_rk| < 2^{E_r - 1}, so F = |a_rk| 2^{63 - E_r} is an integer
+// below 2^62 (taken from the mantissa bits with shifts). (2) Digit planes:
+// adding the constant 64 in every 7-bit digit position (plus half a unit of
+// the last kept digit) and reading the digits back gives balanced digits
 // d_1 .. d_s in [-64, 64] with F = sum_p d_p 2^{63 - 7p} + rounding error
 // below 2^{62 - 7s}: a_rk ~ 2^{E_r} sum_p d_p 2^{-7p}. Every digit is exact in
-// bf16. Columns of B are split the same way (E_c).
+// bf16; the s planes of every operand tile are written to global memory in
+// the canonical K-major shared-memory layout, by many small blocks (the split
+// is the bulk of the work and needs many warps per SM to hide its latency).
+// Columns of B are split the same way (E_c). (3) Products, below.
 //
 // Products. Digit pairs with p + q <= s + 1 are kept; pairs of one level
 // L = p + q accumulate (tcgen05.mma, fp32 in TMEM) into the TMEM region of that
-// level. Per 64-wide K-chunk a level sum is an integer of magnitude at most
+// level (one MMA chain per digit of A against all digits of B at once). Per 64-wide K-chunk a level sum is an integer of magnitude at most
 // 8 * 64 * 64^2 = 2^21, so fp32 holds it exactly. After each chunk the levels
 // are read back, converted to integers exactly (magic-number addition) and
 // added into two int64 accumulators per output, H = sum_{L<=5} D_L 2^{7(5-L)}
@@ -28,9 +31,10 @@
 // max_k |a_rk| max_k |b_kc|; s = 8 keeps 56 bits (FP64 class). Rows of A or
 // columns of B that hold Inf or NaN give NaN outputs; subnormals count as zero.
 //
-// Tile: 128 rows (one TMEM lane each) x 32 columns, 256 threads (8 warps).
-// Operand chunks of 128 x 64 and 32 x 64 digits per plane are staged in shared
-// memory in the canonical K-major layout of tc_sm103.cuh.
+// Product tile: 128 rows (one TMEM lane each) x 32 columns, 256 threads (8
+// warps). Per K-chunk (64 wide, or the K extent rounded up to 16 when K is
+// short) one bulk copy brings the s planes of A and one those of B into shared
+// memory (completion on an mbarrier); one thread issues the MMAs.
 #include <algorithm>
 #include <cmath>
 
@@ -93,7 +97,9 @@ __device__ __forceinline__ int float_to_int_small(float x) {
 }
 
 // Rounds T 2^{e2} to float64, T = H 2^28 + Lo (128-bit), with integer operations.
-__device__ __forceinline__ double round_i128(long long H, long long Lo, int e2) {
+// Kept out of line: the epilogue calls it for every output column, and inlined
+// copies would overflow the instruction cache.
+__device__ __noinline__ double round_i128(long long H, long long Lo, int e2) {
   const uint64_t tl = uint64_t(H) << 28;
   const long long th = H >> 36;
   uint64_t ml = tl + uint64_t(Lo);
@@ -135,6 +141,17 @@ __device__ __forceinline__ double round_i128(long long H, long long Lo, int e2) 
   return __longlong_as_double((long long)(sgn | (uint64_t(E + 1023) << 52) | frac));
 }
 
+// One output: C = alpha * round(T 2^{Er + Ec - 63}) + beta * C, NaN when the
+// row or column held Inf / NaN (out of line, like round_i128).
+__device__ __noinline__ void store_out(double* cp, long long H, long long Lo, int Er, int Ec, double alpha,
+                                       double beta) {
+  double v = (Er == kNonFinite || Ec == kNonFinite) ? __longlong_as_double(0x7FF8000000000000LL)
+                                                    : round_i128(H, Lo, Er + Ec - 63);
+  if (alpha != 1.0) v *= alpha;
+  if (beta != 0.0) v = fma(beta, *cp, v);
+  *cp = v;
+}
+
 struct TcArgs {
   const GemmDesc* descs;
   int ndesc;
@@ -142,20 +159,30 @@ struct TcArgs {
   int epoch;      // tag of this launch's exponents (tags of older launches lose the max)
 };
 
-__device__ __forceinline__ int find_desc(const GemmDesc* descs, int ndesc, int64_t t, bool exp_pass) {
-  int lo = 0, hi = ndesc - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    const int64_t b = exp_pass ? descs[mid].exp_begin : descs[mid].tile_begin;
-    if (b <= t) lo = mid; else hi = mid - 1;
+// Index of the descriptor whose block range holds block t: the largest i with
+// begin(i) <= t, for the product tiles (kind 0), the exponent pass (1) or the
+// split pass (2). Warp-parallel (32 descriptors per load round); every thread
+// of the block calls it and gets the same answer.
+__device__ __forceinline__ int find_desc(const GemmDesc* descs, int ndesc, int64_t t, int kind) {
+  const int lane = threadIdx.x & 31;
+  int count = 0;
+  for (int base = 0; base < ndesc; base += 32) {
+    const int i = base + lane;
+    bool le = false;
+    if (i < ndesc) {
+      const int64_t b = kind == 0 ? __ldg(&descs[i].tile_begin)
+                                  : (kind == 1 ? __ldg(&descs[i].exp_begin) : __ldg(&descs[i].split_begin));
+      le = b <= t;
+    }
+    count += __popc(__ballot_sync(0xffffffffu, le));
   }
-  return lo;
+  return max(count - 1, 0);
 }
 
 // ---- pass 1: largest exponent per row of A and per column of B over all of K
 __global__ void __launch_bounds__(256) tc_exponent_kernel(TcArgs args) {
   const int64_t t = blockIdx.x;
-  const GemmDesc& d = args.descs[find_desc(args.descs, args.ndesc, t, true)];
+  const GemmDesc d = args.descs[find_desc(args.descs, args.ndesc, t, 1)];
   int64_t local = t - d.exp_begin;
   // block counts as in gemm_tc_prepare (at least one block per side)
   const int64_t kb = max((d.K + EX_IN - 1) / EX_IN, int64_t(1));
@@ -179,21 +206,27 @@ __global__ void __launch_bounds__(256) tc_exponent_kernel(TcArgs args) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tag = args.epoch << 16;
   if (is == 1) {
-    // inner index contiguous: a warp reads along K for four rows
+    // inner index contiguous: a warp reads along K for four rows (32 loads in flight)
+    double x[4][8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t o = o0 + warp + 8 * j;
+      const double* p = base + o * os;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t k = k0 + lane + 32 * u;
+        x[j][u] = (o < outer && k < d.K) ? __ldg(p + k) : 0.0;
+      }
+    }
+#pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t o = o0 + warp + 8 * j;
       int m = -1;
-      if (o < outer) {
-        const double* p = base + o * os;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int64_t k = k0 + lane + 32 * u;
-          if (k < d.K) m = max(m, dexp(__ldg(p + k)));
-        }
-      }
+      for (int u = 0; u < 8; ++u) m = max(m, dexp(x[j][u]));
 #pragma unroll
       for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
-      if (lane == 0 && m >= 0) atomicMax(out + o, tag | m);
+      if (lane == 0 && o < outer && m >= 0) atomicMax(out + o, tag | m);
     }
   } else {
     // outer index contiguous (or neither): lanes along the rows, warps along K
@@ -202,9 +235,16 @@ __global__ void __launch_bounds__(256) tc_exponent_kernel(TcArgs args) {
     int m = -1;
     if (o < outer) {
       const double* p = base + o * os;
-      for (int u = 0; u < EX_IN / 8; ++u) {
-        const int64_t k = k0 + warp + 8 * u;
-        if (k < d.K) m = max(m, dexp(__ldg(p + k * is)));
+#pragma unroll
+      for (int u0 = 0; u0 < EX_IN / 8; u0 += 16) {
+        double x[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int64_t k = k0 + warp + 8 * (u0 + u);
+          x[u] = (k < d.K) ? __ldg(p + k * is) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) m = max(m, dexp(x[u]));
       }
     }
     red[warp][lane] = m;
@@ -223,38 +263,116 @@ __device__ __forceinline__ int decode_exp(int v, int epoch) {
   return (v & 0xFFFF) - kExBias + 2;                    // E with |x| < 2^{E-1}
 }
 
-// ---- pass 2: digit products on the tensor cores
+// ---- pass 2: digit planes. A block splits a 32 x bk sub-tile of A (rows) or
+// of B (columns) and writes its s bf16 planes in the canonical K-major layout
+// of the 128 x bk (A) or 32 x bk (B) operand tile, padding with zeros.
+__global__ void __launch_bounds__(256) tc_split_kernel(TcArgs args) {
+  __shared__ int Es[32];
+  const int64_t t = blockIdx.x;
+  const GemmDesc d = args.descs[find_desc(args.descs, args.ndesc, t, 2)];
+  const int s = args.s;
+  const int bk = d.bkc;
+  const int64_t nkc = d.nkc;
+  int64_t local = t - d.split_begin;
+  const int64_t na = int64_t(d.mt) * 4 * nkc, per_batch = na + int64_t(d.nt) * nkc;
+  const int64_t bidx = local / per_batch;
+  local -= bidx * per_batch;
+  const bool sideA = local < na;
+  int64_t kc, tile;
+  int quarter = 0;
+  if (sideA) {
+    kc = local % nkc;
+    const int64_t q4 = local / nkc;
+    quarter = int(q4 & 3);
+    tile = q4 >> 2;
+  } else {
+    local -= na;
+    kc = local % nkc;
+    tile = local / nkc;
+  }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t o0 = sideA ? tile * TC_BM + quarter * 32 : tile * TC_BN;   // first row (A) / column (B)
+  const int64_t outer = sideA ? d.M : d.N;
+  if (tid < 32) {
+    const int64_t o = o0 + tid;
+    const int* ex = sideA ? d.ex_row + bidx * d.M : d.ex_col + bidx * d.N;
+    Es[tid] = o < outer ? decode_exp(__ldcg(ex + o), args.epoch) : 0;
+  }
+  __syncthreads();
+  const double* base = sideA ? d.A + bidx * d.a_bs : d.B + bidx * d.b_bs;
+  const int64_t os = sideA ? d.a_rs : d.b_cs, is = sideA ? d.a_cs : d.b_rs;
+  const uint32_t plane = sideA ? uint32_t(TC_BM * bk * 2) : uint32_t(TC_BN * bk * 2);
+  uint8_t* dst = sideA ? d.pa + ((bidx * d.mt + tile) * nkc + kc) * int64_t(s) * plane
+                       : d.pb + ((bidx * d.nt + tile) * nkc + kc) * int64_t(s) * plane;
+  const int ncm = bk / 2;                      // core matrices (8 rows x 8 k) in the 32 x bk sub-tile
+  const int kgs = bk / 8;
+  const int cr = lane >> 2, ck = (lane & 3) * 2;
+  const int64_t k0 = kc * bk;
+  double x[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int cm = warp + 8 * j;
+    const int rg = cm / kgs, kg = cm % kgs;
+    const int64_t o = o0 + rg * 8 + cr, k = k0 + kg * 8 + ck;
+    const double* p = base + o * os + k * is;
+    const bool ok = cm < ncm && o < outer;
+    x[2 * j] = (ok && k < d.K) ? __ldg(p) : 0.0;
+    x[2 * j + 1] = (ok && k + 1 < d.K) ? __ldg(p + is) : 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int cm = warp + 8 * j;
+    if (cm >= ncm) break;
+    const int rg = cm / kgs, kg = cm % kgs;
+    const int rl = rg * 8 + cr;                         // row within the 32-row sub-tile
+    const int rt = sideA ? quarter * 32 + rl : rl;      // row within the operand tile
+    int d0[8], d1[8];
+    digits(x[2 * j], Es[rl], s, d0);
+    digits(x[2 * j + 1], Es[rl], s, d1);
+    const uint32_t off = tc::canon_off_w(rt, kg * 8 + ck, bk);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (q >= s) break;
+      const __nv_bfloat162 h = __floats2bfloat162_rn(int_to_float_small(d0[q]), int_to_float_small(d1[q]));
+      *reinterpret_cast<__nv_bfloat162*>(dst + q * plane + off) = h;
+    }
+  }
+}
+
+// ---- pass 3: digit products on the tensor cores
 __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int s = args.s;
-  uint8_t* As = smem;                                  // s x (128 x 64 bf16) = s x 16 KB
-  uint8_t* Bs = smem + s * 16384;                      // s x (32 x 64 bf16)  = s x 4 KB
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t lbar, mbar;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_fail, s_last;
+  __shared__ int s_fail, s_last, s_issued;
   __shared__ int Er[TC_BM], Ec[TC_BN];
 
   const int64_t t = blockIdx.x;
-  const GemmDesc d = args.descs[find_desc(args.descs, args.ndesc, t, false)];
+  const GemmDesc d = args.descs[find_desc(args.descs, args.ndesc, t, 0)];
+  const int bk = d.bkc;
+  const uint32_t pA = uint32_t(TC_BM * bk * 2), pB = uint32_t(TC_BN * bk * 2);   // plane bytes
+  uint8_t* As = smem;                                  // s planes of 128 x bk bf16
+  uint8_t* Bs = smem + s * pA;                         // s planes of 32 x bk bf16
   int64_t local = t - d.tile_begin;
   const int ntile = int(local % d.nt); local /= d.nt;
   const int mtile = int(local % d.mt); local /= d.mt;
   const int ks = int(local % d.ksplit);
   const int64_t bidx = local / d.ksplit;
-  const double* A = d.A + bidx * d.a_bs;
-  const double* B = d.B + bidx * d.b_bs;
   const int64_t m0 = int64_t(mtile) * TC_BM, n0 = int64_t(ntile) * TC_BN;
-  const int64_t k_begin = int64_t(ks) * d.kchunk;
-  const int64_t k_end = min(d.K, k_begin + d.kchunk);
+  const int64_t cps = d.kchunk / bk;                   // chunks per split
+  const int64_t kc_begin = int64_t(ks) * cps;
+  const int64_t kc_end = min(d.nkc, kc_begin + cps);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t ncols = tc::tmem_cols_for(s * TC_BN);
+  const uint32_t ncols = tc::tmem_cols_for((2 * s - 1) * TC_BN);   // levels 2 .. 2s
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, ncols);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&bar, 1);
+    tc::mbar_init(&lbar, 1);
+    tc::mbar_init(&mbar, 1);
     s_fail = 0;
   }
   for (int i = tid; i < TC_BM + TC_BN; i += TC_THREADS) {
@@ -270,102 +388,87 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = tmem_base;
-  const uint32_t idesc = tc::idesc_bf16_f32(TC_BM, TC_BN);
+  const uint8_t* srcA = d.pa + ((bidx * d.mt + mtile) * d.nkc) * int64_t(s) * pA;
+  const uint8_t* srcB = d.pb + ((bidx * d.nt + ntile) * d.nkc) * int64_t(s) * pB;
 
-  // staging roles: a warp fills core matrices (8 rows x 8 k); lane -> row lane/4, k pair lane%4
-  const int cr = lane >> 2, ck = (lane & 3) * 2;
   // epilogue roles: TMEM lane quadrant q (warp % 4), column half ch
   const int q = warp & 3, ch = warp >> 2;
   long long accH[16], accL[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) { accH[j] = 0; accL[j] = 0; }
-  uint32_t phase = 0;
+  uint32_t lph = 0, mph = 0;
 
-  for (int64_t kc = k_begin; kc < k_end; kc += TC_BK) {
-    // ---- A: 128 x 64 -> s planes; warp w: row groups 2w, 2w+1, all 8 k groups
-#pragma unroll 2
-    for (int cm = 0; cm < 16; ++cm) {
-      const int rg = 2 * warp + (cm >> 3), kg = cm & 7;
-      const int rr = rg * 8 + cr, kk = kg * 8 + ck;
-      const int64_t r = m0 + rr, k = kc + kk;
-      double x0 = 0.0, x1 = 0.0;
-      if (r < d.M) {
-        const double* p = A + r * d.a_rs + k * d.a_cs;
-        if (k < k_end) x0 = __ldg(p);
-        if (k + 1 < k_end) x1 = __ldg(p + d.a_cs);
-      }
-      int d0[8], d1[8];
-      digits(x0, Er[rr], s, d0);
-      digits(x1, Er[rr], s, d1);
-      const uint32_t off = tc::canon_off(rr, kk);
-#pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        if (p >= s) break;
-        const __nv_bfloat162 h = __floats2bfloat162_rn(int_to_float_small(d0[p]), int_to_float_small(d1[p]));
-        *reinterpret_cast<__nv_bfloat162*>(As + p * 16384 + off) = h;
-      }
-    }
-    // ---- B: 32 x 64 (columns x k) -> s planes; warp w: column group w/2, k groups 4(w%2)..+3
-#pragma unroll
-    for (int cm = 0; cm < 4; ++cm) {
-      const int cg = warp >> 1, kg = (warp & 1) * 4 + cm;
-      const int cc = cg * 8 + cr, kk = kg * 8 + ck;
-      const int64_t c = n0 + cc, k = kc + kk;
-      double x0 = 0.0, x1 = 0.0;
-      if (c < d.N) {
-        const double* p = B + k * d.b_rs + c * d.b_cs;
-        if (k < k_end) x0 = __ldg(p);
-        if (k + 1 < k_end) x1 = __ldg(p + d.b_rs);
-      }
-      int d0[8], d1[8];
-      digits(x0, Ec[cc], s, d0);
-      digits(x1, Ec[cc], s, d1);
-      const uint32_t off = tc::canon_off(cc, kk);
-#pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        if (p >= s) break;
-        const __nv_bfloat162 h = __floats2bfloat162_rn(int_to_float_small(d0[p]), int_to_float_small(d1[p]));
-        *reinterpret_cast<__nv_bfloat162*>(Bs + p * 4096 + off) = h;
-      }
-    }
-    tc::fence_async_smem();
-    __syncthreads();
-    // ---- one thread issues every kept digit-pair product of this chunk
+  for (int64_t kc = kc_begin; kc < kc_end; ++kc) {
+    // ---- the chunk's s planes of A and of B, one bulk copy each
     if (tid == 0) {
-      tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
-      for (int L = 2; L <= s + 1; ++L) {
-        bool first = true;
-        for (int p = 1; p <= s; ++p) {
-          const int qq = L - p;
-          if (qq < 1 || qq > s) continue;
-          for (int st = 0; st < 4; ++st) {
-            tc::mma_bf16(taddr + uint32_t((L - 2) * TC_BN),
-                         tc::smem_desc(a0 + (p - 1) * 16384 + 256 * st, 128, 1024),
-                         tc::smem_desc(b0 + (qq - 1) * 4096 + 256 * st, 128, 1024), idesc, first ? 0u : 1u);
-            first = false;
-          }
-        }
-      }
-      tc::mma_commit(&bar);
+      tc::mbar_arrive_expect_tx(&lbar, uint32_t(s) * (pA + pB));
+      tc::bulk_g2s(As, srcA + kc * int64_t(s) * pA, uint32_t(s) * pA, &lbar);
+      tc::bulk_g2s(Bs, srcB + kc * int64_t(s) * pB, uint32_t(s) * pB, &lbar);
     }
-    if (!tc::mbar_wait_bounded(&bar, phase, kPolls)) atomicExch(&s_fail, 1);
-    phase ^= 1;
+    const bool loaded = tc::mbar_wait_bounded(&lbar, lph, kPolls);
+    if (!loaded) {
+      atomicExch(&s_fail, 1);
+      tc::mbar_wait_bounded(&lbar, lph, kPolls);      // give the copy in flight one more bounded wait
+    }
+    lph ^= 1;
+    // ---- one thread issues every kept digit-pair product of this chunk (only
+    //      after its own wait saw the copy complete); every thread then waits
+    //      for the issued products before anything else touches TMEM or smem
+    if (tid == 0) s_issued = loaded ? 1 : 0;
+    if (tid == 0 && loaded) {
+      tc::fence_after_sync();
+      // B planes are contiguous, i.e. one K-major operand of 32 s rows: the MMA
+      // of A digit p against it (N = 32 s) adds d_p e_q into columns
+      // (p + q - 2) 32, the region of level p + q. The p = 1 chain starts the
+      // kept levels 2 .. s + 1 (columns below 32 s); columns from 32 s on hold
+      // levels above s + 1, which are never read.
+      const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
+      const uint32_t idesc_s = tc::idesc_bf16_f32(TC_BM, TC_BN * s);
+      const int steps = bk / 16;
+      for (int p = 1; p <= s; ++p)
+        for (int st = 0; st < steps; ++st)
+          tc::mma_bf16(taddr + uint32_t((p - 1) * TC_BN), tc::smem_desc(a0 + (p - 1) * pA + 256 * st, 128, 16 * bk),
+                       tc::smem_desc(b0 + 256 * st, 128, 16 * bk), idesc_s, (p == 1 && st == 0) ? 0u : 1u);
+      tc::mma_commit(&mbar);
+    }
+    __syncthreads();
+    if (s_issued) {
+      if (!tc::mbar_wait_bounded(&mbar, mph, kPolls)) {
+        atomicExch(&s_fail, 1);
+        tc::mbar_wait_bounded(&mbar, mph, kPolls);    // let the MMAs in flight finish (bounded)
+      }
+      mph ^= 1;
+    }
     tc::fence_after_sync();
     __syncthreads();
     if (s_fail) break;
-    // ---- exact level sums -> int64 accumulators (TMEM lane q*32+lane, columns ch*16..+16)
+    // ---- exact level sums -> int64 accumulators (TMEM lane q*32+lane, columns
+    //      ch*16..+16); levels are read four at a time, then one wait
+    const uint32_t tl = taddr + (uint32_t(q * 32) << 16) + uint32_t(ch * 16);
 #pragma unroll
-    for (int L = 2; L <= 9; ++L) {
-      if (L > s + 1) break;
-      float v[16];
-      tc::tmem_ld16(taddr + (uint32_t(q * 32) << 16) + uint32_t((L - 2) * TC_BN + ch * 16), v);
-      if (L <= 5) {
+    for (int g = 0; g < 2; ++g) {
+      if (2 + 4 * g > s + 1) break;
+      uint32_t v[64];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) accH[j] += (long long)float_to_int_small(v[j]) << (7 * (5 - L));
-      } else {
+      for (int u = 0; u < 4; ++u) {
+        const int L = 2 + 4 * g + u;
+        if (L <= s + 1) tc::tmem_ld16_nowait(tl + uint32_t((L - 2) * TC_BN), v + 16 * u);
+        else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) accL[j] += (long long)float_to_int_small(v[j]) << (7 * (9 - L));
+          for (int j = 0; j < 16; ++j) v[16 * u + j] = 0u;
+        }
+      }
+      tc::tmem_wait_ld64(v);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int L = 2 + 4 * g + u;
+        if (L > s + 1) break;
+        const int sh = 7 * (3 - u);                 // 7 (5 - L) for H, 7 (9 - L) for Lo
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const long long iv = (long long)float_to_int_small(__uint_as_float(v[16 * u + j])) << sh;
+          if (g == 0) accH[j] += iv; else accL[j] += iv;
+        }
       }
     }
     tc::fence_before_sync();
@@ -376,19 +479,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int
   const int64_t row = m0 + rr;
   const int64_t c0 = n0 + ch * 16;
   const int64_t row_off = d.c_rdiv > 0 ? (row / d.c_rdiv) * d.c_rs + (row % d.c_rdiv) * d.c_rs2 : row * d.c_rs;
-  auto store = [&](int j, double v) {
-    double* cp = d.C + bidx * d.c_bs + row_off + (c0 + j) * d.c_cs;
-    if (Er[rr] == kNonFinite || Ec[ch * 16 + j] == kNonFinite) v = __longlong_as_double(0x7FF8000000000000LL);
-    if (d.alpha != 1.0) v *= d.alpha;
-    if (d.beta != 0.0) v = fma(d.beta, *cp, v);
-    *cp = v;
+  double* const crow = d.C + bidx * d.c_bs + row_off;
+  auto store = [&](int j, long long H, long long Lo) {
+    store_out(crow + (c0 + j) * d.c_cs, H, Lo, Er[rr], Ec[ch * 16 + j], d.alpha, d.beta);
   };
   if (!s_fail) {
     if (d.ksplit == 1) {
       if (row < d.M) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-          if (c0 + j < d.N) store(j, round_i128(accH[j], accL[j], Er[rr] + Ec[ch * 16 + j] - 63));
+          if (c0 + j < d.N) store(j, accH[j], accL[j]);
       }
     } else {
       // integer partials meet in L2; the last CTA of the tile rounds and writes C
@@ -410,22 +510,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int
       __syncthreads();
       if (s_last) {
         __threadfence();
-#pragma unroll 4
+#pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int cc = ch * 16 + j;
-          unsigned long long* ph = acc + cc * TC_BM + rr;
-          unsigned long long* pl = acc + TC_BM * TC_BN + cc * TC_BM + rr;
-          const long long H = (long long)__ldcg(ph), Lo = (long long)__ldcg(pl);
-          *ph = 0;
-          *pl = 0;
-          if (row < d.M && c0 + j < d.N) store(j, round_i128(H, Lo, Er[rr] + Ec[cc] - 63));
+          accH[j] = (long long)__ldcg(acc + cc * TC_BM + rr);
+          accL[j] = (long long)__ldcg(acc + TC_BM * TC_BN + cc * TC_BM + rr);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int cc = ch * 16 + j;
+          acc[cc * TC_BM + rr] = 0;
+          acc[TC_BM * TC_BN + cc * TC_BM + rr] = 0;
+          if (row < d.M && c0 + j < d.N) store(j, accH[j], accL[j]);
         }
       }
     }
   } else {
-    // a wait gave up: let the in-flight MMAs drain (bounded) before freeing TMEM,
-    // raise the flag and leave NaN in this CTA's outputs
-    tc::mbar_wait_bounded(&bar, phase ^ 1, kPolls);
+    // a wait gave up: raise the flag and leave NaN in this CTA's outputs
     if (tid == 0) atomicExch(err, 1);
     if (row < d.M)
       for (int j = 0; j < 16; ++j)
@@ -446,9 +547,9 @@ int tc_digits_for_accuracy(double rel) {
   return s;
 }
 
-void gemm_tc_prepare(std::vector<GemmDesc>& g, int target_ctas, TcPlan* plan, long long* acc_base, int* ex_base,
-                     int* cbase) {
-  int64_t t = 0, eb = 0, acc = 0, ex = 0, c = 0;
+void gemm_tc_prepare(std::vector<GemmDesc>& g, int s, int target_ctas, TcPlan* plan, long long* acc_base,
+                     int* ex_base, int* cbase, uint8_t* plane_base) {
+  int64_t t = 0, eb = 0, sb = 0, acc = 0, ex = 0, c = 0, pl = 0;
   int64_t tiles_total = 0;
   for (auto& d : g) {
     // keep the long side on the 128-row tile
@@ -465,24 +566,35 @@ void gemm_tc_prepare(std::vector<GemmDesc>& g, int target_ctas, TcPlan* plan, lo
     tiles_total += int64_t(d.batch) * d.mt * d.nt;
   }
   for (auto& d : g) {
-    const int64_t chunks = std::max<int64_t>(1, ceil_div(std::max<int64_t>(d.K, 1), TC_BK));
+    // chunk width: the K extent rounded up to 16 when it is short, else 64
+    const int64_t K1 = std::max<int64_t>(d.K, 1);
+    d.bkc = int(K1 >= TC_BK ? TC_BK : ceil_div(K1, 16) * 16);
+    d.nkc = ceil_div(K1, d.bkc);
     // split K only while the grid is below one CTA per SM
     const int64_t want = std::max<int64_t>(1, target_ctas / std::max<int64_t>(tiles_total, 1));
-    const int64_t split = std::min(chunks, want);
-    const int64_t cps = ceil_div(chunks, split);
-    d.kchunk = cps * TC_BK;
-    d.ksplit = int(ceil_div(chunks, cps));
+    const int64_t split = std::min(d.nkc, want);
+    const int64_t cps = ceil_div(d.nkc, split);
+    d.kchunk = cps * d.bkc;
+    d.ksplit = int(ceil_div(d.nkc, cps));
     const int64_t base = int64_t(d.batch) * d.mt * d.nt;
     d.tile_begin = t;
     t += base * d.ksplit;
     d.exp_begin = eb;
-    const int64_t kb = ceil_div(std::max<int64_t>(d.K, 1), EX_IN);
+    const int64_t kb = ceil_div(K1, EX_IN);
     eb += int64_t(d.batch) *
           (ceil_div(std::max<int64_t>(d.M, 1), EX_OUT) + ceil_div(std::max<int64_t>(d.N, 1), EX_OUT)) * kb;
+    d.split_begin = sb;
+    sb += int64_t(d.batch) * (int64_t(d.mt) * 4 + d.nt) * d.nkc;
     d.ex_row = ex_base ? ex_base + ex : nullptr;
     ex += int64_t(d.batch) * d.M;
     d.ex_col = ex_base ? ex_base + ex : nullptr;
     ex += int64_t(d.batch) * d.N;
+    const int64_t pa_bytes = int64_t(d.batch) * d.mt * d.nkc * s * (TC_BM * d.bkc * 2);
+    const int64_t pb_bytes = int64_t(d.batch) * d.nt * d.nkc * s * (TC_BN * d.bkc * 2);
+    d.pa = plane_base ? plane_base + pl : nullptr;
+    pl += pa_bytes;
+    d.pb = plane_base ? plane_base + pl : nullptr;
+    pl += pb_bytes;
     d.P = nullptr;
     d.acc = nullptr;
     d.cnt = nullptr;
@@ -495,9 +607,11 @@ void gemm_tc_prepare(std::vector<GemmDesc>& g, int target_ctas, TcPlan* plan, lo
   }
   plan->tiles = t;
   plan->exp_blocks = eb;
+  plan->split_blocks = sb;
   plan->acc_words = acc;
   plan->ex_ints = ex;
   plan->counters = c;
+  plan->plane_bytes = pl;
 }
 
 int gemm_tc_launch(const GemmDesc* d_descs, int ndesc, const TcPlan& plan, int s, int epoch, double flops, int* err,
@@ -507,7 +621,7 @@ int gemm_tc_launch(const GemmDesc* d_descs, int ndesc, const TcPlan& plan, int s
     set_error("emulated GEMM: digits must be 1..8 and at most 32767 launches per plan");
     return TT_EINVAL;
   }
-  const size_t smem = size_t(s) * (16384 + 4096);
+  const size_t smem = size_t(s) * (TC_BM + TC_BN) * TC_BK * 2;   // upper bound over chunk widths
   static bool attr = false;
   if (!attr) {
     TTR_CHECK_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 164 * 1024));
@@ -516,11 +630,13 @@ int gemm_tc_launch(const GemmDesc* d_descs, int ndesc, const TcPlan& plan, int s
   TcArgs a{d_descs, ndesc, s, epoch};
   tc_exponent_kernel<<<unsigned(plan.exp_blocks), 256, 0, st>>>(a);
   TTR_CHECK_LAUNCH();
+  tc_split_kernel<<<unsigned(plan.split_blocks), 256, 0, st>>>(a);
+  TTR_CHECK_LAUNCH();
   cudaEvent_t e0;
   const bool prof = prof_gemm_begin(st, &e0);
   gemm_tc_kernel<<<unsigned(plan.tiles), TC_THREADS, smem, st>>>(a, err);
   TTR_CHECK_LAUNCH();
-  prof_count_launch(2);
+  prof_count_launch(3);
   if (prof) prof_gemm_end(st, flops);
   return TT_OK;
 }

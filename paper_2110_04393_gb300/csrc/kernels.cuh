@@ -33,6 +33,11 @@ struct GemmDesc {
   int64_t exp_begin;    // prefix of the exponent-pass blocks
   int64_t c_rdiv;       // > 0: row r of C sits at (r / c_rdiv) c_rs + (r % c_rdiv) c_rs2
   int64_t c_rs2;
+  uint8_t* pa;          // digit planes of A (tiles x chunks x s planes, canonical layout)
+  uint8_t* pb;          // digit planes of B
+  int64_t nkc;          // K-chunks
+  int64_t split_begin;  // prefix of the split-pass blocks
+  int32_t bkc;          // K-chunk width (16, 32, 48 or 64)
 };
 
 constexpr int GEMM_BM = 32, GEMM_BN = 32, GEMM_BK = 16, GEMM_THREADS = 256;
@@ -49,16 +54,17 @@ int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, double flops,
 // ----------------------------------------------------------------------------
 // Emulated FP64 GEMM on the tcgen05 tensor cores (same descriptors; see
 // gemm_tc.cu): s = bf16 digits per operand (1..8). One launch group is an
-// exponent pass plus the product pass. The exponent region (ex_ints) must be
+// exponent pass, a digit-split pass (planes in plane_bytes of scratch, no
+// initial value needed) and the product pass. The exponent region (ex_ints) must be
 // zero before the first group of a plan; each group of the plan gets its own
 // epoch 1, 2, ... The accumulator region (acc_words) must be zero before the
 // first group and is left zero. *err (device) becomes 1 if a bounded wait gave up.
 struct TcPlan {
-  int64_t tiles = 0, exp_blocks = 0, acc_words = 0, ex_ints = 0, counters = 0;
+  int64_t tiles = 0, exp_blocks = 0, split_blocks = 0, acc_words = 0, ex_ints = 0, counters = 0, plane_bytes = 0;
 };
 int tc_digits_for_accuracy(double rel);
-void gemm_tc_prepare(std::vector<GemmDesc>& g, int target_ctas, TcPlan* plan, long long* acc_base, int* ex_base,
-                     int* cbase);
+void gemm_tc_prepare(std::vector<GemmDesc>& g, int s, int target_ctas, TcPlan* plan, long long* acc_base,
+                     int* ex_base, int* cbase, uint8_t* plane_base);
 int gemm_tc_launch(const GemmDesc* d_descs, int ndesc, const TcPlan& plan, int s, int epoch, double flops, int* err,
                    cudaStream_t st);
 

@@ -33,6 +33,8 @@ struct Schedule {
   int64_t acc_need = 0, ex_need = 0;            // emulated-GEMM accumulators / exponent tags (largest group)
   long long* acc = nullptr;                     // zeroed once per call, left zero by every group
   int* ex = nullptr;                            // zeroed once per call, tagged by epoch
+  int64_t plane_need = 0;                       // digit-plane bytes (largest group)
+  uint8_t* planes = nullptr;
   int tc_epoch = 0;
   // Group run by the emulated FP64 GEMM on the tensor cores (s digits).
   void gemm_tc(std::vector<GemmDesc> g, int s) {
@@ -40,7 +42,8 @@ struct Schedule {
     double flops = 0.0;
     for (const auto& d : g) flops += 2.0 * double(d.M) * double(d.N) * double(d.K) * double(d.batch);
     TcPlan tp;
-    gemm_tc_prepare(g, num_sms(), &tp, acc, ex, cnt);
+    gemm_tc_prepare(g, s, num_sms(), &tp, acc, ex, cnt, planes);
+    if (tp.plane_bytes > plane_need) plane_need = tp.plane_bytes;
     if (tp.acc_words > acc_need) acc_need = tp.acc_words;
     if (tp.ex_ints > ex_need) ex_need = tp.ex_ints;
     if (tp.counters > cnt_need) cnt_need = tp.counters;
