@@ -109,21 +109,52 @@ int tt_round_sum_rand(int32_t N, int32_t K, const int64_t* dims, const int64_t* 
                       double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
                       void* stream);
 /*
- * TT_PREC_MIXED (no counterpart in the paper): the three long contractions of
- * every bond -- H(Z) H(Omega_n)^T of Algorithm 3, the sketch V(X_n) W_n and the
- * projection Q^T V(X_n) -- run on the tcgen05 tensor cores as split float64
- * products: each operand is cut, per 64-wide K-chunk and per row / column, into
- * s bf16 digits of 7 bits whose pairwise products are exact in the fp32 tensor
- * accumulator, and the kept pairs (p + q <= s + 1) are recombined exactly in
- * integers. The relative error per product is about 2^(10 - 7 s). QR, the
- * small SVD and the remaining short contractions stay float64.
- * tt_mixed_digits(tol, N) returns the s used: products accurate to 1e-3 tol / N
- * (the errors of the N-step contraction recursion compound and enter the kept
- * subspace of redundant sums), 1e-7 / N in fixed-rank mode; 1 <= s <= 8.
+ * TT_PREC_MIXED (no counterpart in the paper, which computes in FP64): every
+ * contraction runs on the tcgen05 tensor cores as the emulated float64 product
+ * of tt_gemm_emulated_f64 (bf16 digits of 7 bits relative to the largest
+ * exponent of each row / column, exact digit products and sums, one rounding):
+ *   - the partial contractions of Algorithm 3 with 2 digits (their rounding
+ *     only perturbs the sketch: each sketched core stays in the range of its
+ *     unfolding, so the subspaces and the rounding error are unaffected);
+ *   - the core updates X_n = M_{n-1} Y_n, the sketches V(X_n) W_n and the
+ *     projections Q^T V(X_n) with s = tt_mixed_digits(tol, N) digits: products
+ *     accurate to 1e-3 tol / N (1e-7 / N in fixed-rank mode), 1 <= s <= 8, so
+ *     s = 8 (FP64 class) at tol = 1e-8.
+ * QR, the small SVD and the truncation stay float64.
  */
 int tt_mixed_digits(double tol, int32_t N);
 size_t tt_round_sum_rand_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
                                    const int64_t* ells, double tol, int32_t precision);
+
+/*
+ * Captured plans of tt_round_sum_rand (an execution mechanism, no counterpart
+ * in the paper). tt_sum_plan_create fixes N, K, dims, ranks (K x (N+1)), the
+ * sketch ranks ells (N+1), tol and precision, builds the whole schedule of the
+ * rounding once and captures it into a CUDA graph; the plan owns its device
+ * memory (input copies, outputs at the clamped sketch ranks, workspace).
+ * tt_sum_plan_run replays it on the given stream for any summand cores
+ * (cores: K*N device pointers, summand-major, shapes as in tt_round_sum_rand),
+ * coefficients (host, K values, NULL = ones) and sketch seed (the sketch is
+ * always drawn on the device): one pinned host-to-device copy of these
+ * arguments and one graph launch. The graph copies the cores in, runs every
+ * step of tt_round_sum_rand in the same order -- results are bit-wise those of
+ * tt_round_sum_rand with sketch NULL and the same seed -- and writes the
+ * rounded cores to out (N device pointers, capacities as in
+ * tt_round_sum_rand, written compactly). out_ranks (host, N+1) receives the
+ * ranks; with tol > 0 the call waits for the stream to read them, otherwise it
+ * returns at once. Runs of one plan are ordered by their streams; one plan
+ * must not run on two streams at the same time. tt_sum_plan_launches returns
+ * the kernels one replay launches; tt_sum_plan_destroy synchronizes the device
+ * and frees the plan (NULL is allowed).
+ * Errors: as tt_round_sum_rand; TT_ECUDA if the capture fails.
+ */
+typedef struct tt_sum_plan tt_sum_plan;
+int tt_sum_plan_create(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const int64_t* ells,
+                       double tol, int32_t precision, tt_sum_plan** plan, void* stream);
+int tt_sum_plan_run(tt_sum_plan* plan, const double* const* cores, const double* coeffs, uint64_t seed,
+                    double* const* out, int64_t* out_ranks, void* stream);
+int tt_sum_plan_destroy(tt_sum_plan* plan);
+int64_t tt_sum_plan_launches(const tt_sum_plan* plan);
 
 /*
  * tt_round_rand -- Algorithm 5 (Randomize-then-Orthogonalize, Section 3.2):

@@ -151,6 +151,57 @@ def tt_round_sum_rand(summands, ells, *, tol=0.0, sketch=None, seed=0, coeffs=No
     return res
 
 
+class SumRoundingPlan:
+    """Captured plan of tt_round_sum_rand for fixed mode sizes, summand ranks,
+    sketch ranks, tolerance and precision; calling it replays the CUDA graph on
+    new summand cores, coefficients and seed (results bit-wise equal to
+    tt_round_sum_rand with the same seed)."""
+
+    def __init__(self, dims, summand_ranks, ells, *, tol=0.0, precision="fp64", device=None, stream=None):
+        self.dims = [int(d) for d in dims]
+        self.N = len(self.dims)
+        self.summand_ranks = [[int(r) for r in R] for R in summand_ranks]
+        self.K = len(self.summand_ranks)
+        self.ell = clamp_ranks(self.dims, ells)
+        self.tol = float(tol)
+        self.device = torch.device(device or "cuda")
+        flat = [r for R in self.summand_ranks for r in R]
+        h = ctypes.c_void_p()
+        _check(nat.lib().tt_sum_plan_create(self.N, self.K, _i64(self.dims), _i64(flat), _i64(self.ell), self.tol,
+                                            _PREC[precision], ctypes.byref(h), _stream(stream, self.device)))
+        self._h = h
+
+    @property
+    def launches(self):
+        return int(nat.lib().tt_sum_plan_launches(self._h))
+
+    def __call__(self, summands, *, seed=0, coeffs=None, out=None, stream=None):
+        N, K, dims, ranks, flat = _sum_args(summands)
+        if (N, K, dims) != (self.N, self.K, self.dims) or ranks != [r for R in self.summand_ranks for r in R]:
+            raise ValueError("summands do not match the plan's sizes and ranks")
+        ell = self.ell
+        if out is None:
+            out = [torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float64, device=self.device)
+                   for n in range(N)]
+        co = None if coeffs is None else (ctypes.c_double * K)(*[float(c) for c in coeffs])
+        out_ranks = (ctypes.c_int64 * (N + 1))()
+        _check(nat.lib().tt_sum_plan_run(self._h, _ptrs(flat), co, ctypes.c_uint64(int(seed)), _ptrs(out),
+                                         out_ranks, _stream(stream, self.device)))
+        r = [int(x) for x in out_ranks]
+        return [out[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib().tt_sum_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _sum_args(summands):
     N = len(summands[0])
     dims = [int(c.shape[1]) for c in summands[0]]

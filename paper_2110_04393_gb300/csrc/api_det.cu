@@ -334,7 +334,7 @@ int build_orthrand(const DetProblem& P, const std::vector<int64_t>& ell, const d
       double* o = ar.take<double>(Rp[n] * ell[n]);
       Om[n] = o;
       const int64_t rr = Rp[n], ll = ell[n];
-      sc.add([=](cudaStream_t s) -> int { return sketch_launch(o, 1, rr, ll, n - 1, seed, s); });
+      sc.add([=](cudaStream_t s) -> int { return sketch_launch(o, 1, rr, ll, n - 1, seed, nullptr, s); });
     }
   }
   // Z_1 = X_1 (already right-orthogonal remainder on the right)

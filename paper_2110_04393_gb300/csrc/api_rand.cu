@@ -19,6 +19,7 @@
 #include <string>
 
 #include "plan.cuh"
+#include "prof.cuh"
 #include "qr.cuh"
 #include "problem.cuh"
 
@@ -46,6 +47,34 @@ int plan_workspace_bytes(const BuildFn& build, size_t* bytes) {
   Schedule s;
   TTR_TRY(build(a, s));
   *bytes = schedule_bytes(a, s);
+  return TT_OK;
+}
+
+// Takes the schedule's own regions from the arena (sizes from the sizing pass).
+static GemmDesc* bind_schedule_regions(Arena& a, const Schedule& probe, Schedule& s) {
+  s.pbuf = a.take<double>(size_t(std::max<int64_t>(probe.pbuf_need, 1)));
+  GemmDesc* d_descs = a.take<GemmDesc>(std::max<size_t>(probe.descs.size(), 1));
+  s.cnt = a.take<int>(size_t(std::max<int64_t>(probe.cnt_need, 1)));
+  s.d_copies = a.take<Copy3>(std::max<size_t>(probe.copies.size(), 1));
+  s.tc_err = a.take<int>(1);
+  s.acc = a.take<long long>(size_t(std::max<int64_t>(probe.acc_need, 1)));
+  s.ex = a.take<int>(size_t(std::max<int64_t>(probe.ex_need, 1)));
+  s.planes = a.take<uint8_t>(size_t(std::max<int64_t>(probe.plane_need, 1)));
+  return d_descs;
+}
+
+// Zeroes what must start at zero on every run (counters, flags, emulated-GEMM
+// accumulators and exponent tags).
+static int reset_schedule_regions(const Schedule& probe, const Schedule& s, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(s.cnt, 0, size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.tc_err, 0, sizeof(int), st);
+  if (e == cudaSuccess && probe.acc_need > 0)
+    e = cudaMemsetAsync(s.acc, 0, size_t(probe.acc_need) * sizeof(long long), st);
+  if (e == cudaSuccess && probe.ex_need > 0) e = cudaMemsetAsync(s.ex, 0, size_t(probe.ex_need) * sizeof(int), st);
+  if (e != cudaSuccess) {
+    set_error(std::string("counter reset: ") + cudaGetErrorString(e));
+    return TT_ECUDA;
+  }
   return TT_OK;
 }
 
@@ -82,26 +111,8 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
   a.base = static_cast<char*>(ws);
   a.cap = need;
   Schedule s;
-  s.pbuf = a.take<double>(size_t(std::max<int64_t>(probe.pbuf_need, 1)));
-  GemmDesc* d_descs = a.take<GemmDesc>(std::max<size_t>(probe.descs.size(), 1));
-  s.cnt = a.take<int>(size_t(std::max<int64_t>(probe.cnt_need, 1)));
-  s.d_copies = a.take<Copy3>(std::max<size_t>(probe.copies.size(), 1));
-  s.tc_err = a.take<int>(1);
-  s.acc = a.take<long long>(size_t(std::max<int64_t>(probe.acc_need, 1)));
-  s.ex = a.take<int>(size_t(std::max<int64_t>(probe.ex_need, 1)));
-  s.planes = a.take<uint8_t>(size_t(std::max<int64_t>(probe.plane_need, 1)));
-  int rc = TT_OK;
-  {
-    cudaError_t e = cudaMemsetAsync(s.cnt, 0, size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.tc_err, 0, sizeof(int), st);
-    if (e == cudaSuccess && probe.acc_need > 0)
-      e = cudaMemsetAsync(s.acc, 0, size_t(probe.acc_need) * sizeof(long long), st);
-    if (e == cudaSuccess && probe.ex_need > 0) e = cudaMemsetAsync(s.ex, 0, size_t(probe.ex_need) * sizeof(int), st);
-    if (e != cudaSuccess) {
-      set_error(std::string("counter reset: ") + cudaGetErrorString(e));
-      rc = TT_ECUDA;
-    }
-  }
+  GemmDesc* d_descs = bind_schedule_regions(a, probe, s);
+  int rc = reset_schedule_regions(probe, s, st);
   if (rc == TT_OK) rc = build(a, s);
   if (rc == TT_OK && !s.descs.empty()) {
     cudaError_t e = cudaMemcpyAsync(d_descs, s.descs.data(), s.descs.size() * sizeof(GemmDesc),
@@ -122,6 +133,126 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
   for (size_t i = 0; rc == TT_OK && i < s.items.size(); ++i) rc = s.items[i](st, d_descs);
   if (owned) cudaFreeAsync(ws, st);
   return rc;
+}
+
+void plan_free(GraphPlan* gp) {
+  if (gp->exec) cudaGraphExecDestroy(gp->exec);
+  for (auto& q : gp->prof) {
+    cudaEventDestroy(q.e0);
+    cudaEventDestroy(q.e1);
+  }
+  gp->prof.clear();
+  if (gp->ws) cudaFree(gp->ws);
+  if (gp->pristine) cudaFree(gp->pristine);
+  if (gp->seed_dev) cudaFree(gp->seed_dev);
+  delete gp->sc;
+  *gp = GraphPlan{};
+}
+
+int plan_capture(const BuildFn& build, const StageFn& prologue, const StageFn& epilogue, cudaStream_t st,
+                 GraphPlan* gp) {
+  *gp = GraphPlan{};
+  Schedule probe;
+  size_t need = 0;
+  {
+    Arena a;
+    a.sizing = true;
+    TTR_TRY(build(a, probe));
+    need = schedule_bytes(a, probe);
+  }
+  auto fail = [&](int rc) {
+    plan_free(gp);
+    return rc;
+  };
+  if (cudaMalloc(&gp->ws, std::max<size_t>(need, 256)) != cudaSuccess ||
+      cudaMalloc(&gp->seed_dev, 256) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("plan: workspace allocation of " + std::to_string(need) + " bytes failed");
+    return fail(TT_ENOMEM);
+  }
+  Arena a;
+  a.sizing = false;
+  a.base = static_cast<char*>(gp->ws);
+  a.cap = need;
+  gp->sc = new Schedule;
+  Schedule& s = *gp->sc;
+  gp->d_descs = bind_schedule_regions(a, probe, s);
+  s.seed_dev = gp->seed_dev;
+  int rc = build(a, s);
+  if (rc != TT_OK) return fail(rc);
+  // static tables and the pristine copies of the uploads, before the capture
+  if (!s.descs.empty() &&
+      cudaMemcpy(gp->d_descs, s.descs.data(), s.descs.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    set_error("plan: descriptor upload failed");
+    return fail(TT_ECUDA);
+  }
+  if (!s.copies.empty() &&
+      cudaMemcpy(s.d_copies, s.copies.data(), s.copies.size() * sizeof(Copy3), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    set_error("plan: copy descriptor upload failed");
+    return fail(TT_ECUDA);
+  }
+  if (s.upload_total > 0) {
+    if (cudaMalloc(&gp->pristine, s.upload_total * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("plan: upload buffer allocation failed");
+      return fail(TT_ENOMEM);
+    }
+    size_t off = 0;
+    for (const auto& v : s.host_keep) {
+      if (!v.empty() &&
+          cudaMemcpy(gp->pristine + off, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("plan: upload copy failed");
+        return fail(TT_ECUDA);
+      }
+      off += v.size();
+    }
+    s.upload_dev = gp->pristine;
+  }
+  // capture: prologue, resets, the schedule, epilogue
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("plan: capture stream creation failed");
+    return fail(TT_ECUDA);
+  }
+  prof_capture_begin(&gp->prof);
+  cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (ce != cudaSuccess) {
+    prof_capture_end();
+    cudaStreamDestroy(cs);
+    set_error(std::string("plan: begin capture: ") + cudaGetErrorString(ce));
+    return fail(TT_ECUDA);
+  }
+  if (prologue) rc = prologue(cs);
+  if (rc == TT_OK) rc = reset_schedule_regions(probe, s, cs);
+  for (size_t i = 0; rc == TT_OK && i < s.items.size(); ++i) rc = s.items[i](cs, gp->d_descs);
+  if (rc == TT_OK && epilogue) rc = epilogue(cs);
+  cudaGraph_t graph = nullptr;
+  ce = cudaStreamEndCapture(cs, &graph);
+  gp->kernels = prof_capture_end();
+  cudaStreamDestroy(cs);
+  if (rc == TT_OK && ce != cudaSuccess) {
+    set_error(std::string("plan: end capture: ") + cudaGetErrorString(ce));
+    rc = TT_ECUDA;
+  }
+  if (rc == TT_OK) {
+    ce = cudaGraphInstantiate(&gp->exec, graph, 0);
+    if (ce != cudaSuccess) {
+      set_error(std::string("plan: graph instantiation: ") + cudaGetErrorString(ce));
+      rc = TT_ECUDA;
+    }
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  if (rc != TT_OK) return fail(rc);
+  (void)st;
+  return TT_OK;
+}
+
+int plan_replay(GraphPlan& gp, cudaStream_t st) {
+  TTR_CHECK_CUDA(cudaGraphLaunch(gp.exec, st));
+  return TT_OK;
 }
 
 std::vector<int64_t> clamp_rank_vector(const std::vector<int64_t>& I, const int64_t* r) {
@@ -270,8 +401,8 @@ static int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int
 // bf16 digits of the Algorithm 3 contractions in the mixed path (14 bits).
 constexpr int kSketchDigits = 2;
 
-static int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol,
-                          int digits, double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev) {
+int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol, int digits,
+                   double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev, size_t* coeff_off) {
   // digits == 0: every contraction in FP64. Else every contraction runs on the
   // tensor cores (emulated GEMM): the core updates and projections with
   // `digits` bf16 digits, the partial contractions of Algorithm 3 with
@@ -318,12 +449,16 @@ static int build_sum_rand(const SumProblem& P, const double* const* sketch_in, u
 
   // ---- set-up: counters, W_N = ones, M_0 = coefficients, sketch
   sc.add([=](cudaStream_t s) -> int { return fill_launch(W[N], S[N] * ell[N], 1.0, s); });
-  sc.upload(Mb[0], P.coeffs);
+  {
+    const size_t off = sc.upload(Mb[0], P.coeffs);
+    if (coeff_off) *coeff_off = off;
+  }
   if (!sketch_in) {
     for (int n = 2; n <= N; ++n) {
       double* dst = skw[n];
       const int64_t a = ell[n - 1], b = In(n), c = ell[n];
-      sc.add([=](cudaStream_t s) -> int { return sketch_launch(dst, a, b, c, n - 1, seed, s); });
+      const Schedule* scp = &sc;
+      sc.add([=](cudaStream_t s) -> int { return sketch_launch(dst, a, b, c, n - 1, seed, scp->seed_dev, s); });
     }
   }
 
@@ -381,6 +516,15 @@ static int build_sum_rand(const SumProblem& P, const double* const* sketch_in, u
   return TT_OK;
 }
 
+// Digits of the mixed path. Errors of the Algorithm 3 contractions compound over
+// the N-step recursion and enter the kept subspace directly when the sum is
+// redundant, so the per-product target is 1e-3 tol / N (1e-7 / N in fixed-rank
+// mode, an FP32-class target).
+int mixed_digits(double tol, int N) {
+  const double base = tol > 0.0 ? 1e-3 * tol : 1e-7;
+  return tc_digits_for_accuracy(base / double(std::max(N, 1)));
+}
+
 }  // namespace ttr
 
 using namespace ttr;
@@ -403,20 +547,11 @@ int tt_sketch_gaussian(int32_t N, const int64_t* dims, const int64_t* ells, uint
       return TT_EINVAL;
     }
   }
-  for (int n = 1; n <= N; ++n) TTR_TRY(sketch_launch(out[n - 1], ells[n - 1], dims[n - 1], ells[n], n - 1, seed, s));
+  for (int n = 1; n <= N; ++n) TTR_TRY(sketch_launch(out[n - 1], ells[n - 1], dims[n - 1], ells[n], n - 1, seed, nullptr, s));
   return TT_OK;
 }
 
-// Digits of the mixed path. Errors of the Algorithm 3 contractions compound over
-// the N-step recursion and enter the kept subspace directly when the sum is
-// redundant, so the per-product target is 1e-3 tol / N (1e-7 / N in fixed-rank
-// mode, an FP32-class target).
-static int mixed_digits(double tol, int N) {
-  const double base = tol > 0.0 ? 1e-3 * tol : 1e-7;
-  return tc_digits_for_accuracy(base / double(std::max(N, 1)));
-}
-
-int tt_mixed_digits(double tol, int32_t N) { return mixed_digits(tol, N); }
+int tt_mixed_digits(double tol, int32_t N) { return ttr::mixed_digits(tol, N); }
 
 __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, const int64_t* dims,
                                                          const int64_t* ranks,
@@ -443,7 +578,7 @@ __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, 
   std::vector<double*> out_v(N, nullptr);
   if (out) out_v.assign(out, out + N);
   BuildFn build = [&](Arena& ar, Schedule& sc) {
-    return build_sum_rand(P, sketch, seed, tol, digits, out_v.data(), ar, sc, &rk_dev);
+    return build_sum_rand(P, sketch, seed, tol, digits, out_v.data(), ar, sc, &rk_dev, nullptr);
   };
   if (size_only) return plan_workspace_bytes(build, size_only);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -88,7 +88,7 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
       double* d = ar.take<double>(ell[n - 1] * In(n) * ell[n]);
       L[n] = d;
       const int64_t a = ell[n - 1], b = In(n), c = ell[n];
-      sc.add([=](cudaStream_t s) -> int { return sketch_launch(d, a, b, c, n - 1, seed, s); });
+      sc.add([=](cudaStream_t s) -> int { return sketch_launch(d, a, b, c, n - 1, seed, nullptr, s); });
     }
     if (skR) {
       Rs[n] = skR[n - 1];
@@ -96,7 +96,7 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
       double* d = ar.take<double>(rho[n - 1] * In(n) * rho[n]);
       Rs[n] = d;
       const int64_t a = rho[n - 1], b = In(n), c = rho[n];
-      sc.add([=](cudaStream_t s) -> int { return sketch_launch(d, a, b, c, n - 1, seed + 1, s); });
+      sc.add([=](cudaStream_t s) -> int { return sketch_launch(d, a, b, c, n - 1, seed + 1, nullptr, s); });
     }
   }
   sc.add([=](cudaStream_t s) -> int {

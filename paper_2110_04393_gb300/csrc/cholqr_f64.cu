@@ -61,20 +61,33 @@ struct CqrPass {
                             // [4] the next pass multiplies by a first-order correction and ends the chain
 };
 
+// A usable pivot: positive, finite and normal, decided on the bit pattern
+// (integer operations instead of FP64 compares on the critical path).
+__device__ __forceinline__ bool pivot_ok(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned e = unsigned(b >> 52);            // sign and exponent
+  return e != 0 && e < 0x7FFu;                     // sign 0, exponent neither 0 nor all ones
+}
+
 // In-place right-looking Cholesky of G (k x k row-major, lower part) with
 // X := L^{-1} formed alongside; returns false on a non-positive pivot. FP64
 // issues a dependent operation only every ~65 cycles on GB300 and a reciprocal
-// square root takes ~430, so the 30-odd pivots are the critical path: every
-// step packs all of its trailing updates (the lower triangle of G below the
-// pivot and the rows of X below it) densely over threads 1.., while thread 0
-// only updates the next diagonal entry and takes its reciprocal square root.
-// Two block barriers per step. colj: k doubles of scratch.
+// square root takes ~400, so the pivots are the critical path. Thread 0 only
+// updates the next diagonal entry and takes its reciprocal square root; the
+// trailing updates (the lower triangle of G below the pivot and the rows of X
+// below it) are packed densely over the warps of the other three SM
+// sub-partitions (warp % 4 != 0), so no update queues on the FP64 pipe that
+// thread 0 uses. Two block barriers per step. colj: k doubles of scratch.
+// blockDim.x must be a multiple of 128.
 __device__ bool chol_with_inverse(double* G, double* X, double* colj, int k, double* s_rd, int* s_bad) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const bool worker = (warp & 3) != 0;
+  const int nwk = (nt >> 5) / 4 * 3 * 32;                      // worker threads
+  const int wid = ((warp >> 2) * 3 + (warp & 3) - 1) * 32 + lane;   // valid for workers
   for (int e = tid; e < k * k; e += nt) X[e] = (e % (k + 1) == 0) ? 1.0 : 0.0;
   if (tid == 0) {
     const double d = G[0];
-    const bool bad = !(d > 0.0) || !isfinite(d);
+    const bool bad = !pivot_ok(d);
     *s_bad = bad ? 1 : 0;
     *s_rd = bad ? 1.0 : rsqrt(d);
   }
@@ -84,10 +97,11 @@ __device__ bool chol_with_inverse(double* G, double* X, double* colj, int k, dou
     const double rd = *s_rd;
     const int n = k - j - 1;                      // rows / columns below the pivot
     // column j of L (scaled), the diagonal, and row j of X
-    for (int e = tid; e <= n + j; e += nt) {
-      if (e < n) colj[j + 1 + e] = G[(j + 1 + e) * k + j] * rd;
-      else X[j * k + (e - n)] *= rd;
-    }
+    if (worker)
+      for (int e = wid; e <= n + j; e += nwk) {
+        if (e < n) colj[j + 1 + e] = G[(j + 1 + e) * k + j] * rd;
+        else X[j * k + (e - n)] *= rd;
+      }
     if (tid == 0) G[j * k + j] *= rd;
     __syncthreads();
     const int ng = n * (n + 1) / 2, nx = n * (j + 1);
@@ -95,13 +109,13 @@ __device__ bool chol_with_inverse(double* G, double* X, double* colj, int k, dou
       if (n > 0) {
         const double d = fma(-colj[j + 1], colj[j + 1], G[(j + 1) * k + j + 1]);
         G[(j + 1) * k + j + 1] = d;
-        const bool bad = !(d > 0.0) || !isfinite(d);
+        const bool bad = !pivot_ok(d);
         *s_bad = bad ? 1 : 0;
         *s_rd = bad ? 1.0 : rsqrt(d);
       }
-    } else {
+    } else if (worker) {
       // entry 0 of the packed lower triangle is the next diagonal (thread 0's)
-      for (int e = tid; e < ng + nx; e += nt - 1) {
+      for (int e = wid + 1; e < ng + nx; e += nwk) {
         if (e < ng) {
           int ip = int((sqrtf(8.0f * float(e) + 1.0f) - 1.0f) * 0.5f);
           while (ip * (ip + 1) / 2 > e) --ip;
@@ -114,7 +128,7 @@ __device__ bool chol_with_inverse(double* G, double* X, double* colj, int k, dou
           X[i * k + c] = fma(-colj[i], X[j * k + c], X[i * k + c]);
         }
       }
-      for (int i = j + tid; i < k; i += nt - 1) G[i * k + j] = colj[i];   // rows j+1.. of column j
+      for (int i = j + 1 + wid; i < k; i += nwk) G[i * k + j] = colj[i];   // rows j+1.. of column j
     }
     __syncthreads();
   }

@@ -127,8 +127,9 @@ int copy3_launch(const Copy3* d_descs, int n, int64_t total, cudaStream_t s);
 // dst[0] := 1 if src[0] != 0 (device flags)
 int or_flag_launch(int* dst, const int* src, cudaStream_t s);
 int fill_launch(double* p, int64_t n, double v, cudaStream_t s);
+// seed_dev (may be null): read the seed from device memory instead (graph replays).
 int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, uint64_t seed,
-                  cudaStream_t s);
+                  const uint64_t* seed_dev, cudaStream_t s);
 // eps = tol * ||x||_F / sqrt(N-1) into *eps_out; x has n doubles.
 int norm_eps_launch(const double* x, int64_t n, double tol, int N, double* eps_out, cudaStream_t s);
 // Copy core (r0max, I, r1max) from src into dst compactly as (r0, I, r1) with

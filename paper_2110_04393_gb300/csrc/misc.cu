@@ -36,7 +36,13 @@ __device__ __forceinline__ double u52(uint32_t a, uint32_t b) {
   return (double(bits) + 0.5) * 0x1p-52;
 }
 
-__global__ void sketch_kernel(double* out, int64_t E, int core_index, uint32_t k0, uint32_t k1, double stdv) {
+__global__ void sketch_kernel(double* out, int64_t E, int core_index, uint32_t k0, uint32_t k1, double stdv,
+                              const uint64_t* seed_dev) {
+  if (seed_dev) {                       // seed of this run, written by the host before a graph replay
+    const uint64_t sd = *seed_dev;
+    k0 = uint32_t(sd);
+    k1 = uint32_t(sd >> 32);
+  }
   const int64_t npairs = (E + 1) / 2;
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < npairs;
        p += int64_t(gridDim.x) * blockDim.x) {
@@ -91,12 +97,13 @@ int fill_launch(double* p, int64_t n, double v, cudaStream_t s) {
   return TT_OK;
 }
 
-int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, uint64_t seed, cudaStream_t s) {
+int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, uint64_t seed,
+                  const uint64_t* seed_dev, cudaStream_t s) {
   const int64_t E = r0 * I * r1;
   if (E <= 0) return TT_OK;
   const double stdv = 1.0 / std::sqrt(double(r0) * double(I) * double(r1));
   sketch_kernel<<<grid_for((E + 1) / 2, 256), 256, 0, s>>>(out, E, core_index, uint32_t(seed),
-                                                            uint32_t(seed >> 32), stdv);
+                                                            uint32_t(seed >> 32), stdv, seed_dev);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
   return TT_OK;

@@ -73,17 +73,28 @@ struct Schedule {
     Copy3** base = &d_copies;
     items.push_back([=](cudaStream_t s, const GemmDesc*) { return copy3_launch(*base + off, n, t, s); });
   }
-  // H2D copy of host values kept alive by the schedule.
-  void upload(double* dst, std::vector<double> v) {
+  // Copy of host values into device memory, run every time the schedule runs.
+  // Eager runs copy from the kept host vector; a captured (graph) run copies
+  // from upload_dev, the pristine device copies laid out in upload order.
+  // Returns the upload's offset (doubles) in that layout.
+  size_t upload_total = 0;
+  const double* upload_dev = nullptr;
+  const uint64_t* seed_dev = nullptr;           // graph runs: sketch seed read on the device
+  size_t upload(double* dst, std::vector<double> v) {
     host_keep.push_back(std::move(v));
-    const std::vector<double>* src = &host_keep.back();
-    const size_t bytes = src->size() * sizeof(double);
-    const double* hp = src->data();
-    add([dst, hp, bytes](cudaStream_t s) -> int {
-      if (!dst || bytes == 0) return int(TT_OK);
-      TTR_CHECK_CUDA(cudaMemcpyAsync(dst, hp, bytes, cudaMemcpyHostToDevice, s));
+    const size_t idx = host_keep.size() - 1, off = upload_total, n = host_keep.back().size();
+    upload_total += n;
+    const Schedule* self = this;
+    add([self, dst, idx, off, n](cudaStream_t s) -> int {
+      if (!dst || n == 0) return int(TT_OK);
+      if (self->upload_dev)
+        TTR_CHECK_CUDA(cudaMemcpyAsync(dst, self->upload_dev + off, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      else
+        TTR_CHECK_CUDA(
+            cudaMemcpyAsync(dst, self->host_keep[idx].data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
       return int(TT_OK);
     });
+    return off;
   }
 };
 
@@ -105,5 +116,30 @@ inline GemmDesc gdesc(const double* A, int64_t a_rs, int64_t a_cs, const double*
 using BuildFn = std::function<int(Arena&, Schedule&)>;
 int plan_workspace_bytes(const BuildFn& build, size_t* bytes);
 int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStream_t s);
+
+// A schedule captured once into a CUDA graph and replayed (no host planning or
+// per-kernel launch cost on replay). The graph owns nothing: the plan keeps the
+// workspace, the schedule (whose items hold the device pointers) and the
+// pristine copies of the uploads. prologue / epilogue add nodes before and
+// after the schedule (may be empty).
+struct ProfPair {
+  cudaEvent_t e0, e1;
+  double flops;
+};
+struct GraphPlan {
+  Schedule* sc = nullptr;
+  void* ws = nullptr;
+  double* pristine = nullptr;
+  uint64_t* seed_dev = nullptr;
+  GemmDesc* d_descs = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;                 // kernel launches per replay
+  std::vector<ProfPair> prof;          // GEMM event pairs, when captured with profiling on
+};
+using StageFn = std::function<int(cudaStream_t)>;
+int plan_capture(const BuildFn& build, const StageFn& prologue, const StageFn& epilogue, cudaStream_t st,
+                 GraphPlan* gp);
+int plan_replay(GraphPlan& gp, cudaStream_t st);
+void plan_free(GraphPlan* gp);
 
 }  // namespace ttr

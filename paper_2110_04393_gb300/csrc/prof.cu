@@ -4,7 +4,7 @@
 #include <atomic>
 #include <mutex>
 
-#include "kernels.cuh"
+#include "plan.cuh"
 #include "prof.cuh"
 
 namespace ttr {
@@ -23,11 +23,63 @@ Prof& P() {
   return p;
 }
 std::atomic<int64_t> g_launches{0};
+thread_local std::vector<ProfPair>* t_sink = nullptr;
+thread_local int64_t t_sink_launches = 0;
+thread_local cudaEvent_t t_sink_e0 = nullptr;
+double g_replay_ms = 0.0;       // guarded by P().mu
 }  // namespace
 
-void prof_count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void prof_count_launch(int n) {
+  if (t_sink) {
+    t_sink_launches += n;
+    return;
+  }
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+
+void prof_capture_begin(std::vector<ProfPair>* sink) {
+  t_sink = sink;
+  t_sink_launches = 0;
+}
+int64_t prof_capture_end() {
+  t_sink = nullptr;
+  return t_sink_launches;
+}
+bool prof_on() {
+  Prof& p = P();
+  std::lock_guard<std::mutex> g(p.mu);
+  return p.on;
+}
+
+int prof_replayed(const std::vector<ProfPair>& pairs, int64_t launches) {
+  Prof& p = P();
+  std::lock_guard<std::mutex> g(p.mu);
+  if (!p.on) return TT_OK;
+  for (const auto& q : pairs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, q.e0, q.e1) != cudaSuccess) {
+      set_error("profiling: elapsed time of a replayed event pair failed");
+      return TT_ECUDA;
+    }
+    g_replay_ms += t;
+    p.flops += q.flops;
+    p.gemm_launches += 1;
+  }
+  g_launches.fetch_add(launches, std::memory_order_relaxed);
+  return TT_OK;
+}
 
 bool prof_gemm_begin(cudaStream_t s, cudaEvent_t* e0) {
+  if (t_sink) {
+    if (!prof_on()) return false;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+    // an event node of the graph (a plain record in a capture is only a dependency)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    t_sink_e0 = e;
+    *e0 = e;
+    return true;
+  }
   Prof& p = P();
   std::lock_guard<std::mutex> g(p.mu);
   if (!p.on) return false;
@@ -42,6 +94,13 @@ bool prof_gemm_begin(cudaStream_t s, cudaEvent_t* e0) {
 }
 
 void prof_gemm_end(cudaStream_t s, double flops) {
+  if (t_sink) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    t_sink->push_back(ProfPair{t_sink_e0, e, flops});
+    return;
+  }
   Prof& p = P();
   std::lock_guard<std::mutex> g(p.mu);
   cudaEventRecord(p.pool[p.used + 1], s);
@@ -69,6 +128,7 @@ int tt_prof_reset(void) {
   p.used = 0;
   p.flops = 0.0;
   p.gemm_launches = 0;
+  g_replay_ms = 0.0;
   g_launches.store(0);
   return TT_OK;
 }
@@ -89,7 +149,7 @@ int tt_prof_read(double* gemm_ms, double* gemm_flops, int64_t* gemm_launches, in
     }
     ms += t;
   }
-  if (gemm_ms) *gemm_ms = ms;
+  if (gemm_ms) *gemm_ms = ms + g_replay_ms;
   if (gemm_flops) *gemm_flops = p.flops;
   if (gemm_launches) *gemm_launches = p.gemm_launches;
   if (kernel_launches) *kernel_launches = g_launches.load();

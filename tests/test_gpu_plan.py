@@ -1,0 +1,51 @@
+"""Captured plans (CUDA graph replay) of the sum rounding against the eager
+entry point: bit-wise equal results for the same seed, over several replays
+with new data, seeds and coefficients, in both precisions and both modes."""
+import pytest
+import torch
+
+import synth
+from tests._gpu import to_dev, const_ranks
+
+import paper_2110_04393_gb300 as tt
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [40, 50, 45, 60, 40, 55]
+RANKS = [6, 9, 4, 7]
+
+
+def _summands(seed):
+    N = len(DIMS)
+    return [to_dev(synth.gaussian_tt(synth.rng_for(seed, j), DIMS, const_ranks(N, r))) for j, r in enumerate(RANKS)]
+
+
+def _same(a, b):
+    return len(a) == len(b) and all(x.shape == y.shape and torch.equal(x, y) for x, y in zip(a, b))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("tol", [0.0, 1e-8])
+def test_plan_replays_match_eager_bitwise(precision, tol):
+    N = len(DIMS)
+    ell = const_ranks(N, 20)
+    ranks = [const_ranks(N, r) for r in RANKS]
+    plan = tt.SumRoundingPlan(DIMS, ranks, ell, tol=tol, precision=precision)
+    assert plan.launches > 0
+    for rep, (dseed, sseed) in enumerate([(300, 5), (301, 9), (300, 5)]):
+        Yd = _summands(dseed)
+        coeffs = None if rep != 1 else [1.0, -0.5, 2.0, 0.25]
+        Xp = plan(Yd, seed=sseed, coeffs=coeffs)
+        Xe = tt.tt_round_sum_rand(Yd, ell, seed=sseed, tol=tol, coeffs=coeffs, precision=precision)
+        torch.cuda.synchronize()
+        assert _same(Xp, Xe), (rep, [tuple(x.shape) for x in Xp], [tuple(x.shape) for x in Xe])
+    plan.close()
+
+
+def test_plan_rejects_mismatched_summands():
+    N = len(DIMS)
+    plan = tt.SumRoundingPlan(DIMS, [const_ranks(N, r) for r in RANKS], const_ranks(N, 20), tol=1e-8)
+    Yd = _summands(302)
+    with pytest.raises(ValueError):
+        plan(Yd[:3])
+    plan.close()
