@@ -127,6 +127,26 @@ size_t tt_round_sum_rand_workspace(int32_t N, int32_t K, const int64_t* dims, co
                                    const int64_t* ells, double tol, int32_t precision);
 
 /*
+ * tt_round_rand_backward -- reverse-mode derivative of fixed-sketch
+ * Randomize-then-Orthogonalize (Algorithm 5 with the sketch Omega held fixed,
+ * fixed target ranks, no tolerance truncation). The paper gives no derivative;
+ * this is the chain rule through Algorithm 5 (thin-QR backward with the R
+ * factor not differentiated) and Algorithm 3, in FP64. Given the forward input
+ * Y (N, dims, ranks, cores as in tt_round_rand), the clamped target ranks of
+ * ells (N+1), the sketch (N device cores (l_{n-1}, I_n, l_n); core 1 unused)
+ * and xbar = dL/dX_hat for the output cores X_hat of tt_round_rand with that
+ * sketch (N device cores (l_{n-1}, I_n, l_n)), writes ybar = dL/dY (N device
+ * cores shaped like Y, overwritten). The forward quantities are recomputed
+ * (the partial contractions W_n included), not kept from the forward call.
+ * workspace: as tt_round_rand, sized by tt_round_rand_backward_workspace.
+ * Errors: TT_EINVAL, TT_EUNSUPPORTED (a rank above 1024), TT_ENOMEM, TT_ECUDA.
+ */
+int tt_round_rand_backward(int32_t N, const int64_t* dims, const int64_t* ranks, const double* const* cores,
+                           const int64_t* ells, const double* const* sketch, const double* const* xbar,
+                           double* const* ybar, void* workspace, size_t workspace_bytes, void* stream);
+size_t tt_round_rand_backward_workspace(int32_t N, const int64_t* dims, const int64_t* ranks, const int64_t* ells);
+
+/*
  * Captured plans of tt_round_sum_rand (an execution mechanism, no counterpart
  * in the paper). tt_sum_plan_create fixes N, K, dims, ranks (K x (N+1)), the
  * sketch ranks ells (N+1), tol and precision, builds the whole schedule of the

@@ -151,6 +151,62 @@ def tt_round_sum_rand(summands, ells, *, tol=0.0, sketch=None, seed=0, coeffs=No
     return res
 
 
+def tt_round_rand_backward(cores, ells, sketch, xbar, *, workspace=None, stream=None):
+    """dL/dY for fixed-sketch RandOrth (Algorithm 5, fixed ranks) given
+    xbar = dL/dX_hat for its output cores; returns tensors shaped like cores."""
+    N = len(cores)
+    device = cores[0].device
+    dims = [int(c.shape[1]) for c in cores]
+    ranks = [int(cores[0].shape[0])] + [int(c.shape[2]) for c in cores]
+    for n, c in enumerate(cores):
+        _check_core(c, f"core {n}")
+    ell = clamp_ranks(dims, ells)
+    for n in range(N):
+        want = (ell[n], dims[n], ell[n + 1])
+        _check_core(xbar[n], f"xbar core {n}")
+        if tuple(xbar[n].shape) != want:
+            raise ValueError(f"xbar core {n} has shape {tuple(xbar[n].shape)}, expected {want}")
+        if n > 0:
+            _check_core(sketch[n], f"sketch core {n}")
+            if tuple(sketch[n].shape) != want:
+                raise ValueError(f"sketch core {n} has shape {tuple(sketch[n].shape)}, expected {want}")
+    sk = [sketch[n] if n > 0 else xbar[0] for n in range(N)]     # core 1 of the sketch is not used
+    ybar = [torch.empty_like(c) for c in cores]
+    L = nat.lib()
+    dims_a, ranks_a, ell_a = _i64(dims), _i64(ranks), _i64(ell)
+    nbytes = L.tt_round_rand_backward_workspace(N, dims_a, ranks_a, ell_a)
+    workspace, wp, wb = _workspace(nbytes, device, workspace)
+    _check(L.tt_round_rand_backward(N, dims_a, ranks_a, _ptrs(cores), ell_a, _ptrs(sk), _ptrs(xbar), _ptrs(ybar),
+                                    wp, wb, _stream(stream, device)))
+    return ybar
+
+
+class _RandOrthFixedSketch(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, ell, sketch, *cores):
+        out = tt_round_rand(list(cores), ell, sketch=sketch, tol=0.0, precision="fp64")
+        ctx.save_for_backward(*cores)
+        ctx.ell = list(ell)
+        ctx.sketch = sketch
+        return tuple(o.contiguous() for o in out)
+
+    @staticmethod
+    def backward(ctx, *gout):
+        cores = ctx.saved_tensors
+        ell = clamp_ranks([int(c.shape[1]) for c in cores], ctx.ell)
+        xb = [g.contiguous() if g is not None else
+              torch.zeros((ell[n], cores[n].shape[1], ell[n + 1]), dtype=torch.float64, device=cores[0].device)
+              for n, g in enumerate(gout)]
+        ybar = tt_round_rand_backward(list(cores), ctx.ell, ctx.sketch, xb)
+        return (None, None, *ybar)
+
+
+def round_rand_fixed_sketch(cores, ells, sketch):
+    """Differentiable fixed-sketch RandOrth (Algorithm 5, fixed ranks, FP64):
+    forward by tt_round_rand, backward by tt_round_rand_backward."""
+    return list(_RandOrthFixedSketch.apply(list(ells), list(sketch), *cores))
+
+
 class SumRoundingPlan:
     """Captured plan of tt_round_sum_rand for fixed mode sizes, summand ranks,
     sketch ranks, tolerance and precision; calling it replays the CUDA graph on

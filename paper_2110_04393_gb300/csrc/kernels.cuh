@@ -127,6 +127,10 @@ int copy3_launch(const Copy3* d_descs, int n, int64_t total, cudaStream_t s);
 // dst[0] := 1 if src[0] != 0 (device flags)
 int or_flag_launch(int* dst, const int* src, cudaStream_t s);
 int fill_launch(double* p, int64_t n, double v, cudaStream_t s);
+// Adjoint helpers: X = T^{-1} (upper triangular, k x k), A := tril(A) + tril(A, -1)^T, y += x.
+int triu_inverse_launch(const double* T, double* X, int k, cudaStream_t s);
+int sym_lower_launch(double* A, int k, cudaStream_t s);
+int axpy_launch(double* y, const double* x, int64_t n, cudaStream_t s);
 // seed_dev (may be null): read the seed from device memory instead (graph replays).
 int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, uint64_t seed,
                   const uint64_t* seed_dev, cudaStream_t s);

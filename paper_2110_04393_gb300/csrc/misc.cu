@@ -181,3 +181,63 @@ int or_flag_launch(int* dst, const int* src, cudaStream_t s) {
   return TT_OK;
 }
 }  // namespace ttr
+
+// ---------------------------------------------------------------------------
+// Small dense helpers of the fixed-sketch adjoint.
+namespace ttr {
+namespace {
+
+// X = T^{-1} for an upper-triangular k x k row-major T: one column per thread,
+// back substitution.
+__global__ void triu_inverse_kernel(const double* T, double* X, int k) {
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int i = k - 1; i > c; --i) X[i * k + c] = 0.0;
+    X[c * k + c] = 1.0 / T[c * k + c];
+    for (int i = c - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int j = i + 1; j <= c; ++j) s = fma(T[i * k + j], X[j * k + c], s);
+      X[i * k + c] = -s / T[i * k + i];
+    }
+  }
+}
+
+// A := tril(A) + tril(A, -1)^T in place (k x k row-major); only the strict upper part is written.
+__global__ void sym_lower_kernel(double* A, int k) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < k * k; idx += gridDim.x * blockDim.x) {
+    const int i = idx / k, j = idx - i * k;
+    if (j > i) A[idx] = A[j * k + i];
+  }
+}
+
+__global__ void axpy_kernel(double* y, const double* x, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] += x[i];
+}
+
+}  // namespace
+
+int triu_inverse_launch(const double* T, double* X, int k, cudaStream_t s) {
+  if (k <= 0 || !T || !X) return TT_OK;
+  triu_inverse_kernel<<<1, 256, 0, s>>>(T, X, k);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+int sym_lower_launch(double* A, int k, cudaStream_t s) {
+  if (k <= 0 || !A) return TT_OK;
+  sym_lower_kernel<<<grid_for(int64_t(k) * k, 256), 256, 0, s>>>(A, k);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+int axpy_launch(double* y, const double* x, int64_t n, cudaStream_t s) {
+  if (n <= 0 || !y || !x) return TT_OK;
+  axpy_kernel<<<grid_for(n, 256), 256, 0, s>>>(y, x, n);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+}  // namespace ttr
