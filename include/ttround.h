@@ -177,6 +177,35 @@ int tt_sum_plan_destroy(tt_sum_plan* plan);
 int64_t tt_sum_plan_launches(const tt_sum_plan* plan);
 
 /*
+ * Batched plans: B independent sum roundings (the uneven sums of TT-GMRES,
+ * Section 4.2) in one CUDA graph. Problem b (its N, K, dims, ranks K x (N+1),
+ * ells N+1 and tol, as for tt_sum_plan_create) runs on chain b mod width of the
+ * graph; the chains are independent, so the kernels of different problems run
+ * concurrently and fill each other's idle SMs. width (1..B) is a schedule
+ * parameter that changes no result (tt_batch_plan_* callers may tune it).
+ * tt_batch_plan_run: cores = the problems' core pointer arrays concatenated
+ * (problem b: K_b*N_b device pointers as in tt_sum_plan_run), seeds = B sketch
+ * seeds (host; NULL = 0, 1, ..., B-1), out = the problems' N_b output pointers
+ * concatenated, out_ranks = the problems' N_b+1 ranks concatenated (host).
+ * Every problem's result is bit-wise that of tt_round_sum_rand with its seed.
+ * The call waits for the stream only if some problem has tol > 0.
+ */
+typedef struct {
+  int32_t N, K;
+  const int64_t* dims;     /* N */
+  const int64_t* ranks;    /* K*(N+1), summand-major */
+  const int64_t* ells;     /* N+1 */
+  double tol;              /* <= 0: fixed ranks */
+} tt_sum_problem;
+typedef struct tt_batch_plan tt_batch_plan;
+int tt_batch_plan_create(int32_t B, const tt_sum_problem* probs, int32_t precision, int32_t width,
+                         tt_batch_plan** plan, void* stream);
+int tt_batch_plan_run(tt_batch_plan* plan, const double* const* cores, const uint64_t* seeds, double* const* out,
+                      int64_t* out_ranks, void* stream);
+int tt_batch_plan_destroy(tt_batch_plan* plan);
+int64_t tt_batch_plan_launches(const tt_batch_plan* plan);
+
+/*
  * tt_round_rand -- Algorithm 5 (Randomize-then-Orthogonalize, Section 3.2):
  * the single-tensor case K = 1 of tt_round_sum_rand, same arguments with
  * ranks of length N+1 and N core pointers.

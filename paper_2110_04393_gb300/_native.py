@@ -46,6 +46,10 @@ SIGNATURES = {
     "tt_sum_plan_run": (c_i32, [c_vp, P_vp, P_dbl, c_u64, P_vp, P_i64, c_vp]),
     "tt_sum_plan_destroy": (c_i32, [c_vp]),
     "tt_sum_plan_launches": (c_i64, [c_vp]),
+    "tt_batch_plan_create": (c_i32, [c_i32, c_vp, c_i32, c_i32, P_vp, c_vp]),
+    "tt_batch_plan_run": (c_i32, [c_vp, P_vp, c_vp, P_vp, P_i64, c_vp]),
+    "tt_batch_plan_destroy": (c_i32, [c_vp]),
+    "tt_batch_plan_launches": (c_i64, [c_vp]),
     "tt_gemm_emulated_f64": (c_i32, [c_i64, c_i64, c_i64, c_dbl, c_vp, c_i64, c_i64, c_vp, c_i64, c_i64, c_dbl,
                                      c_vp, c_i64, c_i64, c_i32, c_vp, c_size, c_vp]),
     "tt_selftest_tcgen05_bf16": (c_i32, [c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),

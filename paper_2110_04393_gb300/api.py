@@ -258,6 +258,112 @@ class SumRoundingPlan:
             pass
 
 
+class _SumProblem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("K", ctypes.c_int32), ("dims", ctypes.POINTER(ctypes.c_int64)),
+                ("ranks", ctypes.POINTER(ctypes.c_int64)), ("ells", ctypes.POINTER(ctypes.c_int64)),
+                ("tol", ctypes.c_double)]
+
+
+class BatchRoundingPlan:
+    """B independent sum roundings captured in one CUDA graph (problem b on
+    chain b mod width). problems: list of dicts with keys dims, summand_ranks
+    (K lists of N+1 ranks), ells (N+1) and optionally tol (default 0)."""
+
+    def __init__(self, problems, *, precision="mixed", width=1, device=None, stream=None):
+        self.device = torch.device(device or "cuda")
+        self.problems = []
+        keep = []
+        arr = (_SumProblem * len(problems))()
+        for b, pr in enumerate(problems):
+            dims = [int(d) for d in pr["dims"]]
+            R = [[int(r) for r in Rj] for Rj in pr["summand_ranks"]]
+            ell = clamp_ranks(dims, pr["ells"])
+            tol = float(pr.get("tol", 0.0))
+            a_d, a_r, a_e = _i64(dims), _i64([r for Rj in R for r in Rj]), _i64(ell)
+            keep += [a_d, a_r, a_e]
+            arr[b] = _SumProblem(len(dims), len(R), a_d, a_r, a_e, tol)
+            self.problems.append(dict(dims=dims, summand_ranks=R, ell=ell, tol=tol))
+        self.width = int(width)
+        h = ctypes.c_void_p()
+        _check(nat.lib().tt_batch_plan_create(len(problems), ctypes.cast(arr, ctypes.c_void_p), _PREC[precision],
+                                              self.width, ctypes.byref(h), _stream(stream, self.device)))
+        self._h = h
+
+    @property
+    def launches(self):
+        return int(nat.lib().tt_batch_plan_launches(self._h))
+
+    def __call__(self, batch, *, seeds=None, out=None, stream=None):
+        """batch: per problem, its list of K summand TTs (device cores)."""
+        if len(batch) != len(self.problems):
+            raise ValueError("batch size differs from the plan's")
+        flat, outs, nrk = [], [], 0
+        for b, (summands, pr) in enumerate(zip(batch, self.problems)):
+            N, K, dims, ranks, fl = _sum_args(summands)
+            if dims != pr["dims"] or ranks != [r for Rj in pr["summand_ranks"] for r in Rj]:
+                raise ValueError(f"problem {b} does not match the plan")
+            flat += fl
+            ell = pr["ell"]
+            o = out[b] if out is not None else [
+                torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float64, device=self.device) for n in range(N)]
+            outs.append(o)
+            nrk += N + 1
+        sd = None
+        if seeds is not None:
+            sd = (ctypes.c_uint64 * len(seeds))(*[int(x) for x in seeds])
+        rk = (ctypes.c_int64 * nrk)()
+        _check(nat.lib().tt_batch_plan_run(self._h, _ptrs(flat), ctypes.cast(sd, ctypes.c_void_p) if sd else None,
+                                           _ptrs([c for o in outs for c in o]), rk, _stream(stream, self.device)))
+        res, i = [], 0
+        for o, pr in zip(outs, self.problems):
+            N, dims = len(pr["dims"]), pr["dims"]
+            r = [int(rk[i + n]) for n in range(N + 1)]
+            i += N + 1
+            res.append([o[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)])
+        return res
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.lib().tt_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_TUNED = {}
+
+
+def tune_batch_width(problems, batch, *, precision="mixed", candidates=(8, 32, 128), reps=2, stream=None):
+    """Autotuner of the batched schedule: captures the batch at each candidate
+    width, times `reps` replays with CUDA events and returns (best width,
+    {width: ms}); the choice is cached per problem set in this process."""
+    key = (precision, tuple((tuple(p["dims"]), tuple(tuple(r) for r in p["summand_ranks"]), tuple(p["ells"]),
+                             float(p.get("tol", 0.0))) for p in problems))
+    if key in _TUNED:
+        return _TUNED[key]
+    B = len(problems)
+    times = {}
+    for w in sorted({max(1, min(int(c), B)) for c in candidates}):
+        plan = BatchRoundingPlan(problems, precision=precision, width=w)
+        plan(batch)                                   # warm-up replay
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            plan(batch)
+        e1.record()
+        torch.cuda.synchronize()
+        times[w] = e0.elapsed_time(e1) / reps
+        plan.close()
+    best = min(times, key=times.get)
+    _TUNED[key] = (best, times)
+    return _TUNED[key]
+
+
 def _sum_args(summands):
     N = len(summands[0])
     dims = [int(c.shape[1]) for c in summands[0]]

@@ -61,12 +61,10 @@ std::vector<CopyBlock> copy_blocks(const std::vector<int64_t>& sizes) {
   return v;
 }
 
-}  // namespace
-}  // namespace ttr
-
-using namespace ttr;
-
-struct tt_sum_plan {
+// One sum rounding inside a graph: plan-owned inputs / outputs, the prepared
+// schedule and the copy tables; its run arguments live at stage_off in a
+// staging block shared by all problems of the graph.
+struct SumUnit {
   SumProblem P;
   double tol = 0.0;
   int digits = 0;
@@ -76,7 +74,6 @@ struct tt_sum_plan {
   int64_t* rk_dev = nullptr;
   size_t coeff_off = 0;
   GraphPlan gp;
-  // static device tables: gather / scatter blocks, offsets, mode sizes
   void* tables = nullptr;
   CopyBlock* gblocks = nullptr;
   CopyBlock* sblocks = nullptr;
@@ -84,55 +81,29 @@ struct tt_sum_plan {
   int64_t* out_off = nullptr;
   int64_t* dims = nullptr;
   int ngb = 0, nsb = 0;
-  // per-run arguments: [src pointers K*N | dst pointers N | seed | coefficients K]
-  size_t stage_bytes = 0;
-  void* d_stage = nullptr;
-  void* h_stage = nullptr;
-  int64_t* h_rk = nullptr;
-  cudaEvent_t staged = nullptr;
+  size_t stage_off = 0;
 };
 
-static void sum_plan_free(tt_sum_plan* p) {
-  if (!p) return;
-  plan_free(&p->gp);
-  if (p->in_buf) cudaFree(p->in_buf);
-  if (p->out_buf) cudaFree(p->out_buf);
-  if (p->tables) cudaFree(p->tables);
-  if (p->d_stage) cudaFree(p->d_stage);
-  if (p->h_stage) cudaFreeHost(p->h_stage);
-  if (p->h_rk) cudaFreeHost(p->h_rk);
-  if (p->staged) cudaEventDestroy(p->staged);
-  delete p;
+size_t unit_stage_bytes(int N, int K) {
+  return sizeof(double*) * (size_t(K) * N + N) + sizeof(uint64_t) + sizeof(double) * K;
 }
 
-extern "C" {
+void unit_free(SumUnit* u) {
+  plan_free(&u->gp);
+  if (u->in_buf) cudaFree(u->in_buf);
+  if (u->out_buf) cudaFree(u->out_buf);
+  if (u->tables) cudaFree(u->tables);
+  u->in_buf = u->out_buf = nullptr;
+  u->tables = nullptr;
+}
 
-int tt_sum_plan_create(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const int64_t* ells,
-                       double tol, int32_t precision, tt_sum_plan** plan, void* stream) {
-  if (!plan) {
-    set_error("tt_sum_plan_create: null plan pointer");
-    return TT_EINVAL;
-  }
-  *plan = nullptr;
-  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
-    set_error("tt_sum_plan_create: unknown precision mode");
-    return TT_EINVAL;
-  }
-  tt_sum_plan* p = new tt_sum_plan;
-  int rc = validate_sum(N, K, dims, ranks, nullptr, nullptr, ells, false, &p->P);
-  if (rc != TT_OK) {
-    delete p;
-    return rc;
-  }
-  SumProblem& P = p->P;
-  p->tol = tol;
-  p->digits = (precision == TT_PREC_MIXED) ? mixed_digits(tol, N) : 0;
-  auto fail = [&](int code, const std::string& msg) {
-    if (!msg.empty()) set_error("tt_sum_plan_create: " + msg);
-    sum_plan_free(p);
-    return code;
-  };
-  // plan-owned inputs (summand cores packed) and outputs (capacity l_{n-1} I_n l_n)
+// Validates, allocates, uploads the copy tables and prepares the schedule.
+int unit_init(SumUnit* u, int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const int64_t* ells,
+              double tol, int32_t precision) {
+  TTR_TRY(validate_sum(N, K, dims, ranks, nullptr, nullptr, ells, false, &u->P));
+  SumProblem& P = u->P;
+  u->tol = tol;
+  u->digits = (precision == TT_PREC_MIXED) ? mixed_digits(tol, N) : 0;
   std::vector<int64_t> in_sizes, in_off, out_sizes, out_off;
   int64_t tot = 0;
   for (int j = 0; j < K; ++j)
@@ -149,90 +120,264 @@ int tt_sum_plan_create(int32_t N, int32_t K, const int64_t* dims, const int64_t*
     tot += out_sizes.back();
   }
   const int64_t out_total = tot;
-  if (cudaMalloc(&p->in_buf, sizeof(double) * std::max<int64_t>(in_total, 1)) != cudaSuccess ||
-      cudaMalloc(&p->out_buf, sizeof(double) * std::max<int64_t>(out_total, 1)) != cudaSuccess) {
+  if (cudaMalloc(&u->in_buf, sizeof(double) * std::max<int64_t>(in_total, 1)) != cudaSuccess ||
+      cudaMalloc(&u->out_buf, sizeof(double) * std::max<int64_t>(out_total, 1)) != cudaSuccess) {
     cudaGetLastError();
-    return fail(TT_ENOMEM, "buffer allocation failed");
+    set_error("plan: buffer allocation failed");
+    return TT_ENOMEM;
   }
   P.cores.assign(size_t(K) * N, nullptr);
   for (int j = 0; j < K; ++j)
-    for (int n = 1; n <= N; ++n) P.cores[size_t(j) * N + (n - 1)] = p->in_buf + in_off[size_t(j) * N + (n - 1)];
-  p->outs.resize(N);
-  for (int n = 0; n < N; ++n) p->outs[n] = p->out_buf + out_off[n];
-
-  // static tables
+    for (int n = 1; n <= N; ++n) P.cores[size_t(j) * N + (n - 1)] = u->in_buf + in_off[size_t(j) * N + (n - 1)];
+  u->outs.resize(N);
+  for (int n = 0; n < N; ++n) u->outs[n] = u->out_buf + out_off[n];
   const auto gb = copy_blocks(in_sizes), sb = copy_blocks(out_sizes);
-  p->ngb = int(gb.size());
-  p->nsb = int(sb.size());
-  const size_t tb_bytes = align256(sizeof(CopyBlock) * std::max<size_t>(gb.size(), 1)) +
-                          align256(sizeof(CopyBlock) * std::max<size_t>(sb.size(), 1)) +
-                          align256(sizeof(int64_t) * in_off.size()) + align256(sizeof(int64_t) * out_off.size()) +
-                          align256(sizeof(int64_t) * N);
-  if (cudaMalloc(&p->tables, tb_bytes) != cudaSuccess) {
+  u->ngb = int(gb.size());
+  u->nsb = int(sb.size());
+  const size_t gbb = align256(sizeof(CopyBlock) * std::max<size_t>(gb.size(), 1));
+  const size_t sbb = align256(sizeof(CopyBlock) * std::max<size_t>(sb.size(), 1));
+  const size_t tb_bytes = gbb + sbb + align256(sizeof(int64_t) * in_off.size()) +
+                          align256(sizeof(int64_t) * out_off.size()) + align256(sizeof(int64_t) * N);
+  if (cudaMalloc(&u->tables, tb_bytes) != cudaSuccess) {
     cudaGetLastError();
-    return fail(TT_ENOMEM, "table allocation failed");
+    set_error("plan: table allocation failed");
+    return TT_ENOMEM;
   }
-  char* t = static_cast<char*>(p->tables);
-  p->gblocks = reinterpret_cast<CopyBlock*>(t);
-  t += align256(sizeof(CopyBlock) * std::max<size_t>(gb.size(), 1));
-  p->sblocks = reinterpret_cast<CopyBlock*>(t);
-  t += align256(sizeof(CopyBlock) * std::max<size_t>(sb.size(), 1));
-  p->in_off = reinterpret_cast<int64_t*>(t);
+  char* t = static_cast<char*>(u->tables);
+  u->gblocks = reinterpret_cast<CopyBlock*>(t);
+  t += gbb;
+  u->sblocks = reinterpret_cast<CopyBlock*>(t);
+  t += sbb;
+  u->in_off = reinterpret_cast<int64_t*>(t);
   t += align256(sizeof(int64_t) * in_off.size());
-  p->out_off = reinterpret_cast<int64_t*>(t);
+  u->out_off = reinterpret_cast<int64_t*>(t);
   t += align256(sizeof(int64_t) * out_off.size());
-  p->dims = reinterpret_cast<int64_t*>(t);
-  if ((!gb.empty() && cudaMemcpy(p->gblocks, gb.data(), sizeof(CopyBlock) * gb.size(), cudaMemcpyHostToDevice)) ||
-      (!sb.empty() && cudaMemcpy(p->sblocks, sb.data(), sizeof(CopyBlock) * sb.size(), cudaMemcpyHostToDevice)) ||
-      cudaMemcpy(p->in_off, in_off.data(), sizeof(int64_t) * in_off.size(), cudaMemcpyHostToDevice) ||
-      cudaMemcpy(p->out_off, out_off.data(), sizeof(int64_t) * out_off.size(), cudaMemcpyHostToDevice) ||
-      cudaMemcpy(p->dims, P.I.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice))
-    return fail(TT_ECUDA, "table upload failed");
-
-  // per-run staging
-  p->stage_bytes = sizeof(double*) * (size_t(K) * N + N) + sizeof(uint64_t) + sizeof(double) * K;
-  if (cudaMalloc(&p->d_stage, p->stage_bytes) != cudaSuccess ||
-      cudaMallocHost(&p->h_stage, p->stage_bytes) != cudaSuccess ||
-      cudaMallocHost(reinterpret_cast<void**>(&p->h_rk), sizeof(int64_t) * (N + 1)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->staged, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(TT_ENOMEM, "staging allocation failed");
+  u->dims = reinterpret_cast<int64_t*>(t);
+  if ((!gb.empty() && cudaMemcpy(u->gblocks, gb.data(), sizeof(CopyBlock) * gb.size(), cudaMemcpyHostToDevice)) ||
+      (!sb.empty() && cudaMemcpy(u->sblocks, sb.data(), sizeof(CopyBlock) * sb.size(), cudaMemcpyHostToDevice)) ||
+      cudaMemcpy(u->in_off, in_off.data(), sizeof(int64_t) * in_off.size(), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(u->out_off, out_off.data(), sizeof(int64_t) * out_off.size(), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(u->dims, P.I.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice)) {
+    set_error("plan: table upload failed");
+    return TT_ECUDA;
   }
-  std::memset(p->h_stage, 0, p->stage_bytes);
-  char* ds = static_cast<char*>(p->d_stage);
-  const double* const* d_src = reinterpret_cast<const double* const*>(ds);
-  double* const* d_dst = reinterpret_cast<double* const*>(ds + sizeof(double*) * size_t(K) * N);
-  const uint64_t* d_seed = reinterpret_cast<const uint64_t*>(ds + sizeof(double*) * (size_t(K) * N + N));
-  const double* d_coeffs = reinterpret_cast<const double*>(ds + sizeof(double*) * (size_t(K) * N + N) + 8);
+  BuildFn build = [u](Arena& ar, Schedule& sc) {
+    return build_sum_rand(u->P, nullptr, 0, u->tol, u->digits, u->outs.data(), ar, sc, &u->rk_dev, &u->coeff_off);
+  };
+  return plan_prepare(build, &u->gp);
+}
 
-  BuildFn build = [p](Arena& ar, Schedule& sc) {
-    return build_sum_rand(p->P, nullptr, 0, p->tol, p->digits, p->outs.data(), ar, sc, &p->rk_dev, &p->coeff_off);
-  };
-  GraphPlan* gpp = &p->gp;
-  const int Kc = K;
-  StageFn prologue = [p, gpp, d_src, d_seed, d_coeffs, Kc](cudaStream_t s) -> int {
-    TTR_CHECK_CUDA(cudaMemcpyAsync(gpp->seed_dev, d_seed, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-    if (gpp->pristine)
-      TTR_CHECK_CUDA(cudaMemcpyAsync(gpp->pristine + p->coeff_off, d_coeffs, sizeof(double) * Kc,
+// Prologue / epilogue of a unit whose staging starts at `stage` (device).
+StageFn unit_prologue(SumUnit* u, const char* stage) {
+  const int N = u->P.N, K = u->P.K;
+  const double* const* d_src = reinterpret_cast<const double* const*>(stage);
+  const uint64_t* d_seed = reinterpret_cast<const uint64_t*>(stage + sizeof(double*) * (size_t(K) * N + N));
+  const double* d_coeffs = reinterpret_cast<const double*>(stage + sizeof(double*) * (size_t(K) * N + N) + 8);
+  return [u, d_src, d_seed, d_coeffs, K](cudaStream_t s) -> int {
+    TTR_CHECK_CUDA(cudaMemcpyAsync(u->gp.seed_dev, d_seed, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    if (u->gp.pristine)
+      TTR_CHECK_CUDA(cudaMemcpyAsync(u->gp.pristine + u->coeff_off, d_coeffs, sizeof(double) * K,
                                      cudaMemcpyDeviceToDevice, s));
-    if (p->ngb > 0) {
-      gather_kernel<<<unsigned(p->ngb), 256, 0, s>>>(p->gblocks, d_src, p->in_off, p->in_buf);
+    if (u->ngb > 0) {
+      gather_kernel<<<unsigned(u->ngb), 256, 0, s>>>(u->gblocks, d_src, u->in_off, u->in_buf);
       TTR_CHECK_LAUNCH();
       prof_count_launch(1);
     }
     return int(TT_OK);
   };
-  StageFn epilogue = [p, d_dst](cudaStream_t s) -> int {
-    if (p->nsb > 0) {
-      scatter_kernel<<<unsigned(p->nsb), 256, 0, s>>>(p->sblocks, p->out_buf, p->out_off, d_dst,
-                                                      p->tol > 0.0 ? p->rk_dev : nullptr, p->dims);
+}
+StageFn unit_epilogue(SumUnit* u, const char* stage) {
+  const int N = u->P.N, K = u->P.K;
+  double* const* d_dst = reinterpret_cast<double* const*>(stage + sizeof(double*) * size_t(K) * N);
+  return [u, d_dst](cudaStream_t s) -> int {
+    if (u->nsb > 0) {
+      scatter_kernel<<<unsigned(u->nsb), 256, 0, s>>>(u->sblocks, u->out_buf, u->out_off, d_dst,
+                                                      u->tol > 0.0 ? u->rk_dev : nullptr, u->dims);
       TTR_CHECK_LAUNCH();
       prof_count_launch(1);
     }
     return int(TT_OK);
   };
-  rc = plan_capture(build, prologue, epilogue, static_cast<cudaStream_t>(stream), &p->gp);
-  if (rc != TT_OK) return fail(rc, "");
+}
+
+// Host side of a unit's staging: core pointers, output pointers, seed, coefficients.
+int unit_fill_stage(const SumUnit* u, char* hs, const double* const* cores, const double* coeffs, uint64_t seed,
+                    double* const* out) {
+  const int N = u->P.N, K = u->P.K;
+  for (size_t i = 0; i < size_t(K) * N; ++i)
+    if (!cores[i]) {
+      set_error("plan run: null core pointer");
+      return TT_EINVAL;
+    }
+  for (int n = 0; n < N; ++n)
+    if (!out[n]) {
+      set_error("plan run: null output core pointer");
+      return TT_EINVAL;
+    }
+  std::memcpy(hs, cores, sizeof(double*) * size_t(K) * N);
+  std::memcpy(hs + sizeof(double*) * size_t(K) * N, out, sizeof(double*) * N);
+  std::memcpy(hs + sizeof(double*) * (size_t(K) * N + N), &seed, sizeof(uint64_t));
+  double* hc = reinterpret_cast<double*>(hs + sizeof(double*) * (size_t(K) * N + N) + 8);
+  for (int j = 0; j < K; ++j) hc[j] = coeffs ? coeffs[j] : 1.0;
+  return TT_OK;
+}
+
+// Graph of several units on `width` parallel chains (unit b on chain b mod width).
+struct UnitGraph {
+  std::vector<SumUnit*> units;
+  size_t stage_bytes = 0;
+  void* d_stage = nullptr;
+  void* h_stage = nullptr;
+  int64_t* h_rk = nullptr;       // all units' ranks (sum of N_b + 1)
+  std::vector<size_t> rk_off;
+  cudaEvent_t staged = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<ProfPair> prof;
+  int64_t kernels = 0;
+  int width = 1;
+};
+
+void unit_graph_free(UnitGraph* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (auto& q : g->prof) {
+    cudaEventDestroy(q.e0);
+    cudaEventDestroy(q.e1);
+  }
+  for (SumUnit* u : g->units) {
+    unit_free(u);
+    delete u;
+  }
+  g->units.clear();
+  if (g->d_stage) cudaFree(g->d_stage);
+  if (g->h_stage) cudaFreeHost(g->h_stage);
+  if (g->h_rk) cudaFreeHost(g->h_rk);
+  if (g->staged) cudaEventDestroy(g->staged);
+  *g = UnitGraph{};
+}
+
+// Staging layout, then one capture: fork into width chains, every unit's
+// prologue / schedule / epilogue on its chain, join.
+int unit_graph_capture(UnitGraph* g, int width) {
+  g->width = std::max(1, std::min<int>(width, int(g->units.size())));
+  size_t off = 0, rk = 0;
+  for (SumUnit* u : g->units) {
+    u->stage_off = off;
+    off += align256(unit_stage_bytes(u->P.N, u->P.K));
+    g->rk_off.push_back(rk);
+    rk += size_t(u->P.N) + 1;
+  }
+  g->stage_bytes = std::max<size_t>(off, 256);
+  if (cudaMalloc(&g->d_stage, g->stage_bytes) != cudaSuccess ||
+      cudaMallocHost(&g->h_stage, g->stage_bytes) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&g->h_rk), sizeof(int64_t) * std::max<size_t>(rk, 1)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->staged, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("plan: staging allocation failed");
+    return TT_ENOMEM;
+  }
+  std::memset(g->h_stage, 0, g->stage_bytes);
+  const char* ds = static_cast<const char*>(g->d_stage);
+  auto body = [&](cudaStream_t cs) -> int {
+    if (g->width == 1) {
+      for (SumUnit* u : g->units)
+        TTR_TRY(plan_emit(u->gp, unit_prologue(u, ds + u->stage_off), unit_epilogue(u, ds + u->stage_off), cs));
+      return int(TT_OK);
+    }
+    std::vector<cudaStream_t> chains(g->width, nullptr);
+    std::vector<cudaEvent_t> ev(g->width + 1, nullptr);
+    int rc = TT_OK;
+    for (auto& e : ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = TT_ECUDA;
+    for (auto& c : chains)
+      if (cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess) rc = TT_ECUDA;
+    if (rc == TT_OK && cudaEventRecord(ev[g->width], cs) != cudaSuccess) rc = TT_ECUDA;
+    for (int w = 0; rc == TT_OK && w < g->width; ++w)
+      if (cudaStreamWaitEvent(chains[w], ev[g->width], 0) != cudaSuccess) rc = TT_ECUDA;
+    for (size_t b = 0; rc == TT_OK && b < g->units.size(); ++b) {
+      SumUnit* u = g->units[b];
+      rc = plan_emit(u->gp, unit_prologue(u, ds + u->stage_off), unit_epilogue(u, ds + u->stage_off),
+                     chains[b % size_t(g->width)]);
+    }
+    for (int w = 0; rc == TT_OK && w < g->width; ++w) {
+      if (cudaEventRecord(ev[w], chains[w]) != cudaSuccess || cudaStreamWaitEvent(cs, ev[w], 0) != cudaSuccess)
+        rc = TT_ECUDA;
+    }
+    if (rc == TT_ECUDA) set_error("plan: fork / join of the capture failed");
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    for (auto& c : chains)
+      if (c) cudaStreamDestroy(c);
+    return rc;
+  };
+  return capture_graph(body, &g->exec, &g->prof, &g->kernels);
+}
+
+// One replay: staging copy, graph launch, rank read-back (tolerance units).
+int unit_graph_run(UnitGraph* g, cudaStream_t s, int64_t* const* out_ranks) {
+  TTR_CHECK_CUDA(cudaMemcpyAsync(g->d_stage, g->h_stage, g->stage_bytes, cudaMemcpyHostToDevice, s));
+  TTR_CHECK_CUDA(cudaEventRecord(g->staged, s));
+  TTR_CHECK_CUDA(cudaGraphLaunch(g->exec, s));
+  bool synced = false;
+  bool any_tol = false;
+  for (SumUnit* u : g->units) any_tol = any_tol || u->tol > 0.0;
+  if (any_tol) {
+    for (size_t b = 0; b < g->units.size(); ++b) {
+      SumUnit* u = g->units[b];
+      if (u->tol > 0.0)
+        TTR_CHECK_CUDA(cudaMemcpyAsync(g->h_rk + g->rk_off[b], u->rk_dev, sizeof(int64_t) * (u->P.N + 1),
+                                       cudaMemcpyDeviceToHost, s));
+    }
+    TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+    synced = true;
+  }
+  for (size_t b = 0; b < g->units.size(); ++b) {
+    SumUnit* u = g->units[b];
+    for (int n = 0; n <= u->P.N; ++n) out_ranks[b][n] = u->tol > 0.0 ? g->h_rk[g->rk_off[b] + n] : u->P.ell[n];
+  }
+  if (prof_on()) {
+    if (!synced) TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+    TTR_TRY(prof_replayed(g->prof, g->kernels));
+  }
+  return TT_OK;
+}
+
+}  // namespace
+}  // namespace ttr
+
+using namespace ttr;
+
+struct tt_sum_plan {
+  UnitGraph g;
+};
+struct tt_batch_plan {
+  UnitGraph g;
+  std::vector<int> N, K;
+};
+
+extern "C" {
+
+int tt_sum_plan_create(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const int64_t* ells,
+                       double tol, int32_t precision, tt_sum_plan** plan, void* stream) {
+  if (!plan) {
+    set_error("tt_sum_plan_create: null plan pointer");
+    return TT_EINVAL;
+  }
+  *plan = nullptr;
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
+    set_error("tt_sum_plan_create: unknown precision mode");
+    return TT_EINVAL;
+  }
+  tt_sum_plan* p = new tt_sum_plan;
+  SumUnit* u = new SumUnit;
+  p->g.units.push_back(u);
+  int rc = unit_init(u, N, K, dims, ranks, ells, tol, precision);
+  if (rc == TT_OK) rc = unit_graph_capture(&p->g, 1);
+  if (rc != TT_OK) {
+    unit_graph_free(&p->g);
+    delete p;
+    return rc;
+  }
+  (void)stream;
   *plan = p;
   return TT_OK;
 }
@@ -243,50 +388,85 @@ int tt_sum_plan_run(tt_sum_plan* p, const double* const* cores, const double* co
     set_error("tt_sum_plan_run: null argument");
     return TT_EINVAL;
   }
-  const SumProblem& P = p->P;
-  const int N = P.N, K = P.K;
-  for (size_t i = 0; i < size_t(K) * N; ++i)
-    if (!cores[i]) {
-      set_error("tt_sum_plan_run: null core pointer");
-      return TT_EINVAL;
-    }
-  for (int n = 0; n < N; ++n)
-    if (!out[n]) {
-      set_error("tt_sum_plan_run: null output core pointer");
-      return TT_EINVAL;
-    }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the previous run's staging copy must have left the pinned buffer
-  TTR_CHECK_CUDA(cudaEventSynchronize(p->staged));
-  char* hs = static_cast<char*>(p->h_stage);
-  std::memcpy(hs, cores, sizeof(double*) * size_t(K) * N);
-  std::memcpy(hs + sizeof(double*) * size_t(K) * N, out, sizeof(double*) * N);
-  std::memcpy(hs + sizeof(double*) * (size_t(K) * N + N), &seed, sizeof(uint64_t));
-  double* hc = reinterpret_cast<double*>(hs + sizeof(double*) * (size_t(K) * N + N) + 8);
-  for (int j = 0; j < K; ++j) hc[j] = coeffs ? coeffs[j] : 1.0;
-  TTR_CHECK_CUDA(cudaMemcpyAsync(p->d_stage, p->h_stage, p->stage_bytes, cudaMemcpyHostToDevice, s));
-  TTR_CHECK_CUDA(cudaEventRecord(p->staged, s));
-  TTR_TRY(plan_replay(p->gp, s));
-  if (p->tol > 0.0) {
-    TTR_CHECK_CUDA(cudaMemcpyAsync(p->h_rk, p->rk_dev, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, s));
-    TTR_CHECK_CUDA(cudaStreamSynchronize(s));
-    for (int n = 0; n <= N; ++n) out_ranks[n] = p->h_rk[n];
-  } else {
-    for (int n = 0; n <= N; ++n) out_ranks[n] = P.ell[n];
-  }
-  if (prof_on()) {
-    TTR_CHECK_CUDA(cudaStreamSynchronize(s));
-    TTR_TRY(prof_replayed(p->gp.prof, p->gp.kernels));
-  }
-  return TT_OK;
+  TTR_CHECK_CUDA(cudaEventSynchronize(p->g.staged));   // the previous staging copy left the pinned block
+  SumUnit* u = p->g.units[0];
+  TTR_TRY(unit_fill_stage(u, static_cast<char*>(p->g.h_stage) + u->stage_off, cores, coeffs, seed, out));
+  int64_t* const rk[1] = {out_ranks};
+  return unit_graph_run(&p->g, static_cast<cudaStream_t>(stream), rk);
 }
 
 int tt_sum_plan_destroy(tt_sum_plan* p) {
-  if (p) cudaDeviceSynchronize();
-  sum_plan_free(p);
+  if (!p) return TT_OK;
+  cudaDeviceSynchronize();
+  unit_graph_free(&p->g);
+  delete p;
   return TT_OK;
 }
 
-int64_t tt_sum_plan_launches(const tt_sum_plan* p) { return p ? p->gp.kernels : 0; }
+int64_t tt_sum_plan_launches(const tt_sum_plan* p) { return p ? p->g.kernels : 0; }
+
+int tt_batch_plan_create(int32_t B, const tt_sum_problem* probs, int32_t precision, int32_t width,
+                         tt_batch_plan** plan, void* stream) {
+  if (!plan || B < 1 || !probs || width < 1) {
+    set_error("tt_batch_plan_create: need B >= 1 problems, width >= 1 and a plan pointer");
+    return TT_EINVAL;
+  }
+  *plan = nullptr;
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
+    set_error("tt_batch_plan_create: unknown precision mode");
+    return TT_EINVAL;
+  }
+  tt_batch_plan* p = new tt_batch_plan;
+  int rc = TT_OK;
+  for (int b = 0; rc == TT_OK && b < B; ++b) {
+    SumUnit* u = new SumUnit;
+    p->g.units.push_back(u);
+    rc = unit_init(u, probs[b].N, probs[b].K, probs[b].dims, probs[b].ranks, probs[b].ells, probs[b].tol,
+                   precision);
+    if (rc != TT_OK) set_error("tt_batch_plan_create: problem " + std::to_string(b) + ": " + tt_last_error());
+    p->N.push_back(probs[b].N);
+    p->K.push_back(probs[b].K);
+  }
+  if (rc == TT_OK) rc = unit_graph_capture(&p->g, width);
+  if (rc != TT_OK) {
+    unit_graph_free(&p->g);
+    delete p;
+    return rc;
+  }
+  (void)stream;
+  *plan = p;
+  return TT_OK;
+}
+
+int tt_batch_plan_run(tt_batch_plan* p, const double* const* cores, const uint64_t* seeds, double* const* out,
+                      int64_t* out_ranks, void* stream) {
+  if (!p || !cores || !out || !out_ranks) {
+    set_error("tt_batch_plan_run: null argument");
+    return TT_EINVAL;
+  }
+  TTR_CHECK_CUDA(cudaEventSynchronize(p->g.staged));
+  std::vector<int64_t*> rk(p->g.units.size());
+  size_t ci = 0, oi = 0, ri = 0;
+  for (size_t b = 0; b < p->g.units.size(); ++b) {
+    SumUnit* u = p->g.units[b];
+    TTR_TRY(unit_fill_stage(u, static_cast<char*>(p->g.h_stage) + u->stage_off, cores + ci, nullptr,
+                            seeds ? seeds[b] : uint64_t(b), out + oi));
+    rk[b] = out_ranks + ri;
+    ci += size_t(u->P.K) * u->P.N;
+    oi += size_t(u->P.N);
+    ri += size_t(u->P.N) + 1;
+  }
+  return unit_graph_run(&p->g, static_cast<cudaStream_t>(stream), rk.data());
+}
+
+int tt_batch_plan_destroy(tt_batch_plan* p) {
+  if (!p) return TT_OK;
+  cudaDeviceSynchronize();
+  unit_graph_free(&p->g);
+  delete p;
+  return TT_OK;
+}
+
+int64_t tt_batch_plan_launches(const tt_batch_plan* p) { return p ? p->g.kernels : 0; }
 
 }  // extern "C"

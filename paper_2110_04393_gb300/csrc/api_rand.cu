@@ -146,41 +146,43 @@ void plan_free(GraphPlan* gp) {
   if (gp->pristine) cudaFree(gp->pristine);
   if (gp->seed_dev) cudaFree(gp->seed_dev);
   delete gp->sc;
+  delete gp->probe;
   *gp = GraphPlan{};
 }
 
-int plan_capture(const BuildFn& build, const StageFn& prologue, const StageFn& epilogue, cudaStream_t st,
-                 GraphPlan* gp) {
+int plan_prepare(const BuildFn& build, GraphPlan* gp) {
   *gp = GraphPlan{};
-  Schedule probe;
-  size_t need = 0;
-  {
-    Arena a;
-    a.sizing = true;
-    TTR_TRY(build(a, probe));
-    need = schedule_bytes(a, probe);
-  }
   auto fail = [&](int rc) {
     plan_free(gp);
     return rc;
   };
+  gp->probe = new Schedule;
+  size_t need = 0;
+  {
+    Arena a;
+    a.sizing = true;
+    const int rc = build(a, *gp->probe);
+    if (rc != TT_OK) return fail(rc);
+    need = schedule_bytes(a, *gp->probe);
+  }
   if (cudaMalloc(&gp->ws, std::max<size_t>(need, 256)) != cudaSuccess ||
       cudaMalloc(&gp->seed_dev, 256) != cudaSuccess) {
     cudaGetLastError();
     set_error("plan: workspace allocation of " + std::to_string(need) + " bytes failed");
     return fail(TT_ENOMEM);
   }
+  gp->ws_bytes = need;
   Arena a;
   a.sizing = false;
   a.base = static_cast<char*>(gp->ws);
   a.cap = need;
   gp->sc = new Schedule;
   Schedule& s = *gp->sc;
-  gp->d_descs = bind_schedule_regions(a, probe, s);
+  gp->d_descs = bind_schedule_regions(a, *gp->probe, s);
   s.seed_dev = gp->seed_dev;
   int rc = build(a, s);
   if (rc != TT_OK) return fail(rc);
-  // static tables and the pristine copies of the uploads, before the capture
+  // static tables and the pristine copies of the uploads, before any capture
   if (!s.descs.empty() &&
       cudaMemcpy(gp->d_descs, s.descs.data(), s.descs.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice) !=
           cudaSuccess) {
@@ -210,34 +212,44 @@ int plan_capture(const BuildFn& build, const StageFn& prologue, const StageFn& e
     }
     s.upload_dev = gp->pristine;
   }
-  // capture: prologue, resets, the schedule, epilogue
+  return TT_OK;
+}
+
+int plan_emit(GraphPlan& gp, const StageFn& prologue, const StageFn& epilogue, cudaStream_t cs) {
+  int rc = TT_OK;
+  if (prologue) rc = prologue(cs);
+  if (rc == TT_OK) rc = reset_schedule_regions(*gp.probe, *gp.sc, cs);
+  for (size_t i = 0; rc == TT_OK && i < gp.sc->items.size(); ++i) rc = gp.sc->items[i](cs, gp.d_descs);
+  if (rc == TT_OK && epilogue) rc = epilogue(cs);
+  return rc;
+}
+
+int capture_graph(const std::function<int(cudaStream_t)>& body, cudaGraphExec_t* exec, std::vector<ProfPair>* prof,
+                  int64_t* kernels) {
   cudaStream_t cs;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
     set_error("plan: capture stream creation failed");
-    return fail(TT_ECUDA);
+    return TT_ECUDA;
   }
-  prof_capture_begin(&gp->prof);
+  prof_capture_begin(prof);
   cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
   if (ce != cudaSuccess) {
     prof_capture_end();
     cudaStreamDestroy(cs);
     set_error(std::string("plan: begin capture: ") + cudaGetErrorString(ce));
-    return fail(TT_ECUDA);
+    return TT_ECUDA;
   }
-  if (prologue) rc = prologue(cs);
-  if (rc == TT_OK) rc = reset_schedule_regions(probe, s, cs);
-  for (size_t i = 0; rc == TT_OK && i < s.items.size(); ++i) rc = s.items[i](cs, gp->d_descs);
-  if (rc == TT_OK && epilogue) rc = epilogue(cs);
+  int rc = body(cs);
   cudaGraph_t graph = nullptr;
   ce = cudaStreamEndCapture(cs, &graph);
-  gp->kernels = prof_capture_end();
+  *kernels = prof_capture_end();
   cudaStreamDestroy(cs);
   if (rc == TT_OK && ce != cudaSuccess) {
     set_error(std::string("plan: end capture: ") + cudaGetErrorString(ce));
     rc = TT_ECUDA;
   }
   if (rc == TT_OK) {
-    ce = cudaGraphInstantiate(&gp->exec, graph, 0);
+    ce = cudaGraphInstantiate(exec, graph, 0);
     if (ce != cudaSuccess) {
       set_error(std::string("plan: graph instantiation: ") + cudaGetErrorString(ce));
       rc = TT_ECUDA;
@@ -245,7 +257,19 @@ int plan_capture(const BuildFn& build, const StageFn& prologue, const StageFn& e
   }
   if (graph) cudaGraphDestroy(graph);
   cudaGetLastError();
-  if (rc != TT_OK) return fail(rc);
+  return rc;
+}
+
+int plan_capture(const BuildFn& build, const StageFn& prologue, const StageFn& epilogue, cudaStream_t st,
+                 GraphPlan* gp) {
+  TTR_TRY(plan_prepare(build, gp));
+  GraphPlan* g = gp;
+  const int rc = capture_graph([&](cudaStream_t cs) { return plan_emit(*g, prologue, epilogue, cs); }, &gp->exec,
+                               &gp->prof, &gp->kernels);
+  if (rc != TT_OK) {
+    plan_free(gp);
+    return rc;
+  }
   (void)st;
   return TT_OK;
 }

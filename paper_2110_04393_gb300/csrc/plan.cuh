@@ -128,7 +128,9 @@ struct ProfPair {
 };
 struct GraphPlan {
   Schedule* sc = nullptr;
+  Schedule* probe = nullptr;           // sizing pass (region sizes for the per-run resets)
   void* ws = nullptr;
+  size_t ws_bytes = 0;
   double* pristine = nullptr;
   uint64_t* seed_dev = nullptr;
   GemmDesc* d_descs = nullptr;
@@ -141,5 +143,14 @@ int plan_capture(const BuildFn& build, const StageFn& prologue, const StageFn& e
                  GraphPlan* gp);
 int plan_replay(GraphPlan& gp, cudaStream_t st);
 void plan_free(GraphPlan* gp);
+// The pieces of plan_capture, for graphs holding several schedules:
+// plan_prepare sizes, allocates, builds and uploads the static tables (no
+// capture); plan_emit issues prologue, resets, items and epilogue on a stream
+// (inside a capture); capture_graph captures body on a fresh stream and
+// instantiates the graph (exec), collecting profiling pairs and launches.
+int plan_prepare(const BuildFn& build, GraphPlan* gp);
+int plan_emit(GraphPlan& gp, const StageFn& prologue, const StageFn& epilogue, cudaStream_t cs);
+int capture_graph(const std::function<int(cudaStream_t)>& body, cudaGraphExec_t* exec, std::vector<ProfPair>* prof,
+                  int64_t* kernels);
 
 }  // namespace ttr
