@@ -364,6 +364,10 @@ int tt_selftest_tcgen05_bf16(int32_t M, int32_t N, int32_t K, const void* A, con
 int tt_prof_enable(int on);
 int tt_prof_reset(void);
 int tt_prof_read(double* gemm_ms, double* gemm_flops, int64_t* gemm_launches, int64_t* kernel_launches);
+/* Same for one kind of timed launch: 0 the contraction groups (the GEMM
+ * launches above), 1 the Cholesky-QR passes (flops: 4 m k^2 per QR of an
+ * m x k block, counted on its first pass). */
+int tt_prof_read_kind(int32_t kind, double* ms, double* flops, int64_t* launches);
 
 #ifdef __cplusplus
 }

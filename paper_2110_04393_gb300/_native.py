@@ -56,6 +56,7 @@ SIGNATURES = {
     "tt_prof_enable": (c_i32, [c_i32]),
     "tt_prof_reset": (c_i32, []),
     "tt_prof_read": (c_i32, [P_dbl, P_dbl, P_i64, P_i64]),
+    "tt_prof_read_kind": (c_i32, [c_i32, P_dbl, P_dbl, P_i64]),
 }
 
 

@@ -491,6 +491,13 @@ def prof_reset():
     _check(nat.lib().tt_prof_reset())
 
 
+def prof_read_kind(kind):
+    """(ms, flops, launches) of one kind of timed launch: 0 contraction groups, 1 QR passes."""
+    ms, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(nat.lib().tt_prof_read_kind(int(kind), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(n)))
+    return ms.value, fl.value, n.value
+
+
 def prof_read():
     """(gemm_ms, gemm_flops, gemm_launches, kernel_launches) since the last reset."""
     ms, fl = ctypes.c_double(), ctypes.c_double()

@@ -390,9 +390,13 @@ int cqr_launch(const CqrPass& p, cudaStream_t s) {
     TTR_CHECK_CUDA(cudaFuncSetAttribute(cqr_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     attr = true;
   }
+  cudaEvent_t e0;
+  const bool prof = prof_begin(s, &e0);
   cqr_pass_kernel<<<p.P, CQ_THREADS, smem, s>>>(p);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
+  // the QR's algorithmic flops (4 m k^2, the Householder count of a thin QR) on its first pass
+  if (prof) prof_end(s, 1, p.pass == 0 ? 4.0 * double(p.m) * double(p.k) * double(p.k) : 0.0);
   return TT_OK;
 }
 

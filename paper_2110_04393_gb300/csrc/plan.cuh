@@ -125,6 +125,7 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
 struct ProfPair {
   cudaEvent_t e0, e1;
   double flops;
+  int kind;
 };
 struct GraphPlan {
   Schedule* sc = nullptr;

@@ -14,9 +14,11 @@ struct Prof {
   std::mutex mu;
   bool on = false;
   std::vector<cudaEvent_t> pool;
+  std::vector<int> kinds;          // kind of each recorded pair
   size_t used = 0;
-  double flops = 0.0;
-  int64_t gemm_launches = 0;
+  double flops[kProfKinds] = {0.0, 0.0};
+  int64_t count[kProfKinds] = {0, 0};
+  double replay_ms[kProfKinds] = {0.0, 0.0};
 };
 Prof& P() {
   static Prof p;
@@ -26,7 +28,6 @@ std::atomic<int64_t> g_launches{0};
 thread_local std::vector<ProfPair>* t_sink = nullptr;
 thread_local int64_t t_sink_launches = 0;
 thread_local cudaEvent_t t_sink_e0 = nullptr;
-double g_replay_ms = 0.0;       // guarded by P().mu
 }  // namespace
 
 void prof_count_launch(int n) {
@@ -61,15 +62,18 @@ int prof_replayed(const std::vector<ProfPair>& pairs, int64_t launches) {
       set_error("profiling: elapsed time of a replayed event pair failed");
       return TT_ECUDA;
     }
-    g_replay_ms += t;
-    p.flops += q.flops;
-    p.gemm_launches += 1;
+    p.replay_ms[q.kind] += t;
+    p.flops[q.kind] += q.flops;
+    p.count[q.kind] += 1;
   }
   g_launches.fetch_add(launches, std::memory_order_relaxed);
   return TT_OK;
 }
 
-bool prof_gemm_begin(cudaStream_t s, cudaEvent_t* e0) {
+bool prof_gemm_begin(cudaStream_t s, cudaEvent_t* e0) { return prof_begin(s, e0); }
+void prof_gemm_end(cudaStream_t s, double flops) { prof_end(s, 0, flops); }
+
+bool prof_begin(cudaStream_t s, cudaEvent_t* e0) {
   if (t_sink) {
     if (!prof_on()) return false;
     cudaEvent_t e;
@@ -93,20 +97,22 @@ bool prof_gemm_begin(cudaStream_t s, cudaEvent_t* e0) {
   return true;
 }
 
-void prof_gemm_end(cudaStream_t s, double flops) {
+void prof_end(cudaStream_t s, int kind, double flops) {
   if (t_sink) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return;
     cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
-    t_sink->push_back(ProfPair{t_sink_e0, e, flops});
+    t_sink->push_back(ProfPair{t_sink_e0, e, flops, kind});
     return;
   }
   Prof& p = P();
   std::lock_guard<std::mutex> g(p.mu);
   cudaEventRecord(p.pool[p.used + 1], s);
+  if (p.kinds.size() < (p.used + 2) / 2) p.kinds.resize((p.used + 2) / 2);
+  p.kinds[p.used / 2] = kind;
   p.used += 2;
-  p.flops += flops;
-  p.gemm_launches += 1;
+  p.flops[kind] += flops;
+  p.count[kind] += 1;
 }
 
 }  // namespace ttr
@@ -126,18 +132,20 @@ int tt_prof_reset(void) {
   Prof& p = P();
   std::lock_guard<std::mutex> g(p.mu);
   p.used = 0;
-  p.flops = 0.0;
-  p.gemm_launches = 0;
-  g_replay_ms = 0.0;
+  for (int k = 0; k < kProfKinds; ++k) {
+    p.flops[k] = 0.0;
+    p.count[k] = 0;
+    p.replay_ms[k] = 0.0;
+  }
   g_launches.store(0);
   return TT_OK;
 }
 
-int tt_prof_read(double* gemm_ms, double* gemm_flops, int64_t* gemm_launches, int64_t* kernel_launches) {
-  Prof& p = P();
-  std::lock_guard<std::mutex> g(p.mu);
-  double ms = 0.0;
+// Sum of the eager event pairs of one kind plus the replayed ones.
+static int kind_ms(Prof& p, int kind, double* out) {
+  double ms = p.replay_ms[kind];
   for (size_t i = 0; i + 1 < p.used; i += 2) {
+    if (p.kinds[i / 2] != kind) continue;
     if (cudaEventSynchronize(p.pool[i + 1]) != cudaSuccess) {
       set_error("tt_prof_read: event synchronize failed");
       return TT_ECUDA;
@@ -149,10 +157,34 @@ int tt_prof_read(double* gemm_ms, double* gemm_flops, int64_t* gemm_launches, in
     }
     ms += t;
   }
-  if (gemm_ms) *gemm_ms = ms + g_replay_ms;
-  if (gemm_flops) *gemm_flops = p.flops;
-  if (gemm_launches) *gemm_launches = p.gemm_launches;
+  *out = ms;
+  return TT_OK;
+}
+
+int tt_prof_read(double* gemm_ms, double* gemm_flops, int64_t* gemm_launches, int64_t* kernel_launches) {
+  Prof& p = P();
+  std::lock_guard<std::mutex> g(p.mu);
+  double ms = 0.0;
+  TTR_TRY(kind_ms(p, 0, &ms));
+  if (gemm_ms) *gemm_ms = ms;
+  if (gemm_flops) *gemm_flops = p.flops[0];
+  if (gemm_launches) *gemm_launches = p.count[0];
   if (kernel_launches) *kernel_launches = g_launches.load();
+  return TT_OK;
+}
+
+int tt_prof_read_kind(int32_t kind, double* ms, double* flops, int64_t* launches) {
+  if (kind < 0 || kind >= kProfKinds) {
+    set_error("tt_prof_read_kind: kind must be 0 (contraction groups) or 1 (QR passes)");
+    return TT_EINVAL;
+  }
+  Prof& p = P();
+  std::lock_guard<std::mutex> g(p.mu);
+  double t = 0.0;
+  TTR_TRY(kind_ms(p, kind, &t));
+  if (ms) *ms = t;
+  if (flops) *flops = p.flops[kind];
+  if (launches) *launches = p.count[kind];
   return TT_OK;
 }
 
