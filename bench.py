@@ -226,9 +226,8 @@ def run_ours(a):
     res_prec, prof_prec, plans = {}, {}, {}
     with Clocks(local) as clk:
         for prec in precs:
-            tt.prof_enable(True)
-            plans[prec] = tt.SumRoundingPlan(dims, ranks_of(Ys), ell, tol=tol, precision=prec, device=dev)
             tt.prof_enable(False)
+            plans[prec] = tt.SumRoundingPlan(dims, ranks_of(Ys), ell, tol=tol, precision=prec, device=dev)
             res_prec[prec] = timed_plan(tt, torch, plans[prec], Yd, a.steps, a.warmup, flush, stream, world, dist)
             tt.prof_enable(True)
             pp = tt.SumRoundingPlan(dims, ranks_of(Ys), ell, tol=tol, precision=prec, device=dev)

@@ -37,6 +37,7 @@ __global__ void eye_kernel(double* dst, int64_t n) {
 int eye_launch(double* dst, int64_t n, cudaStream_t s) {
   const int64_t tot = n * n;
   const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(ceil_div(tot, 256), 4096)));
+  TTR_PREFER_SHARED(eye_kernel);
   eye_kernel<<<g, 256, 0, s>>>(dst, n);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);

@@ -179,6 +179,7 @@ StageFn unit_prologue(SumUnit* u, const char* stage) {
       TTR_CHECK_CUDA(cudaMemcpyAsync(u->gp.pristine + u->coeff_off, d_coeffs, sizeof(double) * K,
                                      cudaMemcpyDeviceToDevice, s));
     if (u->ngb > 0) {
+      TTR_PREFER_SHARED(gather_kernel);
       gather_kernel<<<unsigned(u->ngb), 256, 0, s>>>(u->gblocks, d_src, u->in_off, u->in_buf);
       TTR_CHECK_LAUNCH();
       prof_count_launch(1);
@@ -191,6 +192,7 @@ StageFn unit_epilogue(SumUnit* u, const char* stage) {
   double* const* d_dst = reinterpret_cast<double* const*>(stage + sizeof(double*) * size_t(K) * N);
   return [u, d_dst](cudaStream_t s) -> int {
     if (u->nsb > 0) {
+      TTR_PREFER_SHARED(scatter_kernel);
       scatter_kernel<<<unsigned(u->nsb), 256, 0, s>>>(u->sblocks, u->out_buf, u->out_off, d_dst,
                                                       u->tol > 0.0 ? u->rk_dev : nullptr, u->dims);
       TTR_CHECK_LAUNCH();

@@ -393,7 +393,7 @@ static int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int
     const int64_t m = I[n - 1] * ell[n], k = ell[n - 1];
     double* Xn = out[n - 1];
     double* Xp = out[n - 2];
-    qr_plan(sc, qr_view(pool, m, int(k)), Xn, 1, m, b.Qt, k, 1, b.Rb);
+    qr_plan(sc, qr_view(pool, m, int(k)), Xn, 1, m, b.Qt, k, 1, b.Rb, true);
     sc.add([=](cudaStream_t s) -> int {
       return svd_trunc_launch(int(k), b.Rb, b.eps, int(k), b.G1, b.G2, b.sig, b.rk + (n - 1), s, sbig);
     });

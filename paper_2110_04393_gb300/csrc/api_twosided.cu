@@ -42,6 +42,7 @@ __global__ void colscale_kernel(double* M, int64_t rows, int64_t cols, int64_t l
 int colscale_launch(double* M, int64_t rows, int64_t cols, int64_t ld, const double* sig, double p, double tol_rel,
                     cudaStream_t s) {
   const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows * cols, 256), 2048)));
+  TTR_PREFER_SHARED(colscale_kernel);
   colscale_kernel<<<g, 256, 0, s>>>(M, rows, cols, ld, sig, p, tol_rel);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);

@@ -47,6 +47,7 @@ constexpr int CQ_MAX_PASSES = 6;
 struct CqrPass {
   int64_t m;
   int k, b, P, pass;
+  int fo_r;                 // the first-order last pass may also update the R factor (R no longer triangular)
   const double* A;          // input
   int64_t a_rs, a_cs;
   double* buf[2];           // m x k ping-pong blocks (row-major)
@@ -304,9 +305,12 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
     }
     return;
   }
-  if (a.pass > 0 && a.Racc == nullptr) {
-    // Only Q is wanted and the block is already orthonormal to ||E||_F <= 1e-8,
-    // E = G - I: the last pass multiplies by I - E/2 instead of factoring again
+  if (a.pass > 0 && (a.Racc == nullptr || a.fo_r)) {
+    // The block is already orthonormal to ||E||_F <= 1e-8, E = G - I: the last
+    // pass multiplies by I - E/2 instead of factoring again. When R is wanted
+    // (and allowed to lose its triangular form) it becomes (I + E/2) R: the
+    // correction E R / 2 is ~1e-8 of R or less, so an fp32 product of it keeps R
+    // accurate to float64 rounding.
     __shared__ double s_red[CQ_THREADS / 32];
     double e2 = 0.0;
     for (int idx = tid; idx < k * k; idx += nt) {
@@ -322,6 +326,43 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
       for (int idx = tid; idx < k * k; idx += nt) {
         const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
         a.Rinv[idx] = ((idx % (k + 1) == 0) ? 1.0 : 0.0) - 0.5 * dv;
+      }
+      if (a.Racc) {
+        // X <- E / 2, G0 <- R (the previous factor), then R += (E / 2) R with R
+        // scaled by a power of two near 1 / max|R| for the fp32 product (no
+        // underflow or overflow in fp32 whatever the scale of A)
+        __shared__ int s_emax;
+        if (tid == 0) s_emax = -2000;
+        __syncthreads();
+        int em = -2000;
+        for (int idx = tid; idx < k * k; idx += nt) {
+          X[idx] = 0.5 * (G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0));
+          const double r = a.Racc[idx];
+          G0[idx] = r;
+          const int e = int((uint64_t(__double_as_longlong(r)) >> 52) & 0x7FF);
+          if (e != 0) em = max(em, e - 1023);
+        }
+        atomicMax(&s_emax, em);
+        __syncthreads();
+        const int sh = s_emax == -2000 ? 0 : -s_emax;                 // R 2^sh has entries below 2
+        const double up = __longlong_as_double((long long)(uint64_t(1023 - sh) << 52));   // 2^{-sh}
+        const double down = __longlong_as_double((long long)(uint64_t(1023 + sh) << 52)); // 2^{sh}
+        // fp32 copies first (conversions run on the FP64 pipe: once per entry),
+        // in the memory of G, which is no longer needed (2 k^2 floats = k^2 doubles)
+        float* Xf = reinterpret_cast<float*>(G);                 // E / 2
+        float* Rf = Xf + k * k;                                  // R 2^sh
+        __syncthreads();
+        for (int idx = tid; idx < k * k; idx += nt) {
+          Xf[idx] = float(X[idx]);
+          Rf[idx] = float(G0[idx] * down);
+        }
+        __syncthreads();
+        for (int idx = tid; idx < k * k; idx += nt) {
+          const int r = idx / k, c = idx % k;
+          float corr = 0.0f;
+          for (int l = 0; l < k; ++l) corr = fmaf(Xf[r * k + l], Rf[l * k + c], corr);
+          a.Racc[idx] = fma(double(corr), up, G0[idx]);
+        }
       }
       if (tid == 0) {
         a.status[4] = 1;
@@ -392,6 +433,7 @@ int cqr_launch(const CqrPass& p, cudaStream_t s) {
   }
   cudaEvent_t e0;
   const bool prof = prof_begin(s, &e0);
+  TTR_PREFER_SHARED(cqr_pass_kernel);
   cqr_pass_kernel<<<p.P, CQ_THREADS, smem, s>>>(p);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
@@ -470,7 +512,7 @@ QrBufs qr_reserve(Arena& ar, int64_t m, int k) {
 }
 
 void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q, int64_t q_rs,
-             int64_t q_cs, double* R) {
+             int64_t q_cs, double* R, bool r_may_be_full) {
   const QrBufs bb = b;
   sc.add([bb](cudaStream_t s) -> int {
     if (!bb.status) return int(TT_OK);
@@ -495,6 +537,7 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
   base.counter = b.status ? b.status + 5 : nullptr;
   base.Rinv = b.Rinv;
   base.Racc = R;
+  base.fo_r = r_may_be_full ? 1 : 0;
   base.big = b.big;
   base.status = b.status;
   for (int p = 0; p < CQ_MAX_PASSES; ++p) {

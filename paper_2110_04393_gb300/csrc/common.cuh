@@ -64,4 +64,20 @@ struct Arena {
 
 int num_sms();
 
+// Every kernel of the library prefers the largest shared-memory carveout, so
+// consecutive kernels with small and large shared memory never make an SM
+// switch its L1 / shared-memory split (a switch drains the SM). Called once
+// per kernel (TTR_PREFER_SHARED at the launch site); failures are ignored.
+inline int prefer_shared_once(const void* fn) {
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, int(cudaSharedmemCarveoutMaxShared)) !=
+      cudaSuccess)
+    cudaGetLastError();
+  return 0;
+}
+#define TTR_PREFER_SHARED(k)                                                           \
+  do {                                                                                 \
+    static const int ttr_prefer_shared_once = ::ttr::prefer_shared_once((const void*)(k)); \
+    (void)ttr_prefer_shared_once;                                                      \
+  } while (0)
+
 }  // namespace ttr

@@ -173,6 +173,7 @@ int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, double flops,
   if (ndesc == 0 || tiles == 0) return TT_OK;
   cudaEvent_t e0;
   const bool prof = prof_gemm_begin(s, &e0);
+  TTR_PREFER_SHARED(gemm_f64_kernel);
   gemm_f64_kernel<<<unsigned(tiles), GEMM_THREADS, 0, s>>>(d_descs, ndesc);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);

@@ -91,6 +91,7 @@ unsigned grid_for(int64_t n, int threads) {
 
 int fill_launch(double* p, int64_t n, double v, cudaStream_t s) {
   if (n <= 0) return TT_OK;
+  TTR_PREFER_SHARED(fill_kernel);
   fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(p, n, v);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
@@ -102,6 +103,7 @@ int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index
   const int64_t E = r0 * I * r1;
   if (E <= 0) return TT_OK;
   const double stdv = 1.0 / std::sqrt(double(r0) * double(I) * double(r1));
+  TTR_PREFER_SHARED(sketch_kernel);
   sketch_kernel<<<grid_for((E + 1) / 2, 256), 256, 0, s>>>(out, E, core_index, uint32_t(seed),
                                                             uint32_t(seed >> 32), stdv, seed_dev);
   TTR_CHECK_LAUNCH();
@@ -110,6 +112,7 @@ int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index
 }
 
 int norm_eps_launch(const double* x, int64_t n, double tol, int N, double* eps_out, cudaStream_t s) {
+  TTR_PREFER_SHARED(norm_eps_kernel);
   norm_eps_kernel<<<1, 1024, 0, s>>>(x, n, tol, N, eps_out);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
@@ -118,6 +121,7 @@ int norm_eps_launch(const double* x, int64_t n, double tol, int N, double* eps_o
 
 int compact_core_launch(const double* src, double* dst, int64_t r0max, int64_t I, int64_t r1max,
                         const int64_t* r0p, const int64_t* r1p, cudaStream_t s) {
+  TTR_PREFER_SHARED(compact_kernel);
   compact_kernel<<<grid_for(r0max * I * r1max, 256), 256, 0, s>>>(src, dst, r0max, I, r1max, r0p, r1p);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
@@ -160,6 +164,7 @@ __global__ void copy3_kernel(const Copy3* __restrict__ d, int n, int64_t total) 
 
 int copy3_launch(const Copy3* d_descs, int n, int64_t total, cudaStream_t s) {
   if (n == 0 || total == 0) return TT_OK;
+  TTR_PREFER_SHARED(copy3_kernel);
   copy3_kernel<<<grid_for(total, 256), 256, 0, s>>>(d_descs, n, total);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
@@ -175,6 +180,7 @@ __global__ void or_flag_kernel(int* dst, const int* src) {
 }  // namespace
 int or_flag_launch(int* dst, const int* src, cudaStream_t s) {
   if (!dst || !src) return TT_OK;
+  TTR_PREFER_SHARED(or_flag_kernel);
   or_flag_kernel<<<1, 32, 0, s>>>(dst, src);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
@@ -218,6 +224,7 @@ __global__ void axpy_kernel(double* y, const double* x, int64_t n) {
 
 int triu_inverse_launch(const double* T, double* X, int k, cudaStream_t s) {
   if (k <= 0 || !T || !X) return TT_OK;
+  TTR_PREFER_SHARED(triu_inverse_kernel);
   triu_inverse_kernel<<<1, 256, 0, s>>>(T, X, k);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
@@ -226,6 +233,7 @@ int triu_inverse_launch(const double* T, double* X, int k, cudaStream_t s) {
 
 int sym_lower_launch(double* A, int k, cudaStream_t s) {
   if (k <= 0 || !A) return TT_OK;
+  TTR_PREFER_SHARED(sym_lower_kernel);
   sym_lower_kernel<<<grid_for(int64_t(k) * k, 256), 256, 0, s>>>(A, k);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
@@ -234,6 +242,7 @@ int sym_lower_launch(double* A, int k, cudaStream_t s) {
 
 int axpy_launch(double* y, const double* x, int64_t n, cudaStream_t s) {
   if (n <= 0 || !y || !x) return TT_OK;
+  TTR_PREFER_SHARED(axpy_kernel);
   axpy_kernel<<<grid_for(n, 256), 256, 0, s>>>(y, x, n);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);

@@ -41,7 +41,10 @@ QrBufs qr_view(const QrPool& p, int64_t m, int k);
 QrBufs qr_reserve(Arena& ar, int64_t m, int k);
 // Q must not alias A (the fallback re-reads A). After the schedule ran,
 // status[0] != 0 means no orthonormal Q was produced (only possible for k > 96).
+// r_may_be_full: R may come out as a full k x k matrix (A = Q R still holds;
+// the first-order last pass then spares a factorization); otherwise R is upper
+// triangular with a nonnegative diagonal.
 void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q, int64_t q_rs,
-             int64_t q_cs, double* R);
+             int64_t q_cs, double* R, bool r_may_be_full = false);
 
 }  // namespace ttr

@@ -55,26 +55,41 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
   // ---- certificate: sigma_min(R) >= 1/||R^{-1}||_F > 2 eps  =>  nothing is cut
   if (eps_ptr != nullptr && rcap >= k) {
     // R^{-1} (upper) by a right-looking backward sweep over all columns at once
-    __shared__ double s_rd;
     __shared__ int s_zero;
+    // The diagonal reciprocals are independent (R is triangular): all of them
+    // first, in parallel; then, starting from B = I, the backward
+    // sweep  B(i, c) -= (R(i, j) / R(j, j)) B(j, c), i < j <= c (the scaled
+    // coefficient does not depend on B, so each step has one dependent FMA),
+    // and X(i, c) = B(i, c) / R(i, i) at the end. A is left untouched.
     if (tid == 0) s_zero = 0;
+    __syncthreads();
+    double* rdv = sv;                                        // k reciprocals (sv is free here)
+    for (int j = tid; j < k; j += nt) {
+      const double dj = A[j + j * k];
+      if (dj == 0.0 || !isfinite(dj)) {
+        s_zero = 1;
+        rdv[j] = 0.0;
+      } else {
+        rdv[j] = 1.0 / dj;
+      }
+    }
     for (int idx = tid; idx < kk * kk; idx += nt) Vm[idx] = ((idx % kk) == (idx / kk)) ? 1.0 : 0.0;
     __syncthreads();
-    for (int j = k - 1; j >= 0; --j) {
-      if (tid == 0) {
-        const double dj = A[j + j * k];
-        if (dj == 0.0 || !isfinite(dj)) { s_zero = 1; s_rd = 0.0; } else s_rd = 1.0 / dj;
-      }
-      __syncthreads();
-      const double rd = s_rd;
-      for (int c = j + tid; c < k; c += nt) Vm[j + c * kk] *= rd;        // row j of X final
-      __syncthreads();
-      for (int idx = tid; idx < j * (k - j); idx += nt) {                  // rows i < j, columns c >= j
-        const int i = idx % j, c = j + idx / j;
-        Vm[i + c * kk] = fma(-A[i + j * k], Vm[j + c * kk], Vm[i + c * kk]);
+    for (int j = k - 1; j >= 1; --j) {
+      // the j (k - j) entries (i < j, c >= j) packed densely over the threads:
+      // an FP64 warp instruction costs the same however few lanes it has
+      const double rj = rdv[j];
+      for (int e = tid; e < j * (k - j); e += nt) {
+        const int i = e % j, c = j + e / j;
+        Vm[i + c * kk] = fma(-(A[i + j * k] * rj), Vm[j + c * kk], Vm[i + c * kk]);
       }
       __syncthreads();
     }
+    for (int e = tid; e < k * k; e += nt) {
+      const int i = e % k, c = e / k;
+      if (i <= c) Vm[i + c * kk] *= rdv[i];
+    }
+    __syncthreads();
     double part = 0.0;
     for (int idx = tid; idx < k * k; idx += nt) {
       const int r = idx % k, c = idx / k;
@@ -90,7 +105,20 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
     __syncthreads();
     double tot = 0.0;
     for (int i = 0; i < nwarp; ++i) tot += red[i];
-    const bool certified = !s_flag && isfinite(tot) && tot > 0.0 && (1.0 / sqrt(tot)) > 2.0 * eps;
+    // R may carry a tiny strictly lower part L (first-order QR): with T its
+    // upper triangle, sigma_min(R) >= 1 / ||T^{-1}||_F - ||L||_F
+    double low = 0.0;
+    for (int idx = tid; idx < k * k; idx += nt) {
+      const int r = idx % k, c = idx / k;
+      if (r > c) low = fma(A[r + c * k], A[r + c * k], low);
+    }
+    low = warp_sum(low);
+    __syncthreads();
+    if (lane == 0) red[warp] = low;
+    __syncthreads();
+    double ltot = 0.0;
+    for (int i = 0; i < nwarp; ++i) ltot += red[i];
+    const bool certified = !s_flag && isfinite(tot) && tot > 0.0 && (1.0 / sqrt(tot)) - sqrt(ltot) > 2.0 * eps;
     __syncthreads();
     if (certified) {
       for (int idx = tid; idx < k * k; idx += nt) {
@@ -215,6 +243,7 @@ int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, do
     TTR_CHECK_CUDA(cudaFuncSetAttribute(svd_trunc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_done = true;
   }
+  TTR_PREFER_SHARED(svd_trunc_kernel);
   svd_trunc_kernel<<<1, SVD_THREADS, smem, s>>>(k, R, eps_ptr, rcap, G1, G2, sigma, rank_out,
                                                 k > SVD_SMEM_K ? big : nullptr);
   TTR_CHECK_LAUNCH();

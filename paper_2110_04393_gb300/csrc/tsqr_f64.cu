@@ -321,10 +321,12 @@ int tsqr_launch(const TsqrShape& sh, const TsqrWork& w, const double* A, int64_t
     TTR_CHECK_CUDA(cudaFuncSetAttribute(tsqr_down_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_done = true;
   }
+  TTR_PREFER_SHARED(tsqr_up_kernel);
   tsqr_up_kernel<<<sh.P, TQ_THREADS, up_smem, s>>>(a);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
   if (Q) {
+    TTR_PREFER_SHARED(tsqr_down_kernel);
     tsqr_down_kernel<<<sh.P, TQ_THREADS, dn_smem, s>>>(a);
     TTR_CHECK_LAUNCH();
   prof_count_launch(1);
