@@ -320,8 +320,14 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
     for (int off = 16; off; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
     if ((tid & 31) == 0) s_red[tid >> 5] = e2;
     __syncthreads();
-    double tot = 0.0;
-    for (int w = 0; w < (nt >> 5); ++w) tot += s_red[w];
+    __shared__ double s_e2;
+    if (tid == 0) {
+      double t0 = 0.0;
+      for (int w = 0; w < (nt >> 5); ++w) t0 += s_red[w];
+      s_e2 = t0;
+    }
+    __syncthreads();
+    const double tot = s_e2;
     if (tot <= 1e-16) {                           // ||E||_F <= 1e-8 (false for NaN)
       for (int idx = tid; idx < k * k; idx += nt) {
         const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);

@@ -142,13 +142,16 @@ __device__ __noinline__ double round_i128(long long H, long long Lo, int e2) {
 }
 
 // One output: C = alpha * round(T 2^{Er + Ec - 63}) + beta * C, NaN when the
-// row or column held Inf / NaN (out of line, like round_i128).
-__device__ __noinline__ void store_out(double* cp, long long H, long long Lo, int Er, int Ec, double alpha,
-                                       double beta) {
+// row or column held Inf / NaN (out of line, like round_i128). plain: alpha = 1
+// and beta = 0, decided once per thread (FP64 compares cost the FP64 pipe).
+__device__ __noinline__ void store_out(double* cp, long long H, long long Lo, int Er, int Ec, bool plain,
+                                       double alpha, double beta) {
   double v = (Er == kNonFinite || Ec == kNonFinite) ? __longlong_as_double(0x7FF8000000000000LL)
                                                     : round_i128(H, Lo, Er + Ec - 63);
-  if (alpha != 1.0) v *= alpha;
-  if (beta != 0.0) v = fma(beta, *cp, v);
+  if (!plain) {
+    v *= alpha;
+    if (beta != 0.0) v = fma(beta, *cp, v);      // C is read only when beta != 0
+  }
   *cp = v;
 }
 
@@ -265,42 +268,18 @@ __device__ __forceinline__ int decode_exp(int v, int epoch) {
 
 // ---- pass 2: digit planes. A block splits a 32 x bk sub-tile of A (rows) or
 // of B (columns) and writes its s bf16 planes in the canonical K-major layout
-// of the 128 x bk (A) or 32 x bk (B) operand tile, padding with zeros.
-__global__ void __launch_bounds__(256) tc_split_kernel(TcArgs args) {
-  __shared__ int Es[32];
-  const int64_t t = blockIdx.x;
-  const GemmDesc d = args.descs[find_desc(args.descs, args.ndesc, t, 2)];
-  const int s = args.s;
+// of the 128 x bk (A) or 32 x bk (B) operand tile, padding with zeros. With a
+// short K (lx) one block covers all chunks of its 32 rows / columns and takes
+// their largest exponents itself (written as the tags the product pass reads),
+// so no exponent pass runs for that descriptor.
+constexpr int64_t kLocalExpK = 512;
+
+__device__ __forceinline__ void split_chunk(const GemmDesc& d, int s, bool sideA, int64_t bidx, int64_t tile,
+                                            int quarter, int64_t kc, int64_t o0, int64_t outer, const double* base,
+                                            int64_t os, int64_t is, const int* Es) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int bk = d.bkc;
   const int64_t nkc = d.nkc;
-  int64_t local = t - d.split_begin;
-  const int64_t na = int64_t(d.mt) * 4 * nkc, per_batch = na + int64_t(d.nt) * nkc;
-  const int64_t bidx = local / per_batch;
-  local -= bidx * per_batch;
-  const bool sideA = local < na;
-  int64_t kc, tile;
-  int quarter = 0;
-  if (sideA) {
-    kc = local % nkc;
-    const int64_t q4 = local / nkc;
-    quarter = int(q4 & 3);
-    tile = q4 >> 2;
-  } else {
-    local -= na;
-    kc = local % nkc;
-    tile = local / nkc;
-  }
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t o0 = sideA ? tile * TC_BM + quarter * 32 : tile * TC_BN;   // first row (A) / column (B)
-  const int64_t outer = sideA ? d.M : d.N;
-  if (tid < 32) {
-    const int64_t o = o0 + tid;
-    const int* ex = sideA ? d.ex_row + bidx * d.M : d.ex_col + bidx * d.N;
-    Es[tid] = o < outer ? decode_exp(__ldcg(ex + o), args.epoch) : 0;
-  }
-  __syncthreads();
-  const double* base = sideA ? d.A + bidx * d.a_bs : d.B + bidx * d.b_bs;
-  const int64_t os = sideA ? d.a_rs : d.b_cs, is = sideA ? d.a_cs : d.b_rs;
   const uint32_t plane = sideA ? uint32_t(TC_BM * bk * 2) : uint32_t(TC_BN * bk * 2);
   uint8_t* dst = sideA ? d.pa + ((bidx * d.mt + tile) * nkc + kc) * int64_t(s) * plane
                        : d.pb + ((bidx * d.nt + tile) * nkc + kc) * int64_t(s) * plane;
@@ -337,6 +316,70 @@ __global__ void __launch_bounds__(256) tc_split_kernel(TcArgs args) {
       *reinterpret_cast<__nv_bfloat162*>(dst + q * plane + off) = h;
     }
   }
+}
+
+__global__ void __launch_bounds__(256) tc_split_kernel(TcArgs args) {
+  __shared__ int Es[32];
+  __shared__ int Emax[32];
+  const int64_t t = blockIdx.x;
+  const GemmDesc d = args.descs[find_desc(args.descs, args.ndesc, t, 2)];
+  const int s = args.s;
+  const int64_t nkc = d.nkc;
+  const int64_t per = d.lx ? 1 : nkc;                  // chunk blocks per sub-tile
+  int64_t local = t - d.split_begin;
+  const int64_t na = int64_t(d.mt) * 4 * per, per_batch = na + int64_t(d.nt) * per;
+  const int64_t bidx = local / per_batch;
+  local -= bidx * per_batch;
+  const bool sideA = local < na;
+  int64_t kc, tile;
+  int quarter = 0;
+  if (sideA) {
+    kc = local % per;
+    const int64_t q4 = local / per;
+    quarter = int(q4 & 3);
+    tile = q4 >> 2;
+  } else {
+    local -= na;
+    kc = local % per;
+    tile = local / per;
+  }
+  const int tid = threadIdx.x;
+  const int64_t o0 = sideA ? tile * TC_BM + quarter * 32 : tile * TC_BN;   // first row (A) / column (B)
+  const int64_t outer = sideA ? d.M : d.N;
+  const double* base = sideA ? d.A + bidx * d.a_bs : d.B + bidx * d.b_bs;
+  const int64_t os = sideA ? d.a_rs : d.b_cs, is = sideA ? d.a_cs : d.b_rs;
+  int* ex = sideA ? d.ex_row + bidx * d.M : d.ex_col + bidx * d.N;
+  if (!d.lx) {
+    if (tid < 32) {
+      const int64_t o = o0 + tid;
+      Es[tid] = o < outer ? decode_exp(__ldcg(ex + o), args.epoch) : 0;
+    }
+    __syncthreads();
+    split_chunk(d, s, sideA, bidx, tile, quarter, kc, o0, outer, base, os, is, Es);
+    return;
+  }
+  // short K: the largest exponent of the 32 rows / columns over all of K here
+  if (tid < 32) Emax[tid] = -1;
+  __syncthreads();
+  const int64_t tot = int64_t(32) * d.K;
+  for (int64_t e = tid; e < tot; e += blockDim.x) {
+    int64_t o, k;
+    if (is == 1) { o = e / d.K; k = e - o * d.K; }     // consecutive threads along K
+    else { k = e >> 5; o = e & 31; }                   // consecutive threads along the rows
+    if (o0 + o < outer) {
+      const int v = dexp(__ldg(base + (o0 + o) * os + k * is));
+      if (v >= 0) atomicMax(&Emax[o], v);
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int m = Emax[tid];
+    const int tag = m >= 0 ? ((args.epoch << 16) | m) : 0;
+    if (o0 + tid < outer) ex[o0 + tid] = tag;
+    Es[tid] = decode_exp(tag, args.epoch);
+  }
+  __syncthreads();
+  for (int64_t c = 0; c < nkc; ++c) split_chunk(d, s, sideA, bidx, tile, quarter, c, o0, outer, base, os, is, Es);
 }
 
 // ---- pass 3: digit products on the tensor cores
@@ -480,8 +523,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int
   const int64_t c0 = n0 + ch * 16;
   const int64_t row_off = d.c_rdiv > 0 ? (row / d.c_rdiv) * d.c_rs + (row % d.c_rdiv) * d.c_rs2 : row * d.c_rs;
   double* const crow = d.C + bidx * d.c_bs + row_off;
+  const bool plain = (d.alpha == 1.0 && d.beta == 0.0);
   auto store = [&](int j, long long H, long long Lo) {
-    store_out(crow + (c0 + j) * d.c_cs, H, Lo, Er[rr], Ec[ch * 16 + j], d.alpha, d.beta);
+    store_out(crow + (c0 + j) * d.c_cs, H, Lo, Er[rr], Ec[ch * 16 + j], plain, d.alpha, d.beta);
   };
   if (!s_fail) {
     if (d.ksplit == 1) {
@@ -581,10 +625,12 @@ void gemm_tc_prepare(std::vector<GemmDesc>& g, int s, int target_ctas, TcPlan* p
     t += base * d.ksplit;
     d.exp_begin = eb;
     const int64_t kb = ceil_div(K1, EX_IN);
-    eb += int64_t(d.batch) *
-          (ceil_div(std::max<int64_t>(d.M, 1), EX_OUT) + ceil_div(std::max<int64_t>(d.N, 1), EX_OUT)) * kb;
+    if (d.K > kLocalExpK)
+      eb += int64_t(d.batch) *
+            (ceil_div(std::max<int64_t>(d.M, 1), EX_OUT) + ceil_div(std::max<int64_t>(d.N, 1), EX_OUT)) * kb;
+    d.lx = d.K <= kLocalExpK ? 1 : 0;
     d.split_begin = sb;
-    sb += int64_t(d.batch) * (int64_t(d.mt) * 4 + d.nt) * d.nkc;
+    sb += int64_t(d.batch) * (int64_t(d.mt) * 4 + d.nt) * (d.lx ? 1 : d.nkc);
     d.ex_row = ex_base ? ex_base + ex : nullptr;
     ex += int64_t(d.batch) * d.M;
     d.ex_col = ex_base ? ex_base + ex : nullptr;
@@ -628,9 +674,11 @@ int gemm_tc_launch(const GemmDesc* d_descs, int ndesc, const TcPlan& plan, int s
     attr = true;
   }
   TcArgs a{d_descs, ndesc, s, epoch};
-  TTR_PREFER_SHARED(tc_exponent_kernel);
-  tc_exponent_kernel<<<unsigned(plan.exp_blocks), 256, 0, st>>>(a);
-  TTR_CHECK_LAUNCH();
+  if (plan.exp_blocks > 0) {
+    TTR_PREFER_SHARED(tc_exponent_kernel);
+    tc_exponent_kernel<<<unsigned(plan.exp_blocks), 256, 0, st>>>(a);
+    TTR_CHECK_LAUNCH();
+  }
   TTR_PREFER_SHARED(tc_split_kernel);
   tc_split_kernel<<<unsigned(plan.split_blocks), 256, 0, st>>>(a);
   TTR_CHECK_LAUNCH();
@@ -639,7 +687,7 @@ int gemm_tc_launch(const GemmDesc* d_descs, int ndesc, const TcPlan& plan, int s
   TTR_PREFER_SHARED(gemm_tc_kernel);
   gemm_tc_kernel<<<unsigned(plan.tiles), TC_THREADS, smem, st>>>(a, err);
   TTR_CHECK_LAUNCH();
-  prof_count_launch(3);
+  prof_count_launch(plan.exp_blocks > 0 ? 3 : 2);
   if (prof) prof_gemm_end(st, flops);
   return TT_OK;
 }

@@ -38,6 +38,7 @@ struct GemmDesc {
   int64_t nkc;          // K-chunks
   int64_t split_begin;  // prefix of the split-pass blocks
   int32_t bkc;          // K-chunk width (16, 32, 48 or 64)
+  int32_t lx;           // 1: the split pass takes the exponents itself (short K, no exponent pass)
 };
 
 constexpr int GEMM_BM = 32, GEMM_BN = 32, GEMM_BK = 16, GEMM_THREADS = 256;

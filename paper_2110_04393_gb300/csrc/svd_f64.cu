@@ -103,21 +103,32 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
     if (lane == 0) red[warp] = part;
     if (bad && tid == 0) atomicOr(&s_flag, 1);
     __syncthreads();
-    double tot = 0.0;
-    for (int i = 0; i < nwarp; ++i) tot += red[i];
     // R may carry a tiny strictly lower part L (first-order QR): with T its
     // upper triangle, sigma_min(R) >= 1 / ||T^{-1}||_F - ||L||_F
+    __shared__ double s_tot[2];
     double low = 0.0;
     for (int idx = tid; idx < k * k; idx += nt) {
       const int r = idx % k, c = idx / k;
       if (r > c) low = fma(A[r + c * k], A[r + c * k], low);
     }
     low = warp_sum(low);
+    // one thread sums the per-warp partials (an FP64 chain per warp would cost
+    // every warp the FP64 pipe for the whole chain)
+    if (tid == 0) {
+      double t0 = 0.0;
+      for (int i = 0; i < nwarp; ++i) t0 += red[i];
+      s_tot[0] = t0;
+    }
     __syncthreads();
     if (lane == 0) red[warp] = low;
     __syncthreads();
-    double ltot = 0.0;
-    for (int i = 0; i < nwarp; ++i) ltot += red[i];
+    if (tid == 0) {
+      double t1 = 0.0;
+      for (int i = 0; i < nwarp; ++i) t1 += red[i];
+      s_tot[1] = t1;
+    }
+    __syncthreads();
+    const double tot = s_tot[0], ltot = s_tot[1];
     const bool certified = !s_flag && isfinite(tot) && tot > 0.0 && (1.0 / sqrt(tot)) - sqrt(ltot) > 2.0 * eps;
     __syncthreads();
     if (certified) {
