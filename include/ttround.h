@@ -177,6 +177,30 @@ int tt_sum_plan_destroy(tt_sum_plan* plan);
 int64_t tt_sum_plan_launches(const tt_sum_plan* plan);
 
 /*
+ * Host-buffer replays of a plan (same computation as tt_sum_plan_run). Packed
+ * host layout: the input is one array of all summand cores, summand-major
+ * then core-major, core (j, n) row-major (r_{n-1}, I_n, r_n) at element offset
+ * in_offsets[j*N + n-1]; the output is one array of N slots, slot n at
+ * out_offsets[n-1] with room for the clamped sketch-rank core, the rounded
+ * core written compactly at the slot's start (shape out_ranks[n-1], I_n,
+ * out_ranks[n]). tt_sum_plan_host_layout fills any of its non-NULL
+ * arguments: in_offsets (K*N), out_offsets (N), in_total and out_total
+ * (elements). tt_sum_plan_run_host copies h_in (in_total doubles, host) to a
+ * plan-owned device buffer with one copy, replays the plan and copies the
+ * out_total doubles of slots back to h_out (host) with one copy, then waits
+ * for the stream: on return h_out and out_ranks hold the result. Pinned host
+ * memory gives asynchronous full-speed copies; pageable memory works but is
+ * staged by the CUDA runtime. The first call allocates the device landing
+ * buffers (TT_ENOMEM if that fails).
+ * Errors: TT_EINVAL for a NULL plan, h_in, h_out or out_ranks; as
+ * tt_sum_plan_run otherwise.
+ */
+int tt_sum_plan_host_layout(const tt_sum_plan* plan, int64_t* in_offsets, int64_t* out_offsets, int64_t* in_total,
+                            int64_t* out_total);
+int tt_sum_plan_run_host(tt_sum_plan* plan, const double* h_in, const double* coeffs, uint64_t seed, double* h_out,
+                         int64_t* out_ranks, void* stream);
+
+/*
  * Batched plans: B independent sum roundings (the uneven sums of TT-GMRES,
  * Section 4.2) in one CUDA graph. Problem b (its N, K, dims, ranks K x (N+1),
  * ells N+1 and tol, as for tt_sum_plan_create) runs on chain b mod width of the

@@ -246,6 +246,52 @@ class SumRoundingPlan:
         r = [int(x) for x in out_ranks]
         return [out[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)]
 
+    def host_layout(self):
+        """(in_offsets K*N, out_offsets N, in_total, out_total) of the packed
+        host arrays of run_host, in float64 elements."""
+        io = (ctypes.c_int64 * (self.K * self.N))()
+        oo = (ctypes.c_int64 * self.N)()
+        it, ot = ctypes.c_int64(), ctypes.c_int64()
+        _check(nat.lib().tt_sum_plan_host_layout(self._h, io, oo, ctypes.byref(it), ctypes.byref(ot)))
+        return list(io), list(oo), int(it.value), int(ot.value)
+
+    def pack_host(self, summands, *, pin=True):
+        """One packed float64 host array (pinned by default) of the summands'
+        cores (K lists of N arrays / CPU tensors of the plan's shapes)."""
+        io, _, it, _ = self.host_layout()
+        buf = torch.empty(max(it, 1), dtype=torch.float64, pin_memory=pin)
+        if len(summands) != self.K:
+            raise ValueError("summands do not match the plan's sizes and ranks")
+        for j, Y in enumerate(summands):
+            for n, c in enumerate(Y):
+                t = torch.as_tensor(c, dtype=torch.float64).reshape(-1)
+                R = self.summand_ranks[j]
+                if t.numel() != R[n] * self.dims[n] * R[n + 1]:
+                    raise ValueError("summands do not match the plan's sizes and ranks")
+                buf[io[j * self.N + n]:io[j * self.N + n] + t.numel()].copy_(t)
+        return buf
+
+    def run_host(self, h_in, *, seed=0, coeffs=None, out=None, stream=None):
+        """Replay on host buffers: h_in from pack_host (float64 CPU tensor of
+        in_total elements, pinned for full-speed copies), out a float64 CPU
+        tensor of out_total elements (allocated pinned if None). One copy in,
+        the graph, one copy out; returns the rounded cores as views of out."""
+        _, oo, it, ot = self.host_layout()
+        if h_in.dtype != torch.float64 or h_in.device.type != "cpu" or not h_in.is_contiguous() or h_in.numel() < it:
+            raise ValueError("h_in must be a contiguous float64 CPU tensor of in_total elements")
+        if out is None:
+            out = torch.empty(max(ot, 1), dtype=torch.float64, pin_memory=True)
+        if out.dtype != torch.float64 or out.device.type != "cpu" or not out.is_contiguous() or out.numel() < ot:
+            raise ValueError("out must be a contiguous float64 CPU tensor of out_total elements")
+        co = None if coeffs is None else (ctypes.c_double * self.K)(*[float(c) for c in coeffs])
+        out_ranks = (ctypes.c_int64 * (self.N + 1))()
+        _check(nat.lib().tt_sum_plan_run_host(self._h, ctypes.c_void_p(h_in.data_ptr()), co,
+                                              ctypes.c_uint64(int(seed)), ctypes.c_void_p(out.data_ptr()), out_ranks,
+                                              _stream(stream, self.device)))
+        r = [int(x) for x in out_ranks]
+        d = self.dims
+        return [out[oo[n]:oo[n] + r[n] * d[n] * r[n + 1]].view(r[n], d[n], r[n + 1]) for n in range(self.N)]
+
     def close(self):
         if getattr(self, "_h", None):
             nat.lib().tt_sum_plan_destroy(self._h)

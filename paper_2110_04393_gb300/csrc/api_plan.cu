@@ -82,6 +82,10 @@ struct SumUnit {
   int64_t* dims = nullptr;
   int ngb = 0, nsb = 0;
   size_t stage_off = 0;
+  std::vector<int64_t> h_in_off, h_out_off;   // packed host layout (elements)
+  int64_t in_total = 0, out_total = 0;
+  double* land_in = nullptr;                  // device landing of the host input copy
+  double* land_out = nullptr;                 // device source of the host output copy
 };
 
 size_t unit_stage_bytes(int N, int K) {
@@ -93,6 +97,9 @@ void unit_free(SumUnit* u) {
   if (u->in_buf) cudaFree(u->in_buf);
   if (u->out_buf) cudaFree(u->out_buf);
   if (u->tables) cudaFree(u->tables);
+  if (u->land_in) cudaFree(u->land_in);
+  if (u->land_out) cudaFree(u->land_out);
+  u->land_in = u->land_out = nullptr;
   u->in_buf = u->out_buf = nullptr;
   u->tables = nullptr;
 }
@@ -120,6 +127,10 @@ int unit_init(SumUnit* u, int32_t N, int32_t K, const int64_t* dims, const int64
     tot += out_sizes.back();
   }
   const int64_t out_total = tot;
+  u->h_in_off = in_off;
+  u->h_out_off = out_off;
+  u->in_total = in_total;
+  u->out_total = out_total;
   if (cudaMalloc(&u->in_buf, sizeof(double) * std::max<int64_t>(in_total, 1)) != cudaSuccess ||
       cudaMalloc(&u->out_buf, sizeof(double) * std::max<int64_t>(out_total, 1)) != cudaSuccess) {
     cudaGetLastError();
@@ -395,6 +406,54 @@ int tt_sum_plan_run(tt_sum_plan* p, const double* const* cores, const double* co
   TTR_TRY(unit_fill_stage(u, static_cast<char*>(p->g.h_stage) + u->stage_off, cores, coeffs, seed, out));
   int64_t* const rk[1] = {out_ranks};
   return unit_graph_run(&p->g, static_cast<cudaStream_t>(stream), rk);
+}
+
+int tt_sum_plan_host_layout(const tt_sum_plan* p, int64_t* in_offsets, int64_t* out_offsets, int64_t* in_total,
+                            int64_t* out_total) {
+  if (!p) {
+    set_error("tt_sum_plan_host_layout: null plan");
+    return TT_EINVAL;
+  }
+  const SumUnit* u = p->g.units[0];
+  if (in_offsets) std::copy(u->h_in_off.begin(), u->h_in_off.end(), in_offsets);
+  if (out_offsets) std::copy(u->h_out_off.begin(), u->h_out_off.end(), out_offsets);
+  if (in_total) *in_total = u->in_total;
+  if (out_total) *out_total = u->out_total;
+  return TT_OK;
+}
+
+int tt_sum_plan_run_host(tt_sum_plan* p, const double* h_in, const double* coeffs, uint64_t seed, double* h_out,
+                         int64_t* out_ranks, void* stream) {
+  if (!p || !h_in || !h_out || !out_ranks) {
+    set_error("tt_sum_plan_run_host: null argument");
+    return TT_EINVAL;
+  }
+  SumUnit* u = p->g.units[0];
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!u->land_in) {
+    if (cudaMalloc(&u->land_in, sizeof(double) * std::max<int64_t>(u->in_total, 1)) != cudaSuccess ||
+        cudaMalloc(&u->land_out, sizeof(double) * std::max<int64_t>(u->out_total, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("tt_sum_plan_run_host: landing buffer allocation failed");
+      return TT_ENOMEM;
+    }
+  }
+  const int N = u->P.N, K = u->P.K;
+  std::vector<const double*> cores(size_t(K) * N);
+  std::vector<double*> outs(N);
+  for (size_t i = 0; i < cores.size(); ++i) cores[i] = u->land_in + u->h_in_off[i];
+  for (int n = 0; n < N; ++n) outs[n] = u->land_out + u->h_out_off[n];
+  TTR_CHECK_CUDA(cudaEventSynchronize(p->g.staged));
+  TTR_TRY(unit_fill_stage(u, static_cast<char*>(p->g.h_stage) + u->stage_off, cores.data(), coeffs, seed,
+                          outs.data()));
+  if (u->in_total > 0)
+    TTR_CHECK_CUDA(cudaMemcpyAsync(u->land_in, h_in, sizeof(double) * u->in_total, cudaMemcpyHostToDevice, s));
+  int64_t* const rk[1] = {out_ranks};
+  TTR_TRY(unit_graph_run(&p->g, s, rk));
+  if (u->out_total > 0)
+    TTR_CHECK_CUDA(cudaMemcpyAsync(h_out, u->land_out, sizeof(double) * u->out_total, cudaMemcpyDeviceToHost, s));
+  TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  return TT_OK;
 }
 
 int tt_sum_plan_destroy(tt_sum_plan* p) {

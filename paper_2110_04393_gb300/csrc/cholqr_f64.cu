@@ -73,48 +73,57 @@ __device__ __forceinline__ bool pivot_ok(double d) {
 // In-place right-looking Cholesky of G (k x k row-major, lower part) with
 // X := L^{-1} formed alongside; returns false on a non-positive pivot. FP64
 // issues a dependent operation only every ~65 cycles on GB300 and a reciprocal
-// square root takes ~400, so the pivots are the critical path. Thread 0 only
-// updates the next diagonal entry and takes its reciprocal square root; the
-// trailing updates (the lower triangle of G below the pivot and the rows of X
-// below it) are packed densely over the warps of the other three SM
-// sub-partitions (warp % 4 != 0), so no update queues on the FP64 pipe that
-// thread 0 uses. Two block barriers per step. colj: k doubles of scratch.
+// square root takes ~400, so the pivot chain is the critical path, and every
+// step has exactly one block barrier:
+//   * thread 0 (alone on its SM sub-partition) turns the still unscaled
+//     column entry g = G(j+1, j) into the next pivot d = G(j+1, j+1) -
+//     (g rd_j)^2 and its reciprocal square root rd_{j+1};
+//   * meanwhile the other three sub-partitions update the trailing lower
+//     triangle G(i, l) -= (G(i, j) rd_j)(G(l, j) rd_j) and the rows of X below
+//     j, X(i, c) -= G(i, j) rd_j^2 X(j, c) with X's row j still unscaled, all
+//     packed densely over lanes, and finalise the previous step's column of L
+//     (G(i, j-1) rd_{j-1}) and row of X (X(j-1, :) rd_{j-1}), which no step
+//     reads any more.
+// rd and the pivot test are double-buffered across the barrier.
 // blockDim.x must be a multiple of 128.
-__device__ bool chol_with_inverse(double* G, double* X, double* colj, int k, double* s_rd, int* s_bad) {
+__device__ bool chol_with_inverse(double* G, double* X, int k) {
+  __shared__ double rdb[2];
+  __shared__ int badb[2];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
   const bool worker = (warp & 3) != 0;
-  const int nwk = (nt >> 5) / 4 * 3 * 32;                      // worker threads
+  const int nwk = (nt >> 5) / 4 * 3 * 32;                           // worker threads
   const int wid = ((warp >> 2) * 3 + (warp & 3) - 1) * 32 + lane;   // valid for workers
   for (int e = tid; e < k * k; e += nt) X[e] = (e % (k + 1) == 0) ? 1.0 : 0.0;
   if (tid == 0) {
     const double d = G[0];
     const bool bad = !pivot_ok(d);
-    *s_bad = bad ? 1 : 0;
-    *s_rd = bad ? 1.0 : rsqrt(d);
+    badb[0] = bad ? 1 : 0;
+    rdb[0] = bad ? 1.0 : rsqrt(d);
   }
   __syncthreads();
+  double rprev = 1.0;
   for (int j = 0; j < k; ++j) {
-    if (*s_bad) return false;
-    const double rd = *s_rd;
+    if (badb[j & 1]) return false;
+    const double rd = rdb[j & 1];
+    const double rd2 = rd * rd;
     const int n = k - j - 1;                      // rows / columns below the pivot
-    // column j of L (scaled), the diagonal, and row j of X
-    if (worker)
-      for (int e = wid; e <= n + j; e += nwk) {
-        if (e < n) colj[j + 1 + e] = G[(j + 1 + e) * k + j] * rd;
-        else X[j * k + (e - n)] *= rd;
-      }
-    if (tid == 0) G[j * k + j] *= rd;
-    __syncthreads();
     const int ng = n * (n + 1) / 2, nx = n * (j + 1);
     if (tid == 0) {
+      G[j * k + j] = G[j * k + j] * rd;           // L(j, j) = sqrt(d_j)
       if (n > 0) {
-        const double d = fma(-colj[j + 1], colj[j + 1], G[(j + 1) * k + j + 1]);
+        const double g = G[(j + 1) * k + j] * rd;
+        const double d = fma(-g, g, G[(j + 1) * k + j + 1]);
         G[(j + 1) * k + j + 1] = d;
         const bool bad = !pivot_ok(d);
-        *s_bad = bad ? 1 : 0;
-        *s_rd = bad ? 1.0 : rsqrt(d);
+        badb[(j + 1) & 1] = bad ? 1 : 0;
+        rdb[(j + 1) & 1] = bad ? 1.0 : rsqrt(d);
       }
     } else if (worker) {
+      // the previous step's column of L and row of X are final now
+      if (j > 0) {
+        for (int i = j + wid; i < k; i += nwk) G[i * k + (j - 1)] *= rprev;
+        for (int c = wid; c < j; c += nwk) X[(j - 1) * k + c] *= rprev;
+      }
       // entry 0 of the packed lower triangle is the next diagonal (thread 0's)
       for (int e = wid + 1; e < ng + nx; e += nwk) {
         if (e < ng) {
@@ -122,17 +131,20 @@ __device__ bool chol_with_inverse(double* G, double* X, double* colj, int k, dou
           while (ip * (ip + 1) / 2 > e) --ip;
           while ((ip + 1) * (ip + 2) / 2 <= e) ++ip;
           const int i = j + 1 + ip, l = j + 1 + (e - ip * (ip + 1) / 2);
-          G[i * k + l] = fma(-colj[i], colj[l], G[i * k + l]);
+          G[i * k + l] = fma(-(G[i * k + j] * rd2), G[l * k + j], G[i * k + l]);
         } else {
           const int e2 = e - ng;
           const int i = j + 1 + e2 / (j + 1), c = e2 % (j + 1);
-          X[i * k + c] = fma(-colj[i], X[j * k + c], X[i * k + c]);
+          X[i * k + c] = fma(-(G[i * k + j] * rd2), X[j * k + c], X[i * k + c]);
         }
       }
-      for (int i = j + 1 + wid; i < k; i += nwk) G[i * k + j] = colj[i];   // rows j+1.. of column j
     }
+    rprev = rd;
     __syncthreads();
   }
+  // the last step's column of L is empty; its row of X needs the scaling
+  for (int c = tid; c < k; c += nt) X[(k - 1) * k + c] *= rprev;
+  __syncthreads();
   return true;
 }
 
@@ -146,9 +158,7 @@ __device__ __forceinline__ void tri_ij(int p, int k, int* i, int* j) {
 
 __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   extern __shared__ double sm[];
-  __shared__ int s_last, s_bad;
-  __shared__ double s_rd;
-  __shared__ double s_col[CQ_SMEM_K];
+  __shared__ int s_last;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int k = a.k, b = a.b;
   if (__ldcg(a.status + 2)) return;                         // chain already finished
@@ -268,7 +278,6 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   double* G = big ? a.big : sm;                 // k x k
   double* X = G + k * k;                        // k x k
   double* G0 = X + k * k;                       // k x k
-  double* colj = big ? G0 + k * k : s_col;      // k
   for (int p = tid; p < npair; p += nt) {
     const double* base = a.Gpart + int64_t(a.P) * npair + p;
     double acc = 0.0;
@@ -378,7 +387,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
       return;
     }
   }
-  bool ok = chol_with_inverse(G, X, colj, k, &s_rd, &s_bad);
+  bool ok = chol_with_inverse(G, X, k);
   bool shifted = false;
   if (!ok) {
     __shared__ double s_shift;
@@ -390,7 +399,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
     __syncthreads();
     for (int idx = tid; idx < k * k; idx += nt) G[idx] = G0[idx] + (((idx / k) == (idx % k)) ? s_shift : 0.0);
     __syncthreads();
-    ok = chol_with_inverse(G, X, colj, k, &s_rd, &s_bad);
+    ok = chol_with_inverse(G, X, k);
     shifted = true;
   }
   if (!ok) {                                    // not even the shifted Gram is positive definite
@@ -471,7 +480,7 @@ QrPool qr_pool_reserve(Arena& ar, const std::vector<std::pair<int64_t, int>>& sh
     gp = std::max<size_t>(gp, size_t(P + (P + 15) / 16) * k * k);
     kk = std::max<size_t>(kk, size_t(k) * k);
     mk = std::max<size_t>(mk, size_t(m) * k);
-    if (k > CQ_SMEM_K) bigk = std::max<size_t>(bigk, 3 * size_t(k) * k + size_t(k));
+    if (k > CQ_SMEM_K) bigk = std::max<size_t>(bigk, 3 * size_t(k) * k);
     st = std::max<size_t>(st, size_t(ns));
     if (k <= TSQR_KMAX) {
       size_t ii = 0;

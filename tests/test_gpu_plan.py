@@ -49,3 +49,34 @@ def test_plan_rejects_mismatched_summands():
     with pytest.raises(ValueError):
         plan(Yd[:3])
     plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-8), ("fp64", 0.0)])
+def test_plan_host_buffers_match_device_run(precision, tol):
+    """run_host (one packed copy in, replay, one copy out) returns bit-wise the
+    device replay's cores, at the slots of the packed host layout."""
+    N = len(DIMS)
+    ell = const_ranks(N, 20)
+    plan = tt.SumRoundingPlan(DIMS, [const_ranks(N, r) for r in RANKS], ell, tol=tol, precision=precision)
+    io, oo, it, ot = plan.host_layout()
+    assert len(io) == len(RANKS) * N and len(oo) == N
+    R = [const_ranks(N, r) for r in RANKS]
+    assert it == sum(Rj[n] * DIMS[n] * Rj[n + 1] for Rj in R for n in range(N))
+    assert ot == sum(plan.ell[n] * DIMS[n] * plan.ell[n + 1] for n in range(N))
+    assert io[0] == 0 and oo[0] == 0
+    Yd = _summands(303)
+    h_in = plan.pack_host([[c.cpu() for c in Y] for Y in Yd])
+    assert h_in.is_pinned()
+    coeffs = [0.5, 1.0, -1.5, 2.0]
+    Xh = plan.run_host(h_in, seed=11, coeffs=coeffs)
+    Xd = plan(Yd, seed=11, coeffs=coeffs)
+    torch.cuda.synchronize()
+    assert _same(Xh, [x.cpu() for x in Xd])
+    # the second replay reuses the landing buffers
+    Xh2 = plan.run_host(h_in, seed=12)
+    Xd2 = plan(Yd, seed=12)
+    torch.cuda.synchronize()
+    assert _same(Xh2, [x.cpu() for x in Xd2])
+    with pytest.raises(ValueError):
+        plan.run_host(h_in[:10])
+    plan.close()
