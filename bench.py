@@ -39,8 +39,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--no-det", action="store_true", help="skip the deterministic comparison")
-    p.add_argument("--config", default="sum", choices=["sum", "batched"],
-                   help="sum: 20 TTs, N=50 (default); batched: 256 uneven sums in one graph")
+    p.add_argument("--config", default="sum", choices=["sum", "batched", "large"],
+                   help="sum: 20 TTs, N=50 (default); batched: 256 uneven sums in one graph; "
+                        "large: 30 TTs, N=30, I=256, rank 20")
     return p.parse_args()
 
 
@@ -455,12 +456,93 @@ def run_batched(a):
     plan.close()
 
 
+LARGE = dict(workload="sum of K=30 TT-tensors, N=30, I_n=256, rank 20 each (formal rank 600), sketch rank 70 "
+                      "(Two-Sided 70 / 105), tol 1e-6, Gaussian cores (Definition 3.1 scaling, drawn on the device)",
+             K=30, N=30, I=256, R=20, ell=70, rho=105, tol=1e-6)
+
+
+def run_large(a):
+    """The large sum: Randomize-then-Orthogonalize through captured plans in
+    both precisions, Two-Sided (fixed ranks) and the deterministic rounding of
+    the formed sum (about 22 GB of cores), on the same device-resident inputs
+    (0.74 GB, larger than L2, so no flush)."""
+    import torch
+    import paper_2110_04393_gb300 as tt
+    from paper_2110_04393_gb300.costs import flops_sum_randorth, flops_det
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    dev = torch.device("cuda", 0)
+    K, N, I, R = LARGE["K"], LARGE["N"], LARGE["I"], LARGE["R"]
+    dims = [I] * N
+    rk = [1] + [R] * (N - 1) + [1]
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    Yd = [[torch.randn((rk[n], I, rk[n + 1]), dtype=torch.float64, device=dev, generator=g)
+           / (rk[n] * I * rk[n + 1]) ** 0.5 for n in range(N)] for _ in range(K)]
+    ranks = [rk] * K
+    ell = tt.clamp_ranks(dims, [1] + [LARGE["ell"]] * (N - 1) + [1])
+    rho = tt.clamp_ranks(dims, [1] + [LARGE["rho"]] * (N - 1) + [1])
+    tol = LARGE["tol"]
+    flops = flops_sum_randorth(dims, ranks, ell)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps, warm):
+        for w in range(warm):
+            fn(1000 + w)
+        torch.cuda.synchronize()
+        ts = []
+        for s in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn(s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), out
+
+    variants = {}
+    with Clocks(0) as clk:
+        for prec in ("mixed", "fp64"):
+            plan = tt.SumRoundingPlan(dims, ranks, ell, tol=tol, precision=prec, device=dev)
+            ms, X = timed(lambda s: plan(Yd, seed=s), a.steps, a.warmup)
+            variants["rand_" + prec] = {"ms_per_step": ms, "tflops_alg": flops / (ms * 1e-3) / 1e12,
+                                        "output_ranks_max": max(int(c.shape[2]) for c in X), "graph_replay": True,
+                                        "launches_per_step": plan.launches}
+            plan.close()
+        ms, X = timed(lambda s: tt.tt_round_twosided(Yd, ell, rhos=rho, seed=s), 2, 1)
+        variants["twosided_fp64"] = {"ms_per_step": ms, "eager": True}
+        if not a.no_det:
+            ms, Xd = timed(lambda s: tt.tt_round_det(Yd, tol=tol), 1, 0)
+            dr = [int(Xd[0].shape[0])] + [int(c.shape[2]) for c in Xd]
+            S = [1] + [K * R] * (N - 1) + [1]
+            S[1] = min(S[1], dims[0])
+            for n in range(N - 1, 0, -1):
+                S[n] = min(S[n], dims[n] * S[n + 1])
+            dfl = flops_det(dims, S, dr)
+            variants["det_fp64"] = {"ms_per_step": ms, "tflops_alg": dfl / (ms * 1e-3) / 1e12,
+                                    "gflop_alg": dfl / 1e9, "output_ranks_max": max(dr),
+                                    "rand_mixed_speedup": ms / variants["rand_mixed"]["ms_per_step"]}
+    t = variants["rand_mixed"]["ms_per_step"]
+    print(json.dumps({"metric": METRIC.replace("sum of 20 TTs, N=50", "sum of 30 TTs, N=30, I=256"),
+                      "value": flops / (t * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": a.steps,
+                      "warmup": a.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": dict(LARGE, precision="mixed", l2="inputs (0.74 GB) exceed L2",
+                                     algorithmic_gflop_per_step=flops / 1e9,
+                                     execution="captured CUDA graph per precision, replayed per step"),
+                      "clocks": clk.summary(), "variants": variants}), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.config == "batched":
         run_batched(a)
+    elif a.config == "large":
+        run_large(a)
     else:
         run_ours(a)
 
