@@ -70,14 +70,16 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
   }
   double* T = ar.take<double>(tmax);
   double* Z = ar.take<double>(zmax);
-  double* Am = ar.take<double>(amax);
-  double* Qt = ar.take<double>(amax);
-  double* Rb = ar.take<double>(kmax * kmax);
-  double* G1 = ar.take<double>(kmax * kmax);
-  double* G2 = ar.take<double>(kmax * kmax);
-  double* sig = ar.take<double>(kmax);
-  double* sbig = ar.take<double>(std::max<size_t>(svd_scratch_doubles(int(kmax)), 1));
-  int64_t* rdummy = ar.take<int64_t>(1);
+  // per bond (the bond SVDs are independent and run in one launch)
+  const int64_t nb = std::max(N - 1, 1);
+  double* Am = ar.take<double>(amax * nb);
+  double* Qt = ar.take<double>(amax * nb);
+  double* Rb = ar.take<double>(kmax * kmax * nb);
+  double* G1 = ar.take<double>(kmax * kmax * nb);
+  double* G2 = ar.take<double>(kmax * kmax * nb);
+  double* sig = ar.take<double>(kmax * nb);
+  double* kd = ar.take<double>(nb);
+  double* sbig = ar.take<double>(std::max<size_t>(svd_scratch_doubles(int(kmax)) * size_t(nb), 1));
   std::vector<std::pair<int64_t, int>> shapes;
   for (int n = 1; n < N; ++n) shapes.push_back({rho[n], int(ell[n])});
   const QrPool pool = qr_pool_reserve(ar, shapes);
@@ -139,25 +141,40 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
     sc.gemm({gdesc(Z, In(n) * rho[n], 1, Rs[n], 1, In(n) * rho[n], WR[n - 1], rho[n - 1], 1, S[n - 1], rho[n - 1],
                    In(n) * rho[n])});
   }
-  // ---- per bond: SVD of W^L_n W^R_n and the factors L_n, R_n
+  // ---- per bond: SVD of W^L_n W^R_n and the factors L_n, R_n. First every
+  // bond's product and thin QR, then all bond SVDs in one launch (one block
+  // each), then the factors.
   const double eps52 = std::ldexp(1.0, -52);
+  auto bAm = [&](int n) { return Am ? Am + amax * (n - 1) : nullptr; };
+  auto bQt = [&](int n) { return Qt ? Qt + amax * (n - 1) : nullptr; };
+  auto bK2 = [&](double* base, int n) { return base ? base + kmax * kmax * (n - 1) : nullptr; };
   for (int n = 1; n < N; ++n) {
     const int64_t l = ell[n], r = rho[n];
-    sc.gemm({gdesc(WL[n], S[n], 1, WR[n], r, 1, Am, r, 1, l, r, S[n])});
+    sc.gemm({gdesc(WL[n], S[n], 1, WR[n], r, 1, bAm(n), r, 1, l, r, S[n])});
     // thin QR of A^T (r x l, a strided view of A)
-    qr_plan(sc, qr_view(pool, r, int(l)), Am, 1, r, Qt, l, 1, Rb);
-    sc.add([=](cudaStream_t s) -> int {
-      return svd_trunc_launch(int(l), Rb, nullptr, int(l), G1, G2, sig, rdummy, s, sbig);
-    });
+    qr_plan(sc, qr_view(pool, r, int(l)), bAm(n), 1, r, bQt(n), l, 1, bK2(Rb, n));
+  }
+  if (N > 1) {
+    std::vector<double> ks;
+    for (int n = 1; n < N; ++n) ks.push_back(double(ell[n]));
+    sc.upload(kd, ks);
+    const int nbonds = N - 1, km = int(kmax);
+    sc.add([=](cudaStream_t s) -> int { return svd_batch_launch(nbonds, km, kd, Rb, G1, G2, sig, s, sbig); });
+  }
+  for (int n = 1; n < N; ++n) {
+    const int64_t l = ell[n], r = rho[n];
+    double* am = bAm(n);
+    double* g2 = bK2(G2, n);
+    const double* sg = sig ? sig + kmax * (n - 1) : nullptr;
     const double tol_rel = double(std::max(l, r)) * eps52;
     // P1 = Q U_R S^{+1/2} into Am (r x l)
-    sc.gemm({gdesc(Qt, l, 1, G1, l, 1, Am, l, 1, r, l, l)});
+    sc.gemm({gdesc(bQt(n), l, 1, bK2(G1, n), l, 1, am, l, 1, r, l, l)});
     sc.add([=](cudaStream_t s) -> int {
-      TTR_TRY(colscale_launch(Am, r, l, l, sig, -0.5, tol_rel, s));
-      return colscale_launch(G2, l, l, l, sig, -1.5, tol_rel, s);    // V_R S^{+1/2} = G2 S^{-3/2}
+      TTR_TRY(colscale_launch(am, r, l, l, sg, -0.5, tol_rel, s));
+      return colscale_launch(g2, l, l, l, sg, -1.5, tol_rel, s);    // V_R S^{+1/2} = G2 S^{-3/2}
     });
-    sc.gemm({gdesc(WR[n], r, 1, Am, l, 1, Lf[n], l, 1, S[n], l, r)});         // L_n = W^R_n P1
-    sc.gemm({gdesc(G2, 1, l, WL[n], S[n], 1, Rf[n], S[n], 1, l, S[n], l)});  // R_n = P2^T W^L_n
+    sc.gemm({gdesc(WR[n], r, 1, am, l, 1, Lf[n], l, 1, S[n], l, r)});         // L_n = W^R_n P1
+    sc.gemm({gdesc(g2, 1, l, WL[n], S[n], 1, Rf[n], S[n], 1, l, S[n], l)});  // R_n = P2^T W^L_n
   }
   // ---- distribution of the factors into the cores
   for (int n = 1; n <= N; ++n) {

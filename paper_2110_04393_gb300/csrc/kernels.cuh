@@ -112,6 +112,12 @@ int tsqr_launch(const TsqrShape& sh, const TsqrWork& w, const double* A, int64_t
 size_t svd_scratch_doubles(int k);
 int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, double* G1, double* G2,
                      double* sigma, int64_t* rank_out, cudaStream_t s, double* big = nullptr);
+// B independent full SVDs (no truncation) in one launch, one block each: job b
+// has k_b = kd[b] (a device array of doubles) <= kmax, R_b, G1_b, G2_b at
+// b * kmax * kmax and sigma_b at b * kmax; kmax > 96 needs B * svd_scratch_doubles(kmax)
+// doubles of global scratch.
+int svd_batch_launch(int B, int kmax, const double* kd, const double* R, double* G1, double* G2, double* sigma,
+                     cudaStream_t s, double* big);
 
 // ----------------------------------------------------------------------------
 // Elementwise helpers.

@@ -28,10 +28,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const double* __restrict__ R,
-                                                                const double* __restrict__ eps_ptr, int rcap,
-                                                                double* G1, double* G2, double* sigma,
-                                                                int64_t* rank_out, double* big) {
+// One SVD per block. The input is scaled by the power of two 2^-sh that puts
+// max |R| in [1, 2) (exact), and sigma, G2 and the threshold are taken back by
+// 2^sh: sums of squares of Gaussian-TT products can otherwise underflow, which
+// stalls the Jacobi convergence test. rank_out may be null.
+__device__ __forceinline__ void svd_trunc_body(int k, const double* __restrict__ R, const double* __restrict__ eps_ptr, int rcap,
+                               double* G1, double* G2, double* sigma, int64_t* rank_out, double* big) {
   extern __shared__ double sm[];
   const int kk = k + (k & 1);        // even number of columns for the round-robin schedule
   double* base = big ? big : sm;     // global scratch above SVD_SMEM_K
@@ -44,13 +46,29 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
   int* order = big ? reinterpret_cast<int*>(red + 32) : order_s;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
-  const double eps = eps_ptr ? *eps_ptr : 0.0;
 
+  __shared__ int s_emax;
+  if (tid == 0) s_emax = -2000;
+  __syncthreads();
+  int em = -2000;
   for (int idx = tid; idx < k * kk; idx += nt) {
     const int r = idx % k, c = idx / k;
-    A[r + c * k] = (c < k) ? R[r * k + c] : 0.0;
+    const double v = (c < k) ? R[r * k + c] : 0.0;
+    A[r + c * k] = v;
+    const int e = int((uint64_t(__double_as_longlong(v)) >> 52) & 0x7FF);
+    if (e != 0 && e != 0x7FF) em = max(em, e - 1023);
   }
+  em = __reduce_max_sync(0xffffffffu, em);
+  if (lane == 0) atomicMax(&s_emax, em);
   __syncthreads();
+  const int sh = (s_emax == -2000) ? 0 : max(-1022, min(1022, s_emax));
+  const double dn = __longlong_as_double((long long)(uint64_t(1023 - sh) << 52));   // 2^-sh
+  const double up = __longlong_as_double((long long)(uint64_t(1023 + sh) << 52));   // 2^sh
+  if (sh != 0) {
+    for (int idx = tid; idx < k * kk; idx += nt) A[idx] *= dn;
+    __syncthreads();
+  }
+  const double eps = (eps_ptr ? *eps_ptr : 0.0) * dn;
 
   // ---- certificate: sigma_min(R) >= 1/||R^{-1}||_F > 2 eps  =>  nothing is cut
   if (eps_ptr != nullptr && rcap >= k) {
@@ -135,10 +153,10 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
       for (int idx = tid; idx < k * k; idx += nt) {
         const int r = idx / k, c = idx % k;
         G1[idx] = (r == c) ? 1.0 : 0.0;
-        G2[idx] = A[c + r * k];            // R^T
+        G2[idx] = R[c * k + r];            // R^T
       }
       for (int i = tid; i < k; i += nt) sigma[i] = -1.0;   // not computed
-      if (tid == 0) *rank_out = k;
+      if (tid == 0 && rank_out) *rank_out = k;
       return;
     }
   }
@@ -147,6 +165,10 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
   for (int idx = tid; idx < kk * kk; idx += nt) Vm[idx] = ((idx % kk) == (idx / kk)) ? 1.0 : 0.0;
   __syncthreads();
   const int npairs = kk / 2;
+  // a pair is orthogonal once |gamma| <= k u sqrt(alpha beta): the rounding of a
+  // k-term dot product alone reaches ~sqrt(k) u, so a fixed threshold near u
+  // would keep rotating noise until the sweep limit for larger k
+  const double jtol = fmax(2e-15, double(k) * 0x1p-52);
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
@@ -165,7 +187,7 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
           ga = fma(x, y, ga);
         }
         al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (ga == 0.0 || fabs(ga) <= 2e-15 * sqrt(al * be)) continue;
+        if (ga == 0.0 || fabs(ga) <= jtol * sqrt(al * be)) continue;
         const double zeta = (be - al) / (2.0 * ga);
         const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
         const double c = 1.0 / sqrt(fma(t, t, 1.0));
@@ -214,7 +236,7 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
     if (r > rcap) r = rcap;
     if (r < 1) r = 1;
     s_rank = r;
-    *rank_out = r;
+    if (rank_out) *rank_out = r;
   }
   __syncthreads();
   const int r = s_rank;
@@ -225,12 +247,33 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const dou
       const int c = order[t];
       const double s = sv[c];
       g1 = (s > 0.0) ? A[row + c * k] / s : (row == t ? 1.0 : 0.0);
-      g2 = Vm[row + c * kk] * s;
+      g2 = Vm[row + c * kk] * s * up;
     }
     G1[idx] = g1;
     G2[idx] = g2;
   }
-  for (int t = tid; t < k; t += nt) sigma[t] = sv[order[t]];
+  for (int t = tid; t < k; t += nt) sigma[t] = sv[order[t]] * up;
+}
+
+__global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const double* __restrict__ R,
+                                                                const double* __restrict__ eps_ptr, int rcap,
+                                                                double* G1, double* G2, double* sigma,
+                                                                int64_t* rank_out, double* big) {
+  svd_trunc_body(k, R, eps_ptr, rcap, G1, G2, sigma, rank_out, big);
+}
+
+// B independent full SVDs (no truncation), block b on job b: k_b = kd[b]
+// (stored as a double), R_b / G1_b / G2_b at b * kst * kst, sigma_b at b * kst,
+// scratch at b * bst when the jobs exceed shared memory.
+__global__ void __launch_bounds__(SVD_THREADS, 1) svd_batch_kernel(int kst, const double* __restrict__ kd,
+                                                                const double* __restrict__ R, double* G1,
+                                                                double* G2, double* sigma, double* big,
+                                                                size_t bst) {
+  const int b = blockIdx.x;
+  const int k = int(kd[b]);
+  const size_t o2 = size_t(b) * kst * kst;
+  svd_trunc_body(k, R + o2, nullptr, k, G1 + o2, G2 + o2, sigma + size_t(b) * kst, nullptr,
+                 big ? big + size_t(b) * bst : nullptr);
 }
 
 }  // namespace
@@ -257,6 +300,29 @@ int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, do
   TTR_PREFER_SHARED(svd_trunc_kernel);
   svd_trunc_kernel<<<1, SVD_THREADS, smem, s>>>(k, R, eps_ptr, rcap, G1, G2, sigma, rank_out,
                                                 k > SVD_SMEM_K ? big : nullptr);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+int svd_batch_launch(int B, int kmax, const double* kd, const double* R, double* G1, double* G2, double* sigma,
+                     cudaStream_t s, double* big) {
+  if (B < 1) return TT_OK;
+  if (kmax < 1 || (kmax > SVD_SMEM_K && big == nullptr)) {
+    set_error("svd_batch: k out of range or missing scratch");
+    return TT_EUNSUPPORTED;
+  }
+  const int kk = kmax + (kmax & 1);
+  const size_t smem = (kmax > SVD_SMEM_K) ? 0 : (size_t(kmax) * kk + size_t(kk) * kk + kk + 32) * sizeof(double);
+  static bool attr_done = false;
+  if (!attr_done) {
+    TTR_CHECK_CUDA(cudaFuncSetAttribute(svd_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_done = true;
+  }
+  TTR_PREFER_SHARED(svd_batch_kernel);
+  svd_batch_kernel<<<unsigned(B), SVD_THREADS, smem, s>>>(kmax, kd, R, G1, G2, sigma,
+                                                          kmax > SVD_SMEM_K ? big : nullptr,
+                                                          svd_scratch_doubles(kmax));
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
   return TT_OK;
