@@ -47,6 +47,26 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(x, world, dist, device):
+    """The largest of every rank's value (timings: the job ends with its slowest replica)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank):
+    """Rank r rounds its own sum, drawn from seed 1 + r (replicas, no shared data)."""
+    return 1 + int(rank)
+
+
+def replica_tflops(flops_per_replica, ms, world):
+    """Whole-job throughput of `world` independent replicas finishing within `ms`."""
+    return world * flops_per_replica / (ms * 1e-3) / 1e12
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -65,7 +85,8 @@ class Clocks:
     def __init__(self, index):
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"tt_bench_clocks_{os.getpid()}_{index}.csv")
 
     def __enter__(self):
         try:
@@ -206,7 +227,7 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    Ys = load_workload(1 + rank)
+    Ys = load_workload(replica_seed(rank))
     dims = [c.shape[1] for c in Ys[0]]
     N = len(dims)
     ell = [1] + [WORKLOAD["ell"]] * (N - 1) + [1]
@@ -241,10 +262,8 @@ def run_ours(a):
     t_ms, _, launches, out_ranks = res_prec[prim]
     tp_ms, kinds, _, _ = prof_prec[prim]
     launches = plans[prim].launches * a.steps          # kernels launched by the timed replays
+    t_ms = max_over_ranks(t_ms, world, dist, dev)
     if world > 1:
-        tm = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        t_ms = float(tm.item())
         dist.barrier()
 
     # end to end through the public API with host buffers (pinned): one packed
@@ -268,7 +287,7 @@ def run_ours(a):
         torch.cuda.synchronize()
         if s > 0:
             e2e_times.append(e0.elapsed_time(e1))
-    e2e_ms = statistics.median(e2e_times) if e2e_times else float("nan")
+    e2e_ms = max_over_ranks(statistics.median(e2e_times) if e2e_times else float("nan"), world, dist, dev)
 
     # the same rounding without a captured plan (planning and launches per call)
     ws = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
@@ -349,7 +368,7 @@ def run_ours(a):
     variants["det_fp64"] = det
     res = {
         "metric": METRIC,
-        "value": world * flops / (t_ms * 1e-3) / 1e12,
+        "value": replica_tflops(flops, t_ms, world),
         "unit": "TFLOP/s",
         "n_gpus": world,
         "steps": a.steps,
@@ -364,7 +383,7 @@ def run_ours(a):
                        parallelism=f"replicas x{world}", algorithmic_gflop_per_step=flops / 1e9,
                        algorithmic_mb_per_step=nbytes / 1e6, output_ranks_max=max(out_ranks),
                        execution="captured CUDA graph per precision, replayed per step"),
-        "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+        "e2e": {"value": replica_tflops(flops, e2e_ms, world), "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": lines[dom],
