@@ -534,8 +534,9 @@ def run_large(a):
                                         "launches_per_step": plan.launches}
             plan.close()
         if "twosided" in legs:
-            ms, X = timed(lambda s: tt.tt_round_twosided(Yd, ell, rhos=rho, seed=s), 2, 1)
-            variants["twosided_fp64"] = {"ms_per_step": ms, "eager": True}
+            for prec in ("mixed", "fp64"):
+                ms, X = timed(lambda s: tt.tt_round_twosided(Yd, ell, rhos=rho, seed=s, precision=prec), 2, 1)
+                variants["twosided_" + prec] = {"ms_per_step": ms, "eager": True}
         if "det" in legs and not a.no_det:
             ms, Xd = timed(lambda s: tt.tt_round_det(Yd, tol=tol), 1, 0)
             dr = [int(Xd[0].shape[0])] + [int(c.shape[2]) for c in Xd]

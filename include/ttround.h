@@ -298,17 +298,22 @@ int tt_orthrand_omega_ranks(int32_t N, int32_t K, const int64_t* dims, const int
  *   sketch_right host array of N device pointers (rho_{n-1} x I_n x rho_n) or NULL
  *                (NULL: drawn on the device as tt_sketch_gaussian does, the left
  *                one from seed and the right one from seed + 1)
+ *   precision    TT_PREC_FP64, or TT_PREC_MIXED: every contraction (both
+ *                sketch sweeps included, since W^L and W^R span the projectors'
+ *                ranges themselves) as the emulated float64 product of
+ *                tt_gemm_emulated_f64 with tt_mixed_digits(0, N) digits; the
+ *                QR, the SVD and the factor scaling stay float64
  *   out          host array of N device pointers, core n holds l_{n-1} I_n l_n
- * The result is not orthogonal (Section 3.3). Errors: TT_EINVAL, TT_ENOMEM,
- * TT_ECUDA.
+ * The result is not orthogonal (Section 3.3). Errors: TT_EINVAL (also for an
+ * unknown precision), TT_ENOMEM, TT_ECUDA.
  */
 int tt_round_twosided(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
                       const double* coeffs, const int64_t* ells, const int64_t* rhos,
                       const double* const* sketch_left, const double* const* sketch_right, uint64_t seed,
-                      double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
-                      void* stream);
+                      int32_t precision, double* const* out, int64_t* out_ranks, void* workspace,
+                      size_t workspace_bytes, void* stream);
 size_t tt_round_twosided_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
-                                   const int64_t* ells, const int64_t* rhos);
+                                   const int64_t* ells, const int64_t* rhos, int32_t precision);
 
 /*
  * tt_round_sum_rand_noalloc -- tt_round_sum_rand for callers that cannot

@@ -34,9 +34,9 @@ SIGNATURES = {
                                   c_size, c_vp]),
     "tt_round_orthrand_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64]),
     "tt_orthrand_omega_ranks": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_i64]),
-    "tt_round_twosided": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_i64, P_vp, P_vp, c_u64, P_vp,
-                                  P_i64, c_vp, c_size, c_vp]),
-    "tt_round_twosided_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64, P_i64]),
+    "tt_round_twosided": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_i64, P_vp, P_vp, c_u64, c_i32,
+                                  P_vp, P_i64, c_vp, c_size, c_vp]),
+    "tt_round_twosided_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64, P_i64, c_i32]),
     "tt_noalloc_scratch_bytes": (c_size, []),
     "tt_round_sum_rand_noalloc": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl,
                                           c_i32, P_vp, P_i64, c_vp]),

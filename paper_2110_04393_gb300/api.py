@@ -493,8 +493,10 @@ def tt_round_orthrand(summands, ells, *, omega=None, seed=0, coeffs=None, worksp
 
 
 def tt_round_twosided(summands, ells, *, rhos=None, sketch_left=None, sketch_right=None, seed=0, coeffs=None,
-                      workspace=None, stream=None):
-    """Algorithm 6 (Two-Sided-Randomization) of a sum without forming it."""
+                      precision="fp64", workspace=None, stream=None):
+    """Algorithm 6 (Two-Sided-Randomization) of a sum without forming it
+    (precision "fp64", or "mixed": contractions as emulated FP64 products on
+    the tensor cores)."""
     import math
     N, K, dims, ranks, flat = _sum_args(summands)
     device = summands[0][0].device
@@ -509,7 +511,7 @@ def tt_round_twosided(summands, ells, *, rhos=None, sketch_left=None, sketch_rig
                 if tuple(c.shape) != (rk[n], dims[n], rk[n + 1]):
                     raise ValueError(f"{name} core {n} has shape {tuple(c.shape)}")
     out = [torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float64, device=device) for n in range(N)]
-    nb = L.tt_round_twosided_workspace(N, K, dims_a, ranks_a, ell_a, rho_a)
+    nb = L.tt_round_twosided_workspace(N, K, dims_a, ranks_a, ell_a, rho_a, _PREC[precision])
     if nb == 0:
         raise TTError(1, nat.last_error())
     workspace, wp, wb = _workspace(nb, device, workspace)
@@ -518,7 +520,8 @@ def tt_round_twosided(summands, ells, *, rhos=None, sketch_left=None, sketch_rig
     _check(L.tt_round_twosided(N, K, dims_a, ranks_a, _ptrs(flat), co, ell_a, rho_a,
                                _ptrs(sketch_left) if sketch_left is not None else None,
                                _ptrs(sketch_right) if sketch_right is not None else None,
-                               ctypes.c_uint64(int(seed)), _ptrs(out), out_ranks, wp, wb, _stream(stream, device)))
+                               ctypes.c_uint64(int(seed)), _PREC[precision], _ptrs(out), out_ranks, wp, wb,
+                               _stream(stream, device)))
     return out
 
 

@@ -25,6 +25,8 @@
 
 namespace ttr {
 
+int mixed_digits(double tol, int N);
+
 namespace {
 
 // M[:, c] *= (s_c > thr) ? s_c^p : 0 for c < cols, thr = tol_rel * s_0 (sigma sorted descending).
@@ -50,8 +52,16 @@ int colscale_launch(double* M, int64_t rows, int64_t cols, int64_t ld, const dou
 }
 
 int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const double* const* skL,
-                   const double* const* skR, uint64_t seed, double* const* out, Arena& ar, Schedule& sc) {
+                   const double* const* skR, uint64_t seed, int digits, double* const* out, Arena& ar,
+                   Schedule& sc) {
   const int N = P.N, K = P.K;
+  // every contraction in FP64, or (digits > 0) as the emulated FP64 product on
+  // the tensor cores: both sketches span the projectors' ranges directly, so
+  // all products, the sketch sweeps included, take the same digits
+  auto gemm = [&](std::vector<GemmDesc> g) {
+    if (digits > 0) sc.gemm_tc(std::move(g), digits);
+    else sc.gemm(std::move(g));
+  };
   const auto& S = P.S;
   const auto& ell = P.ell;
   auto In = [&](int n) { return P.I[n - 1]; };
@@ -124,8 +134,8 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
         gb.push_back(gdesc(L[n], 1, ell[n], Tj, r1, 1, Wo, S[n], 1, ell[n], r1, ell[n - 1] * In(n)));
       }
     }
-    sc.gemm(ga);
-    sc.gemm(gb);
+    gemm(ga);
+    gemm(gb);
   }
   // ---- right-to-left partial contractions with R (Algorithm 3 for every summand)
   for (int n = N; n >= 2; --n) {
@@ -136,9 +146,9 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
       const double* Wj = WR[n] ? WR[n] + P.o(j, n) * rho[n] : nullptr;
       ga.push_back(gdesc(P.core(j, n), r1, 1, Wj, rho[n], 1, Zj, rho[n], 1, r0 * In(n), rho[n], r1));
     }
-    sc.gemm(ga);
+    gemm(ga);
     // shared sketch: one GEMM of the stacked H(Z^(j)) with H(R_n)^T
-    sc.gemm({gdesc(Z, In(n) * rho[n], 1, Rs[n], 1, In(n) * rho[n], WR[n - 1], rho[n - 1], 1, S[n - 1], rho[n - 1],
+    gemm({gdesc(Z, In(n) * rho[n], 1, Rs[n], 1, In(n) * rho[n], WR[n - 1], rho[n - 1], 1, S[n - 1], rho[n - 1],
                    In(n) * rho[n])});
   }
   // ---- per bond: SVD of W^L_n W^R_n and the factors L_n, R_n. First every
@@ -150,7 +160,7 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
   auto bK2 = [&](double* base, int n) { return base ? base + kmax * kmax * (n - 1) : nullptr; };
   for (int n = 1; n < N; ++n) {
     const int64_t l = ell[n], r = rho[n];
-    sc.gemm({gdesc(WL[n], S[n], 1, WR[n], r, 1, bAm(n), r, 1, l, r, S[n])});
+    gemm({gdesc(WL[n], S[n], 1, WR[n], r, 1, bAm(n), r, 1, l, r, S[n])});
     // thin QR of A^T (r x l, a strided view of A)
     qr_plan(sc, qr_view(pool, r, int(l)), bAm(n), 1, r, bQt(n), l, 1, bK2(Rb, n));
   }
@@ -168,13 +178,13 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
     const double* sg = sig ? sig + kmax * (n - 1) : nullptr;
     const double tol_rel = double(std::max(l, r)) * eps52;
     // P1 = Q U_R S^{+1/2} into Am (r x l)
-    sc.gemm({gdesc(bQt(n), l, 1, bK2(G1, n), l, 1, am, l, 1, r, l, l)});
+    gemm({gdesc(bQt(n), l, 1, bK2(G1, n), l, 1, am, l, 1, r, l, l)});
     sc.add([=](cudaStream_t s) -> int {
       TTR_TRY(colscale_launch(am, r, l, l, sg, -0.5, tol_rel, s));
       return colscale_launch(g2, l, l, l, sg, -1.5, tol_rel, s);    // V_R S^{+1/2} = G2 S^{-3/2}
     });
-    sc.gemm({gdesc(WR[n], r, 1, am, l, 1, Lf[n], l, 1, S[n], l, r)});         // L_n = W^R_n P1
-    sc.gemm({gdesc(g2, 1, l, WL[n], S[n], 1, Rf[n], S[n], 1, l, S[n], l)});  // R_n = P2^T W^L_n
+    gemm({gdesc(WR[n], r, 1, am, l, 1, Lf[n], l, 1, S[n], l, r)});         // L_n = W^R_n P1
+    gemm({gdesc(g2, 1, l, WL[n], S[n], 1, Rf[n], S[n], 1, l, S[n], l)});  // R_n = P2^T W^L_n
   }
   // ---- distribution of the factors into the cores
   for (int n = 1; n <= N; ++n) {
@@ -185,8 +195,8 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
       const double* Lj = Lf[n] ? Lf[n] + P.o(j, n) * ell[n] : nullptr;
       ga.push_back(gdesc(P.core(j, n), r1, 1, Lj, ell[n], 1, Zj, ell[n], 1, r0 * In(n), ell[n], r1));
     }
-    sc.gemm(ga);
-    sc.gemm({gdesc(Rf[n - 1], S[n - 1], 1, Z, In(n) * ell[n], 1, out[n - 1], In(n) * ell[n], 1, ell[n - 1],
+    gemm(ga);
+    gemm({gdesc(Rf[n - 1], S[n - 1], 1, Z, In(n) * ell[n], 1, out[n - 1], In(n) * ell[n], 1, ell[n - 1],
                    In(n) * ell[n], S[n - 1])});
   }
   return TT_OK;
@@ -202,8 +212,12 @@ extern "C" {
 static int twosided_common(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
                            const double* const* cores, const double* coeffs, const int64_t* ells,
                            const int64_t* rhos, const double* const* skL, const double* const* skR, uint64_t seed,
-                           double* const* out, int64_t* out_ranks, void* workspace, size_t ws_bytes, void* stream,
-                           size_t* size_only) {
+                           int32_t precision, double* const* out, int64_t* out_ranks, void* workspace,
+                           size_t ws_bytes, void* stream, size_t* size_only) {
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
+    set_error("tt_round_twosided: unknown precision mode");
+    return TT_EINVAL;
+  }
   SumProblem P;
   TTR_TRY(validate_sum(N, K, dims, ranks, cores, coeffs, ells, size_only == nullptr, &P));
   if (N < 2) { set_error("two-sided rounding needs N >= 2"); return TT_EINVAL; }
@@ -218,7 +232,10 @@ static int twosided_common(int32_t N, int32_t K, const int64_t* dims, const int6
   if (!size_only && (!out || !out_ranks)) { set_error("null outputs"); return TT_EINVAL; }
   std::vector<double*> outv(N, nullptr);
   if (out) outv.assign(out, out + N);
-  BuildFn build = [&](Arena& ar, Schedule& sc) { return build_twosided(P, rho, skL, skR, seed, outv.data(), ar, sc); };
+  const int digits = (precision == TT_PREC_MIXED) ? mixed_digits(0.0, N) : 0;
+  BuildFn build = [&](Arena& ar, Schedule& sc) {
+    return build_twosided(P, rho, skL, skR, seed, digits, outv.data(), ar, sc);
+  };
   if (size_only) return plan_workspace_bytes(build, size_only);
   TTR_TRY(plan_execute(build, workspace, ws_bytes, static_cast<cudaStream_t>(stream)));
   for (int n = 0; n <= N; ++n) out_ranks[n] = P.ell[n];
@@ -228,16 +245,16 @@ static int twosided_common(int32_t N, int32_t K, const int64_t* dims, const int6
 int tt_round_twosided(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,
                       const double* coeffs, const int64_t* ells, const int64_t* rhos,
                       const double* const* sketch_left, const double* const* sketch_right, uint64_t seed,
-                      double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
-                      void* stream) {
-  return twosided_common(N, K, dims, ranks, cores, coeffs, ells, rhos, sketch_left, sketch_right, seed, out,
-                         out_ranks, workspace, workspace_bytes, stream, nullptr);
+                      int32_t precision, double* const* out, int64_t* out_ranks, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  return twosided_common(N, K, dims, ranks, cores, coeffs, ells, rhos, sketch_left, sketch_right, seed, precision,
+                         out, out_ranks, workspace, workspace_bytes, stream, nullptr);
 }
 
 size_t tt_round_twosided_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
-                                   const int64_t* ells, const int64_t* rhos) {
+                                   const int64_t* ells, const int64_t* rhos, int32_t precision) {
   size_t b = 0;
-  if (twosided_common(N, K, dims, ranks, nullptr, nullptr, ells, rhos, nullptr, nullptr, 0, nullptr, nullptr,
+  if (twosided_common(N, K, dims, ranks, nullptr, nullptr, ells, rhos, nullptr, nullptr, 0, precision, nullptr, nullptr,
                       nullptr, 0, nullptr, &b) != TT_OK)
     return 0;
   return b;

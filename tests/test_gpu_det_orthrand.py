@@ -84,9 +84,12 @@ def test_rand_vs_det_same_accuracy_order_on_low_rank_sum():
     assert O.diff_norm(Xr, ref) <= 1e-12 * O.norm(ref)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", ["single", "sum"])
-def test_twosided_parity(case):
-    """Algorithm 6 in block-sum form == Algorithm 6 on the formed sum (oracle)."""
+def test_twosided_parity(case, precision):
+    """Algorithm 6 in block-sum form == Algorithm 6 on the formed sum (oracle);
+    the mixed form's products are accurate to ~1e-8 relative (tt_mixed_digits in
+    fixed-rank mode), amplified by at most the conditioning of the bond SVDs."""
     if case == "single":
         dims = [11, 13, 12, 10]
         Ys = [synth.gaussian_tt(synth.rng_for(100), dims, [1, 7, 9, 6, 1])]
@@ -101,9 +104,18 @@ def test_twosided_parity(case):
     Rsk = synth.gaussian_tt(synth.rng_for(103), dims, rho)
     coeffs = list(synth.rng_for(104).standard_normal(len(Ys)))
     Xg = to_host(tt.tt_round_twosided([to_dev(Y) for Y in Ys], ell, rhos=rho, sketch_left=to_dev(Lsk),
-                                      sketch_right=to_dev(Rsk), coeffs=coeffs))
+                                      sketch_right=to_dev(Rsk), coeffs=coeffs, precision=precision))
     Xo = O.round_sum_twosided(Ys, Lsk, Rsk, coeffs)
-    assert rel_diff(Xg, Xo) <= FP64_TOL
+    assert rel_diff(Xg, Xo) <= (FP64_TOL if precision == "fp64" else 1e-5), rel_diff(Xg, Xo)
+
+
+def test_twosided_mixed_exact_recovery_and_bad_precision():
+    dims = [8] * 6
+    Y = synth.gaussian_tt(synth.rng_for(106), dims, const_ranks(6, 3))
+    Xg = to_host(tt.tt_round_twosided([to_dev(Y)], const_ranks(6, 4), seed=9, precision="mixed"))
+    assert O.diff_norm(Xg, Y) <= 1e-6 * O.norm(Y), O.diff_norm(Xg, Y) / O.norm(Y)
+    with pytest.raises(Exception):
+        tt.tt_round_twosided([to_dev(Y)], const_ranks(6, 4), seed=9, precision=7)
 
 
 def test_twosided_exact_recovery_seeded():

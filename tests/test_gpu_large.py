@@ -3,7 +3,7 @@ The structured redundant sum of Section 4.2's kind (three base TTs copied with
 scrambled gauges and random coefficients, plus two summands of relative size
 1e-8) is rounded at tolerance 1e-6 by Randomize-then-Orthogonalize (Algorithm
 7 with the Section 3.2 truncation, sketch rank 70) in both precisions, and by
-Two-Sided randomization (Algorithm 6, ranks 70 / 105). The oracle is far too
+Two-Sided randomization (Algorithm 6, ranks 70 / 105) in both precisions. The oracle is far too
 slow at this size, so the checks are properties that hold at any size, taken
 on the GPU with blockwise TT inner products: the rounding error
 ||X - Y|| / ||Y|| stays within the tolerance, both precisions find the same
@@ -75,11 +75,12 @@ def test_large_sum_randorth_both_precisions(large_sum):
     assert emx <= 1.1 * e64 + 1e-7, (e64, emx)
 
 
-def test_large_sum_twosided(large_sum):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_sum_twosided(large_sum, precision):
     Yd, y2 = large_sum
     ell = [1] + [ELL] * (N - 1) + [1]
     rho = [1] + [RHO] * (N - 1) + [1]
-    X = tt.tt_round_twosided(Yd, ell, rhos=rho, seed=4)
+    X = tt.tt_round_twosided(Yd, ell, rhos=rho, seed=4, precision=precision)
     assert [int(c.shape[0]) for c in X] == ell[:-1]
     e = _rel_err(X, Yd, y2)
     assert e <= TOL, e
