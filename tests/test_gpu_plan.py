@@ -80,3 +80,25 @@ def test_plan_host_buffers_match_device_run(precision, tol):
     with pytest.raises(ValueError):
         plan.run_host(h_in[:10])
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_plan_is_the_eager_rounding(precision):
+    """The configuration the benchmark times: the captured plan of the 20-TT sum
+    (N = 50, I = 100, rank 10, sketch rank 30, tol 1e-8) replays bit-wise the
+    eager call that the full-size oracle parity tests check, on device and on
+    host buffers."""
+    Ys = synth.workload_sum_literal(1)
+    N = len(Ys[0])
+    dims = [int(c.shape[1]) for c in Ys[0]]
+    ranks = [[1] + [int(c.shape[2]) for c in Y] for Y in Ys]
+    ell = const_ranks(N, 30)
+    Yd = [to_dev(Y) for Y in Ys]
+    plan = tt.SumRoundingPlan(dims, ranks, ell, tol=1e-8, precision=precision)
+    Xp = plan(Yd, seed=21)
+    Xe = tt.tt_round_sum_rand(Yd, ell, seed=21, tol=1e-8, precision=precision)
+    torch.cuda.synchronize()
+    assert _same(Xp, Xe)
+    Xh = plan.run_host(plan.pack_host(Ys), seed=21)
+    assert _same(Xh, [x.cpu() for x in Xe])
+    plan.close()
