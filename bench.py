@@ -85,8 +85,7 @@ class Clocks:
     def __init__(self, index):
         self.proc = None
         self.index = index
-        import tempfile
-        self.path = os.path.join(tempfile.gettempdir(), f"tt_bench_clocks_{os.getpid()}_{index}.csv")
+        self.path = os.path.join(ROOT, ".bench", f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
