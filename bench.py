@@ -24,6 +24,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TT-round time & TFLOP/s (sum of 20 TTs, N=50): rand vs det, mixed vs FP64"
+DTYPE_MIXED = ("f64-emulated: bf16 digit products on tcgen05 with exact integer sums (2 digits = 14 bits in the "
+               "Algorithm 3 contractions, 8 digits = 56 bits in core updates / sketches / projections), f64 QR / "
+               "SVD / truncation")
 WORKLOAD = dict(workload="sum of K=20 TT-tensors, N=50, I_n=100, rank 10 each (formal rank 200), "
                          "sketch rank 30, tol 1e-8, Gaussian cores (Definition 3.1 scaling)",
                 K=20, N=50, I=100, R=10, ell=30, tol=1e-8)
@@ -37,6 +40,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--no-det", action="store_true", help="skip the deterministic comparison")
     p.add_argument("--legs", default="mixed,fp64,twosided,det",
@@ -130,26 +134,82 @@ def ranks_of(Ys):
     return [[1] + [int(c.shape[2]) for c in Y] for Y in Ys]
 
 
-def cpu_baseline(Ys, reps=2):
-    """The oracle as it stands (NumPy FP64) on the host cores, whole workload."""
+ORACLE_SEED = 7          # sketch seed of the oracle leg (the GPU legs re-run once with it)
+
+
+def _oracle_rounding(Ys, seed=ORACLE_SEED):
+    import oracle
+    dims = [c.shape[1] for c in Ys[0]]
+    ell = [1] + [WORKLOAD["ell"]] * (len(dims) - 1) + [1]
+    sk = oracle.gaussian_sketch_philox(seed, dims, ell)
+    X = oracle.round_sum_randorth(Ys, sk)
+    return oracle.truncate_left_orthogonal(X, WORKLOAD["tol"])
+
+
+def oracle_one_thread_seconds():
+    """One oracle rounding of the workload in a child process limited to one
+    BLAS / OpenMP thread (the thread count is fixed when NumPy loads)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample"], capture_output=True, text=True,
+                       env=env, timeout=900)
+    if p.returncode != 0:
+        return None
+    return json.loads(p.stdout.strip().splitlines()[-1])["seconds"]
+
+
+def oracle_leg(Ys, gpu_results, det_result, reps=2):
+    """The oracle as it stands (NumPy FP64) on the host cores: the cpu_baseline
+    (whole workload, all cores, best of `reps`, plus one rounding on one thread)
+    and, against its result on the same sketch (Philox, seed ORACLE_SEED), the
+    relative Frobenius error of every GPU leg. gpu_results: name -> host cores of
+    the GPU rounding with that sketch seed; det_result: host cores of the
+    deterministic rounding. Rounding errors ||X - sum_j Y_j|| / ||sum_j Y_j||
+    come from inner products (exact algebra; about 1e-8 relative resolution)."""
     import numpy as np
     import oracle
     from paper_2110_04393_gb300.costs import flops_sum_randorth
     dims = [c.shape[1] for c in Ys[0]]
     ell = [1] + [WORKLOAD["ell"]] * (len(dims) - 1) + [1]
-    sk = oracle.gaussian_sketch_philox(7, dims, ell)
     ts = []
+    Xo = None
     for _ in range(reps):
         t0 = time.perf_counter()
-        X = oracle.round_sum_randorth(Ys, sk)
-        oracle.truncate_left_orthogonal(X, WORKLOAD["tol"])
+        Xo = _oracle_rounding(Ys)
         ts.append(time.perf_counter() - t0)
     t = min(ts)
     fl = flops_sum_randorth(dims, ranks_of(Ys), ell)
     threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
-    return {"value": fl / t / 1e12, "unit": "TFLOP/s", "cores": int(threads), "kind": "oracle",
+    t1 = oracle_one_thread_seconds()
+    base = {"value": fl / t / 1e12, "unit": "TFLOP/s", "cores": int(threads), "kind": "oracle",
             "sample": f"whole workload (sum-rounding + truncation, host-drawn sketch), best of {reps}",
-            "seconds_per_rounding": t}
+            "seconds_per_rounding": t,
+            "one_thread": ({"value": fl / t1 / 1e12, "unit": "TFLOP/s", "cores": 1, "seconds_per_rounding": t1,
+                            "sample": "one rounding of the whole workload, BLAS limited to one thread"}
+                           if t1 else None)}
+    K = len(Ys)
+    G = np.array([[oracle.inner(Ys[a], Ys[b]) for b in range(K)] for a in range(K)])
+    yy = float(G.sum())
+
+    def rounding_error(X):
+        xy = sum(oracle.inner(X, Y) for Y in Ys)
+        return float(np.sqrt(max(yy - 2.0 * xy + oracle.inner(X, X), 0.0) / yy))
+
+    e_o = rounding_error(Xo)
+    nrm_o = oracle.norm(Xo)
+    err = {"sketch_seed": ORACLE_SEED, "oracle_rounding_error": e_o,
+           "method": "distance to the oracle's result by orthogonalizing the difference TT; rounding errors "
+                     "from inner products"}
+    for name, X in gpu_results.items():
+        e = rounding_error(X)
+        err[name] = {"rel_diff_vs_oracle_result": oracle.diff_norm(X, Xo) / nrm_o, "rounding_error": e,
+                     "ratio_to_oracle_error": e / e_o if e_o > 0 else None,
+                     "ranks_equal_oracle": oracle.ranks_of(X) == oracle.ranks_of(Xo)}
+    if det_result is not None:
+        err["det_fp64"] = {"rounding_error": rounding_error(det_result),
+                           "note": "deterministic TT-SVD rounding to the same tolerance (the sum is generically "
+                                   "of full rank 200, so its error is at the tolerance while the rank-30 "
+                                   "randomized rounding's is O(1))"}
+    return base, err
 
 
 def run_reference(a):
@@ -277,6 +337,7 @@ def run_ours(a):
         h_out = torch.empty(out_total, dtype=torch.float64, pin_memory=True)
         h2d, d2h = in_total * 8, out_total * 8
     for s in range(0 if a.no_e2e else max(2, a.steps // 2) + 1):
+        flush.fill_(s & 0xFF)                 # L2 flushed like the device-resident steps
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -304,7 +365,16 @@ def run_ours(a):
     eager_ms = min(eager)
 
     # deterministic comparison (Algorithms 1 + 2 on the formed sum), same inputs and tolerance
+    # one more (untimed) rounding per precision with the oracle leg's sketch
+    # seed, copied to the host for the error comparison of the oracle leg
+    err_inputs = {}
+    if world == 1 and not a.no_cpu_baseline:
+        for prec in precs:
+            Xp = plans[prec](Yd, seed=ORACLE_SEED)
+            torch.cuda.synchronize()
+            err_inputs["rand_" + prec] = [c.cpu().numpy() for c in Xp]
     det = None
+    det_host = None
     if not a.no_det:
         from paper_2110_04393_gb300.costs import flops_det
         Xd = tt.tt_round_det(Yd, tol=tol)          # warm-up
@@ -320,6 +390,7 @@ def run_ours(a):
             torch.cuda.synchronize()
             dts.append(e0.elapsed_time(e1))
         dr = [int(Xd[0].shape[0])] + [int(c.shape[2]) for c in Xd]
+        det_host = [c.cpu().numpy() for c in Xd]
         S = [1] + [sum(R[n] for R in ranks_of(Ys)) for n in range(1, N)] + [1]
         S[1] = min(S[1], dims[0])
         for n in range(N - 1, 0, -1):
@@ -376,14 +447,15 @@ def run_ours(a):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": DTYPE_MIXED if prim == "mixed" else "f64",
         "data": "synthetic",
         "config": dict(WORKLOAD, precision=prim, l2="flushed before every timed step (256 MB write)",
                        parallelism=f"replicas x{world}", algorithmic_gflop_per_step=flops / 1e9,
                        algorithmic_mb_per_step=nbytes / 1e6, output_ranks_max=max(out_ranks),
                        execution="captured CUDA graph per precision, replayed per step"),
         "e2e": {"value": replica_tflops(flops, e2e_ms, world), "unit": "TFLOP/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "l2": "flushed before every step (256 MB write, outside the timed region)"},
         "gpu_launches": launches,
         "roofline": lines[dom],
         "roofline_other": lines[1 - dom],
@@ -391,7 +463,7 @@ def run_ours(a):
         "variants": variants,
     }
     if world == 1 and not a.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(Ys)
+        res["cpu_baseline"], res["error_vs_oracle"] = oracle_leg(Ys, err_inputs, det_host)
     print(json.dumps(res), flush=True)
     for pl in plans.values():
         pl.close()
@@ -562,6 +634,12 @@ def run_large(a):
 
 def main():
     a = parse()
+    if a.oracle_sample:
+        Ys = load_workload(replica_seed(0))
+        t0 = time.perf_counter()
+        _oracle_rounding(Ys)
+        print(json.dumps({"seconds": time.perf_counter() - t0}))
+        return
     if a.impl == "reference":
         run_reference(a)
     elif a.config == "batched":

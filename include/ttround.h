@@ -18,9 +18,13 @@
  *   library never frees or keeps them. Pointers named "host" are host memory
  *   read during the call only.
  * - stream is a cudaStream_t passed as void*. All device work is enqueued on it;
- *   inputs are never modified. Calls return after enqueueing unless a tolerance
- *   is given (the data-dependent output ranks are then read back, which
- *   synchronizes the stream once at the end).
+ *   inputs are never modified. The eager entry points (tt_round_*,
+ *   tt_gemm_emulated_f64) synchronize the stream once at the end: they read
+ *   back the run's device status word (and, with a tolerance, the
+ *   data-dependent output ranks) and return TT_ETIMEOUT / TT_ESINGULAR when a
+ *   kernel reported a failure. Plan replays return after enqueueing unless a
+ *   tolerance is given; tt_sum_plan_status / tt_batch_plan_status wait for a
+ *   replay and return its device status.
  * - workspace: device scratch of at least the size the matching *_workspace
  *   query returns, 256-byte aligned. NULL lets the library allocate (and free)
  *   it stream-ordered with cudaMallocAsync.
@@ -43,8 +47,9 @@ typedef enum {
   TT_ENOMEM = 2,        /* allocation failed or workspace too small */
   TT_ECUDA = 3,         /* a CUDA call failed (message has the CUDA error) */
   TT_ENONFINITE = 4,    /* non-finite values met where the method needs finite ones */
-  TT_ESINGULAR = 5,     /* a triangular factor needed by the adjoint is singular */
-  TT_ETIMEOUT = 6,      /* a bounded device wait gave up */
+  TT_ESINGULAR = 5,     /* a factorization broke down: a thin QR above the Householder
+                           fallback limit could not orthogonalize a block */
+  TT_ETIMEOUT = 6,      /* a bounded device wait gave up (the outputs are not valid) */
   TT_EUNSUPPORTED = 7   /* size or option outside what this build handles */
 } tt_status;
 
@@ -101,7 +106,8 @@ int tt_sketch_gaussian(int32_t N, const int64_t* dims, const int64_t* ells, uint
  *                 compactly as (r_{n-1}, I_n, r_n)
  *   out_ranks     host, N+1, receives r_0..r_N
  * Errors: TT_EINVAL (bad sizes/ranks/pointers), TT_EUNSUPPORTED (a target rank
- * above 1024), TT_ENOMEM, TT_ECUDA.
+ * above 1024), TT_ENOMEM, TT_ECUDA, TT_ETIMEOUT (a tensor-core wait gave up),
+ * TT_ESINGULAR (a thin QR of rank above 96 could not orthogonalize a block).
  */
 int tt_round_sum_rand(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
                       const double* const* cores, const double* coeffs, const int64_t* ells,
@@ -175,6 +181,9 @@ int tt_sum_plan_run(tt_sum_plan* plan, const double* const* cores, const double*
                     double* const* out, int64_t* out_ranks, void* stream);
 int tt_sum_plan_destroy(tt_sum_plan* plan);
 int64_t tt_sum_plan_launches(const tt_sum_plan* plan);
+/* Waits for stream and returns the device status of the plan's last replay
+ * (TT_OK, TT_ETIMEOUT or TT_ESINGULAR, as the eager entry point would). */
+int tt_sum_plan_status(tt_sum_plan* plan, void* stream);
 
 /*
  * Host-buffer replays of a plan (same computation as tt_sum_plan_run). Packed
@@ -228,6 +237,8 @@ int tt_batch_plan_run(tt_batch_plan* plan, const double* const* cores, const uin
                       int64_t* out_ranks, void* stream);
 int tt_batch_plan_destroy(tt_batch_plan* plan);
 int64_t tt_batch_plan_launches(const tt_batch_plan* plan);
+/* Waits for stream and returns the combined device status of the last replay. */
+int tt_batch_plan_status(tt_batch_plan* plan, void* stream);
 
 /*
  * tt_round_rand -- Algorithm 5 (Randomize-then-Orthogonalize, Section 3.2):
@@ -316,12 +327,58 @@ size_t tt_round_twosided_workspace(int32_t N, int32_t K, const int64_t* dims, co
                                    const int64_t* ells, const int64_t* rhos, int32_t precision);
 
 /*
+ * tt_round_twosided_orth -- Algorithm 6 with the orthogonalizing restructure
+ * that Section 3.3 mentions without giving it, and the tolerance mode it
+ * enables. The sketches, bond SVDs and factors L_n, R_n are those of
+ * tt_round_twosided; the cores are then formed in a left-to-right sweep that
+ * carries the R factor of each thin QR into the next core (T_0 = 1):
+ *   C_n = (T_{n-1} R_{n-1}) x_1 Y_n x_3 L_n,  V(C_n) = Q_n T_n,  X_n = Q_n (n < N),
+ *   H(X_N) = T_{N-1} R_{N-1} H(Y_N),
+ * which represents the same tensor as Algorithm 6 but left-orthogonal. With
+ * tol > 0 the result is then truncated as in tt_round_sum_rand (Section 3.2,
+ * eps = tol ||X|| / sqrt(N-1)), so ||X_out - X|| <= tol ||X||, X the
+ * Algorithm 6 result. Arguments as tt_round_twosided plus tol; with
+ * TT_PREC_MIXED the contractions take tt_mixed_digits(tol, N) digits. out
+ * cores are written compactly at out_ranks. Errors: as tt_round_twosided.
+ */
+int tt_round_twosided_orth(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                           const double* const* cores, const double* coeffs, const int64_t* ells,
+                           const int64_t* rhos, const double* const* sketch_left,
+                           const double* const* sketch_right, uint64_t seed, double tol, int32_t precision,
+                           double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
+                           void* stream);
+size_t tt_round_twosided_orth_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                                        const int64_t* ells, const int64_t* rhos, double tol, int32_t precision);
+
+/*
+ * tt_truncate_lorth -- the truncation of Section 3.2 for a left-orthogonal TT
+ * (V(X_n)^T V(X_n) = I for n < N, as Algorithms 5 and 7 produce it), without
+ * re-orthogonalizing: Algorithm 2's truncation loop run right to left, per
+ * bond the thin QR of H(X_n)^T, the SVD of R with the eps rule
+ * (eps = tol ||X|| / sqrt(N-1), ||X|| = ||X_N||_F) and at most max_rank
+ * singular values kept, then H(X_n) := (Q U)^T and V(X_{n-1}) := V(X_{n-1}) V S.
+ * ||X_out - X|| <= tol ||X|| when only the tolerance cuts.
+ *   N, dims, ranks  the TT (host; ranks N+1 with r_0 = r_N = 1 and
+ *                   r_{n-1} <= I_n r_n, r_n <= r_{n-1} I_n)
+ *   cores           host array of N device pointers, core n compact
+ *                   (r_{n-1}, I_n, r_n): overwritten with the result, written
+ *                   compactly at out_ranks
+ *   tol, max_rank   tol <= 0: no tolerance; max_rank <= 0: no cap (one of the
+ *                   two must be set)
+ * Errors: TT_EINVAL, TT_EUNSUPPORTED (a rank above 1024), TT_ENOMEM, TT_ECUDA.
+ */
+int tt_truncate_lorth(int32_t N, const int64_t* dims, const int64_t* ranks, double* const* cores, double tol,
+                      int64_t max_rank, int64_t* out_ranks, void* workspace, size_t workspace_bytes, void* stream);
+size_t tt_truncate_lorth_workspace(int32_t N, const int64_t* dims, const int64_t* ranks, double tol,
+                                   int64_t max_rank);
+
+/*
  * tt_round_sum_rand_noalloc -- tt_round_sum_rand for callers that cannot
  * allocate device memory (no counterpart in the paper: it only changes where the
  * scratch lives). Some callers may not call cudaMalloc at the point of the
- * rounding: code being captured into a CUDA graph by a framework that forbids
- * allocation during capture, real-time loops with a fixed memory budget, hosts
- * that hand the library only its inputs and outputs. This entry point takes the
+ * rounding: real-time loops with a fixed memory budget, plug-ins whose host
+ * application hands the library only its inputs and outputs, processes whose
+ * device memory is already claimed by another allocator. This entry point takes the
  * same arguments as tt_round_sum_rand minus the workspace and uses a fixed
  * device array of TT_NOALLOC_SCRATCH_BYTES inside the library instead; every
  * GPU that loads the library holds that array until the process exits. It
@@ -379,6 +436,17 @@ int tt_gemm_emulated_f64(int64_t M, int64_t N, int64_t K, double alpha, const do
  */
 int tt_selftest_tcgen05_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B, float* D, int* err,
                              void* stream);
+
+/*
+ * tt_debug_inject_device_status -- test hook for the failure reporting (no
+ * counterpart in the paper). Arms `bits` (1 = a bounded device wait gave up,
+ * 2 = a thin QR could not orthogonalize a block): the next read-back of a
+ * device status word by this library first overwrites that word on the device
+ * with bits by a host copy, so the call returns the matching status
+ * (TT_ETIMEOUT, TT_ESINGULAR) through the normal path. The device work itself
+ * is not changed. 0 disarms; the hook disarms itself when consumed.
+ */
+void tt_debug_inject_device_status(int32_t bits);
 
 /*
  * Measurement hooks (no counterpart in the paper; used by the benchmark).

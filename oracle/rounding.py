@@ -271,6 +271,18 @@ def round_sum_twosided(Ys, Lsk, Rsk, coeffs=None):
     return round_twosided(block_sum(Ys, coeffs), Lsk, Rsk)
 
 
+def round_sum_twosided_orth(Ys, Lsk, Rsk, coeffs=None, eps0=0.0):
+    """Algorithm 6 with the orthogonalizing restructure that Section 3.3
+    mentions without spelling out (reading: the Two-Sided cores are
+    left-orthogonalized by the left-to-right mirror of Algorithm 1, which
+    carries each thin-QR R factor into the next core), followed, when eps0 > 0,
+    by the Section 3.2 truncation of the left-orthogonal result."""
+    X = orthogonalize_lr(round_sum_twosided(Ys, Lsk, Rsk, coeffs))
+    if eps0 > 0:
+        X = truncate_left_orthogonal(X, eps0)
+    return X
+
+
 def truncate_left_orthogonal(X, eps0=0.0, max_rank=None, return_sv=False):
     """Truncation of a left-orthogonal TT (the Randomize-then-Orthogonalize
     output, Section 3.2) without re-orthogonalizing: ||X|| = ||X_N||;

@@ -37,6 +37,11 @@ SIGNATURES = {
     "tt_round_twosided": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_i64, P_vp, P_vp, c_u64, c_i32,
                                   P_vp, P_i64, c_vp, c_size, c_vp]),
     "tt_round_twosided_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64, P_i64, c_i32]),
+    "tt_round_twosided_orth": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_i64, P_vp, P_vp, c_u64,
+                                       c_dbl, c_i32, P_vp, P_i64, c_vp, c_size, c_vp]),
+    "tt_round_twosided_orth_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64, P_i64, c_dbl, c_i32]),
+    "tt_truncate_lorth": (c_i32, [c_i32, P_i64, P_i64, P_vp, c_dbl, c_i64, P_i64, c_vp, c_size, c_vp]),
+    "tt_truncate_lorth_workspace": (c_size, [c_i32, P_i64, P_i64, c_dbl, c_i64]),
     "tt_noalloc_scratch_bytes": (c_size, []),
     "tt_round_sum_rand_noalloc": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl,
                                           c_i32, P_vp, P_i64, c_vp]),
@@ -46,6 +51,9 @@ SIGNATURES = {
     "tt_sum_plan_run": (c_i32, [c_vp, P_vp, P_dbl, c_u64, P_vp, P_i64, c_vp]),
     "tt_sum_plan_destroy": (c_i32, [c_vp]),
     "tt_sum_plan_launches": (c_i64, [c_vp]),
+    "tt_sum_plan_status": (c_i32, [c_vp, c_vp]),
+    "tt_batch_plan_status": (c_i32, [c_vp, c_vp]),
+    "tt_debug_inject_device_status": (None, [c_i32]),
     "tt_sum_plan_host_layout": (c_i32, [c_vp, P_i64, P_i64, P_i64, P_i64]),
     "tt_sum_plan_run_host": (c_i32, [c_vp, c_vp, P_dbl, c_u64, c_vp, P_i64, c_vp]),
     "tt_batch_plan_create": (c_i32, [c_i32, c_vp, c_i32, c_i32, P_vp, c_vp]),

@@ -292,6 +292,11 @@ class SumRoundingPlan:
         d = self.dims
         return [out[oo[n]:oo[n] + r[n] * d[n] * r[n + 1]].view(r[n], d[n], r[n + 1]) for n in range(self.N)]
 
+    def status(self, stream=None):
+        """Waits for the last replay and raises TTError if a kernel reported a
+        failure (TT_ETIMEOUT, TT_ESINGULAR)."""
+        _check(nat.lib().tt_sum_plan_status(self._h, _stream(stream, self.device)))
+
     def close(self):
         if getattr(self, "_h", None):
             nat.lib().tt_sum_plan_destroy(self._h)
@@ -367,6 +372,10 @@ class BatchRoundingPlan:
             i += N + 1
             res.append([o[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)])
         return res
+
+    def status(self, stream=None):
+        """Waits for the last replay and raises TTError if a kernel reported a failure."""
+        _check(nat.lib().tt_batch_plan_status(self._h, _stream(stream, self.device)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -525,11 +534,82 @@ def tt_round_twosided(summands, ells, *, rhos=None, sketch_left=None, sketch_rig
     return out
 
 
+def tt_round_twosided_orth(summands, ells, *, rhos=None, sketch_left=None, sketch_right=None, seed=0, coeffs=None,
+                           tol=0.0, precision="fp64", workspace=None, stream=None):
+    """Algorithm 6 with the orthogonalizing restructure: the same tensor as
+    tt_round_twosided in left-orthogonal form, truncated to tol (Section 3.2)
+    when tol > 0. Returns the cores at the decided ranks."""
+    import math
+    N, K, dims, ranks, flat = _sum_args(summands)
+    device = summands[0][0].device
+    ell = clamp_ranks(dims, ells)
+    rr = clamp_ranks(dims, rhos if rhos is not None else [int(math.ceil(1.5 * x)) for x in ell])
+    L = nat.lib()
+    dims_a, ranks_a, ell_a, rho_a = _i64(dims), _i64(ranks), _i64(ell), _i64(rr)
+    for sk, rk, name in ((sketch_left, ell, "sketch_left"), (sketch_right, rr, "sketch_right")):
+        if sk is not None:
+            for n, c in enumerate(sk):
+                _check_core(c, f"{name} core {n}")
+                if tuple(c.shape) != (rk[n], dims[n], rk[n + 1]):
+                    raise ValueError(f"{name} core {n} has shape {tuple(c.shape)}")
+    out = [torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float64, device=device) for n in range(N)]
+    nb = L.tt_round_twosided_orth_workspace(N, K, dims_a, ranks_a, ell_a, rho_a, float(tol), _PREC[precision])
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    co = (ctypes.c_double * K)(*[float(c) for c in coeffs]) if coeffs is not None else None
+    out_ranks = (ctypes.c_int64 * (N + 1))()
+    _check(L.tt_round_twosided_orth(N, K, dims_a, ranks_a, _ptrs(flat), co, ell_a, rho_a,
+                                    _ptrs(sketch_left) if sketch_left is not None else None,
+                                    _ptrs(sketch_right) if sketch_right is not None else None,
+                                    ctypes.c_uint64(int(seed)), float(tol), _PREC[precision], _ptrs(out), out_ranks,
+                                    wp, wb, _stream(stream, device)))
+    r = [int(x) for x in out_ranks]
+    return [out[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)]
+
+
+def tt_truncate_lorth(cores, *, tol=0.0, max_rank=0, workspace=None, stream=None):
+    """Section 3.2 truncation of a left-orthogonal TT (list of float64 CUDA
+    cores). The cores are copied first (the call works in place on the copy);
+    returns the truncated cores."""
+    N = len(cores)
+    device = cores[0].device
+    dims = [int(c.shape[1]) for c in cores]
+    ranks = [int(cores[0].shape[0])] + [int(c.shape[2]) for c in cores]
+    work = []
+    for n, c in enumerate(cores):
+        _check_core(c, f"core {n}")
+        work.append(c.clone())
+    L = nat.lib()
+    dims_a, ranks_a = _i64(dims), _i64(ranks)
+    nb = L.tt_truncate_lorth_workspace(N, dims_a, ranks_a, float(tol), int(max_rank))
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    out_ranks = (ctypes.c_int64 * (N + 1))()
+    _check(L.tt_truncate_lorth(N, dims_a, ranks_a, _ptrs(work), float(tol), int(max_rank), out_ranks, wp, wb,
+                               _stream(stream, device)))
+    r = [int(x) for x in out_ranks]
+    return [work[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)]
+
+
 def tt_round_rand(Y, ells, **kw):
     """Algorithm 5 (single TT, Randomize-then-Orthogonalize): tt_round_sum_rand with K = 1."""
     if kw.get("coeffs") is not None:
         raise ValueError("tt_round_rand takes no coefficients")
     return tt_round_sum_rand([Y], ells, **kw)
+
+
+TT_ESINGULAR = 5
+TT_ETIMEOUT = 6
+DEV_TIMEOUT = 1
+DEV_QR_FAIL = 2
+
+
+def debug_inject_device_status(bits):
+    """Test hook: the next read-back of a device status word sees `bits`
+    (DEV_TIMEOUT, DEV_QR_FAIL), written over the device word by a host copy."""
+    nat.lib().tt_debug_inject_device_status(int(bits))
 
 
 def prof_enable(on=True):

@@ -213,7 +213,11 @@ int backward_common(int32_t N, const int64_t* dims, const int64_t* ranks, const 
                                size_only ? nullptr : xbar, size_only ? nullptr : ybar, ar, sc);
   };
   if (size_only) return plan_workspace_bytes(build, size_only);
-  return plan_execute(build, workspace, ws_bytes, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dstat = 0;
+  TTR_TRY(plan_execute(build, workspace, ws_bytes, s, &dstat));
+  TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  return status_code(dstat, "tt_round_rand_backward");
 }
 
 }  // namespace

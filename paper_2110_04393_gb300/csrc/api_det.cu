@@ -100,7 +100,7 @@ int64_t formed_capacity(const DetProblem& P, int n) { return P.S[n - 1] * P.I[n 
 // of the right-orthogonal result in Rp[0..N].
 int plan_formed_orth(const DetProblem& P, Arena& ar, Schedule& sc, const std::vector<double*>& X,
                      std::vector<int64_t>& Rp, double* tmp, int64_t tmp_cap, double* qtmp,
-                     std::vector<const int*>* big_status, const QrPool* pool, double* rbuf) {
+                     const QrPool* pool, double* rbuf) {
   const int N = P.N, K = P.K;
   auto In = [&](int n) { return P.I[n - 1]; };
   // ---- formed sum (Section 2.1)
@@ -160,7 +160,6 @@ int plan_formed_orth(const DetProblem& P, Arena& ar, Schedule& sc, const std::ve
       QrBufs qb = qr_view(*pool, m, int(k));
       double* Rb = rbuf;
       qr_plan(sc, qb, Xn, 1, m, qtmp, k, 1, Rb);
-      if (k > TSQR_KMAX && big_status) big_status->push_back(qb.status);
       // H(X_n) := Q^T, i.e. core n is Q as a column-major m x k array
       sc.copy3({Copy3{qtmp, Xn, 1, m, k, 0, k, 1, 0, 1, m, 1.0, 0}});
       // V(X_{n-1}) := V(X_{n-1}) R^T
@@ -215,7 +214,7 @@ int64_t det_tmp_doubles(const DetProblem& P) {
 
 // -------------------------------------------------------------------------------------------
 int build_det(const DetProblem& P, double tol, int64_t max_rank, double* const* out, Arena& ar, Schedule& sc,
-              int64_t** rk_dev, int** fail_dev) {
+              int64_t** rk_dev) {
   const int N = P.N;
   auto In = [&](int n) { return P.I[n - 1]; };
   const int64_t tcap = det_tmp_doubles(P);
@@ -235,8 +234,7 @@ int build_det(const DetProblem& P, double tol, int64_t max_rank, double* const* 
   const QrPool pool = qr_pool_reserve(ar, shapes);
   double* rbuf = ar.take<double>(kq * kq);
   std::vector<int64_t> Rp;
-  std::vector<const int*> bigst;
-  TTR_TRY(plan_formed_orth(P, ar, sc, X, Rp, tmp, tcap, qtmp, &bigst, &pool, rbuf));
+  TTR_TRY(plan_formed_orth(P, ar, sc, X, Rp, tmp, tcap, qtmp, &pool, rbuf));
   for (int n = 1; n < N; ++n)
     if (Rp[n - 1] * In(n) < Rp[n]) {
       set_error("deterministic rounding: a vertical unfolding would be wide at bond " + std::to_string(n));
@@ -250,9 +248,7 @@ int build_det(const DetProblem& P, double tol, int64_t max_rank, double* const* 
   double* G2 = ar.take<double>(kmax * kmax);
   double* sig = ar.take<double>(kmax);
   double* sbig = ar.take<double>(std::max<size_t>(svd_scratch_doubles(int(kmax)), 1));
-  int* fail = ar.take<int>(1);
   *rk_dev = rk;
-  *fail_dev = fail;
   {
     std::vector<double> raw(N + 1);
     std::vector<int64_t> v(Rp.begin(), Rp.end());
@@ -260,7 +256,6 @@ int build_det(const DetProblem& P, double tol, int64_t max_rank, double* const* 
     sc.upload(reinterpret_cast<double*>(rk), raw);
   }
   sc.add([=](cudaStream_t s) -> int {
-    if (fail) TTR_CHECK_CUDA(cudaMemsetAsync(fail, 0, sizeof(int), s));
     if (tol > 0.0) return norm_eps_launch(X[1], In(1) * Rp[1], tol, N, eps, s);
     return int(TT_OK);
   });
@@ -273,7 +268,6 @@ int build_det(const DetProblem& P, double tol, int64_t max_rank, double* const* 
     double* Xq = X[n + 1];
     qr_plan(sc, qb, Xn, k, 1, qtmp, k, 1, Rb);
     const int rcap = int(max_rank > 0 ? std::min<int64_t>(max_rank, k) : k);
-    if (k > TSQR_KMAX) bigst.push_back(qb.status);
     sc.add([=](cudaStream_t s) -> int {
       return svd_trunc_launch(int(k), Rb, tol > 0.0 ? eps : nullptr, rcap, G1, G2, sig, rk + n, s, sbig);
     });
@@ -288,9 +282,6 @@ int build_det(const DetProblem& P, double tol, int64_t max_rank, double* const* 
       return int(TT_OK);
     });
   }
-  // a Cholesky-QR failure above the Householder limit is reported to the caller
-  for (const int* st : bigst)
-    sc.add([=](cudaStream_t s) -> int { return or_flag_launch(fail, st, s); });
   // ---- compact every core to its decided ranks
   for (int n = 1; n <= N; ++n) {
     double* Xn = X[n];
@@ -320,7 +311,7 @@ int build_orthrand(const DetProblem& P, const std::vector<int64_t>& ell, const d
   const QrPool pool = qr_pool_reserve(ar, shapes);
   double* rbuf = ar.take<double>(kq * kq);
   std::vector<int64_t> Rp;
-  TTR_TRY(plan_formed_orth(P, ar, sc, X, Rp, tmp, tcap, qtmp, nullptr, &pool, rbuf));
+  TTR_TRY(plan_formed_orth(P, ar, sc, X, Rp, tmp, tcap, qtmp, &pool, rbuf));
   int64_t zcap = 1;
   for (int n = 1; n <= N; ++n) zcap = std::max(zcap, ell[n - 1] * In(n) * std::max(Rp[n], ell[n]));
   double* Z[2] = {ar.take<double>(zcap), ar.take<double>(zcap)};
@@ -385,21 +376,25 @@ static int det_common(int32_t N, int32_t K, const int64_t* dims, const int64_t* 
   std::vector<double*> outv(N, nullptr);
   if (out) outv.assign(out, out + N);
   int64_t* rk = nullptr;
-  int* fail = nullptr;
-  BuildFn build = [&](Arena& ar, Schedule& sc) { return build_det(P, tol, max_rank, outv.data(), ar, sc, &rk, &fail); };
+  std::vector<int64_t> r(N + 1);
+  BuildFn build = [&](Arena& ar, Schedule& sc) {
+    TTR_TRY(build_det(P, tol, max_rank, outv.data(), ar, sc, &rk));
+    int64_t* rkd = rk;
+    int64_t* rkh = r.data();
+    const int n1 = N + 1;
+    sc.add([rkd, rkh, n1](cudaStream_t st) -> int {
+      if (rkd) TTR_CHECK_CUDA(cudaMemcpyAsync(rkh, rkd, sizeof(int64_t) * n1, cudaMemcpyDeviceToHost, st));
+      return int(TT_OK);
+    });
+    return int(TT_OK);
+  };
   if (size_only) return plan_workspace_bytes(build, size_only);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  TTR_TRY(plan_execute(build, workspace, ws_bytes, s));
-  std::vector<int64_t> r(N + 1);
-  int f = 0;
-  TTR_CHECK_CUDA(cudaMemcpyAsync(r.data(), rk, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, s));
-  TTR_CHECK_CUDA(cudaMemcpyAsync(&f, fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int dstat = 0;
+  TTR_TRY(plan_execute(build, workspace, ws_bytes, s, &dstat));
   TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  TTR_TRY(status_code(dstat, "tt_round_det"));
   for (int n = 0; n <= N; ++n) out_ranks[n] = r[n];
-  if (f) {
-    set_error("deterministic rounding: Cholesky QR could not orthogonalize a block above the Householder limit");
-    return TT_ESINGULAR;
-  }
   return TT_OK;
 }
 
@@ -438,7 +433,11 @@ static int orthrand_common(int32_t N, int32_t K, const int64_t* dims, const int6
   if (out) outv.assign(out, out + N);
   BuildFn build = [&](Arena& ar, Schedule& sc) { return build_orthrand(P, ell, omega, seed, outv.data(), ar, sc); };
   if (size_only) return plan_workspace_bytes(build, size_only);
-  TTR_TRY(plan_execute(build, workspace, ws_bytes, static_cast<cudaStream_t>(stream)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dstat = 0;
+  TTR_TRY(plan_execute(build, workspace, ws_bytes, s, &dstat));
+  TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  TTR_TRY(status_code(dstat, "tt_round_orthrand"));
   for (int n = 0; n <= N; ++n) out_ranks[n] = ell[n];
   return TT_OK;
 }

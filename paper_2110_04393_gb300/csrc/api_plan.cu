@@ -86,6 +86,7 @@ struct SumUnit {
   int64_t in_total = 0, out_total = 0;
   double* land_in = nullptr;                  // device landing of the host input copy
   double* land_out = nullptr;                 // device source of the host output copy
+  int* h_status = nullptr;                    // pinned slot receiving the replay's device status word
 };
 
 size_t unit_stage_bytes(int N, int K) {
@@ -209,6 +210,8 @@ StageFn unit_epilogue(SumUnit* u, const char* stage) {
       TTR_CHECK_LAUNCH();
       prof_count_launch(1);
     }
+    if (u->h_status)
+      TTR_CHECK_CUDA(cudaMemcpyAsync(u->h_status, u->gp.sc->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     return int(TT_OK);
   };
 }
@@ -242,6 +245,7 @@ struct UnitGraph {
   void* d_stage = nullptr;
   void* h_stage = nullptr;
   int64_t* h_rk = nullptr;       // all units' ranks (sum of N_b + 1)
+  int* h_status = nullptr;       // one device status word per unit (pinned)
   std::vector<size_t> rk_off;
   cudaEvent_t staged = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -264,6 +268,7 @@ void unit_graph_free(UnitGraph* g) {
   if (g->d_stage) cudaFree(g->d_stage);
   if (g->h_stage) cudaFreeHost(g->h_stage);
   if (g->h_rk) cudaFreeHost(g->h_rk);
+  if (g->h_status) cudaFreeHost(g->h_status);
   if (g->staged) cudaEventDestroy(g->staged);
   *g = UnitGraph{};
 }
@@ -283,12 +288,17 @@ int unit_graph_capture(UnitGraph* g, int width) {
   if (cudaMalloc(&g->d_stage, g->stage_bytes) != cudaSuccess ||
       cudaMallocHost(&g->h_stage, g->stage_bytes) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&g->h_rk), sizeof(int64_t) * std::max<size_t>(rk, 1)) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&g->h_status), sizeof(int) * g->units.size()) != cudaSuccess ||
       cudaEventCreateWithFlags(&g->staged, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     set_error("plan: staging allocation failed");
     return TT_ENOMEM;
   }
   std::memset(g->h_stage, 0, g->stage_bytes);
+  for (size_t b = 0; b < g->units.size(); ++b) {
+    g->h_status[b] = 0;
+    g->units[b]->h_status = g->h_status + b;
+  }
   const char* ds = static_cast<const char*>(g->d_stage);
   auto body = [&](cudaStream_t cs) -> int {
     if (g->width == 1) {
@@ -325,11 +335,31 @@ int unit_graph_capture(UnitGraph* g, int width) {
   return capture_graph(body, &g->exec, &g->prof, &g->kernels);
 }
 
+// Device status of the last replay (valid once its stream has been synchronized).
+int unit_graph_status(const UnitGraph* g, const char* who) {
+  int bits = 0;
+  for (size_t b = 0; b < g->units.size(); ++b) bits |= g->h_status[b];
+  return status_code(bits, who);
+}
+
 // One replay: staging copy, graph launch, rank read-back (tolerance units).
+// The replay's device status words land in the pinned h_status slots; with a
+// tolerance (the call waits) they are turned into the return status.
 int unit_graph_run(UnitGraph* g, cudaStream_t s, int64_t* const* out_ranks) {
   TTR_CHECK_CUDA(cudaMemcpyAsync(g->d_stage, g->h_stage, g->stage_bytes, cudaMemcpyHostToDevice, s));
   TTR_CHECK_CUDA(cudaEventRecord(g->staged, s));
   TTR_CHECK_CUDA(cudaGraphLaunch(g->exec, s));
+  {
+    // test hook: overwrite unit 0's device status word after the replay and read it again
+    static thread_local int inj = 0;
+    inj = take_injected_status();
+    if (inj != 0) {
+      SumUnit* u0 = g->units[0];
+      TTR_CHECK_CUDA(cudaMemcpyAsync(u0->gp.sc->dev_status, &inj, sizeof(int), cudaMemcpyHostToDevice, s));
+      TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+      TTR_CHECK_CUDA(cudaMemcpyAsync(u0->h_status, u0->gp.sc->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+  }
   bool synced = false;
   bool any_tol = false;
   for (SumUnit* u : g->units) any_tol = any_tol || u->tol > 0.0;
@@ -342,6 +372,7 @@ int unit_graph_run(UnitGraph* g, cudaStream_t s, int64_t* const* out_ranks) {
     }
     TTR_CHECK_CUDA(cudaStreamSynchronize(s));
     synced = true;
+    TTR_TRY(unit_graph_status(g, "plan replay"));
   }
   for (size_t b = 0; b < g->units.size(); ++b) {
     SumUnit* u = g->units[b];
@@ -453,7 +484,16 @@ int tt_sum_plan_run_host(tt_sum_plan* p, const double* h_in, const double* coeff
   if (u->out_total > 0)
     TTR_CHECK_CUDA(cudaMemcpyAsync(h_out, u->land_out, sizeof(double) * u->out_total, cudaMemcpyDeviceToHost, s));
   TTR_CHECK_CUDA(cudaStreamSynchronize(s));
-  return TT_OK;
+  return unit_graph_status(&p->g, "tt_sum_plan_run_host");
+}
+
+int tt_sum_plan_status(tt_sum_plan* p, void* stream) {
+  if (!p) {
+    set_error("tt_sum_plan_status: null plan");
+    return TT_EINVAL;
+  }
+  TTR_CHECK_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  return unit_graph_status(&p->g, "tt_sum_plan_run");
 }
 
 int tt_sum_plan_destroy(tt_sum_plan* p) {
@@ -518,6 +558,15 @@ int tt_batch_plan_run(tt_batch_plan* p, const double* const* cores, const uint64
     ri += size_t(u->P.N) + 1;
   }
   return unit_graph_run(&p->g, static_cast<cudaStream_t>(stream), rk.data());
+}
+
+int tt_batch_plan_status(tt_batch_plan* p, void* stream) {
+  if (!p) {
+    set_error("tt_batch_plan_status: null plan");
+    return TT_EINVAL;
+  }
+  TTR_CHECK_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  return unit_graph_status(&p->g, "tt_batch_plan_run");
 }
 
 int tt_batch_plan_destroy(tt_batch_plan* p) {

@@ -14,6 +14,7 @@
 // (Section 3.2 with Algorithm 2's loop mirrored): per bond TSQR of H(X_n)^T,
 // the eps-rule on R, then X_n := (Q G1)^T and X_{n-1} := X_{n-1} G2.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -56,7 +57,7 @@ static GemmDesc* bind_schedule_regions(Arena& a, const Schedule& probe, Schedule
   GemmDesc* d_descs = a.take<GemmDesc>(std::max<size_t>(probe.descs.size(), 1));
   s.cnt = a.take<int>(size_t(std::max<int64_t>(probe.cnt_need, 1)));
   s.d_copies = a.take<Copy3>(std::max<size_t>(probe.copies.size(), 1));
-  s.tc_err = a.take<int>(1);
+  s.dev_status = a.take<int>(1);
   s.acc = a.take<long long>(size_t(std::max<int64_t>(probe.acc_need, 1)));
   s.ex = a.take<int>(size_t(std::max<int64_t>(probe.ex_need, 1)));
   s.planes = a.take<uint8_t>(size_t(std::max<int64_t>(probe.plane_need, 1)));
@@ -67,7 +68,7 @@ static GemmDesc* bind_schedule_regions(Arena& a, const Schedule& probe, Schedule
 // accumulators and exponent tags).
 static int reset_schedule_regions(const Schedule& probe, const Schedule& s, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(s.cnt, 0, size_t(std::max<int64_t>(probe.cnt_need, 1)) * sizeof(int), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s.tc_err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.dev_status, 0, sizeof(int), st);
   if (e == cudaSuccess && probe.acc_need > 0)
     e = cudaMemsetAsync(s.acc, 0, size_t(probe.acc_need) * sizeof(long long), st);
   if (e == cudaSuccess && probe.ex_need > 0) e = cudaMemsetAsync(s.ex, 0, size_t(probe.ex_need) * sizeof(int), st);
@@ -78,7 +79,42 @@ static int reset_schedule_regions(const Schedule& probe, const Schedule& s, cuda
   return TT_OK;
 }
 
-int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStream_t st) {
+static std::atomic<int> g_inject{0};
+
+int take_injected_status() { return g_inject.exchange(0); }
+
+int status_code(int bits, const char* who) {
+  if (bits == 0) return TT_OK;
+  if (bits & DEV_TIMEOUT) {
+    set_error(std::string(who) + ": a bounded device wait gave up (outputs are not valid)");
+    return TT_ETIMEOUT;
+  }
+  if (bits & DEV_QR_FAIL) {
+    set_error(std::string(who) + ": a thin QR above the Householder fallback limit could not orthogonalize a block");
+    return TT_ESINGULAR;
+  }
+  set_error(std::string(who) + ": unknown device status " + std::to_string(bits));
+  return TT_ECUDA;
+}
+
+// Enqueues the read-back of a run's device status word into *host (after the
+// armed test injection, if any, overwrote the device word).
+static int enqueue_status_read(int* dev, int* host, cudaStream_t st) {
+  static thread_local int inj_src = 0;
+  inj_src = take_injected_status();
+  if (inj_src != 0) {
+    cudaError_t e = cudaMemcpyAsync(dev, &inj_src, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error(std::string("status injection: ") + cudaGetErrorString(e));
+      return TT_ECUDA;
+    }
+  }
+  TTR_CHECK_CUDA(cudaMemcpyAsync(host, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  return TT_OK;
+}
+
+int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStream_t st, int* host_status) {
   size_t need = 0;
   Schedule probe;
   {
@@ -131,6 +167,7 @@ int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStr
     }
   }
   for (size_t i = 0; rc == TT_OK && i < s.items.size(); ++i) rc = s.items[i](st, d_descs);
+  if (rc == TT_OK && host_status) rc = enqueue_status_read(s.dev_status, host_status, st);
   if (owned) cudaFreeAsync(ws, st);
   return rc;
 }
@@ -356,8 +393,9 @@ struct TruncBufs {
   double* tmp;      // max core size
 };
 
-static int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int64_t>& I,
-                           const std::vector<int64_t>& ell, double tol, double* const* out, int64_t** rk_out) {
+// tol <= 0: no tolerance (ranks capped by max_rank only); max_rank <= 0: no cap.
+int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int64_t>& I, const std::vector<int64_t>& ell,
+                    double tol, double* const* out, int64_t** rk_out, int64_t max_rank) {
   TruncBufs b;
   int64_t qmax = 1, kmax = 1, cmax = 1;
   for (int n = 2; n <= N; ++n) {
@@ -386,16 +424,19 @@ static int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int
     std::memcpy(raw.data(), tmp.data(), sizeof(int64_t) * (N + 1));
     sc.upload(reinterpret_cast<double*>(b.rk), raw);
   }
-  sc.add([=](cudaStream_t s) -> int {
-    return norm_eps_launch(out[N - 1], ell[N - 1] * I[N - 1], tol, N, b.eps, s);
-  });
+  if (tol > 0.0)
+    sc.add([=](cudaStream_t s) -> int {
+      return norm_eps_launch(out[N - 1], ell[N - 1] * I[N - 1], tol, N, b.eps, s);
+    });
+  const double* epsp = tol > 0.0 ? b.eps : nullptr;
   for (int n = N; n >= 2; --n) {
     const int64_t m = I[n - 1] * ell[n], k = ell[n - 1];
+    const int rcap = int(max_rank > 0 ? std::min<int64_t>(max_rank, k) : k);
     double* Xn = out[n - 1];
     double* Xp = out[n - 2];
     qr_plan(sc, qr_view(pool, m, int(k)), Xn, 1, m, b.Qt, k, 1, b.Rb, true);
     sc.add([=](cudaStream_t s) -> int {
-      return svd_trunc_launch(int(k), b.Rb, b.eps, int(k), b.G1, b.G2, b.sig, b.rk + (n - 1), s, sbig);
+      return svd_trunc_launch(int(k), b.Rb, epsp, rcap, b.G1, b.G2, b.sig, b.rk + (n - 1), s, sbig);
     });
     // new H(X_n) = (Q G1)^T : column-major m x k view of core n
     sc.gemm({gdesc(b.Qt, k, 1, b.G1, k, 1, Xn, 1, m, m, k, k)});
@@ -536,7 +577,7 @@ int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t
     big({gdesc(Qn, 1, k, X, S[n], 1, Mn, S[n], 1, k, S[n], m)});
   }
 
-  if (tol > 0.0) TTR_TRY(plan_truncation(ar, sc, N, I, ell, tol, out, rk_dev));
+  if (tol > 0.0) TTR_TRY(plan_truncation(ar, sc, N, I, ell, tol, out, rk_dev, 0));
   return TT_OK;
 }
 
@@ -577,6 +618,8 @@ int tt_sketch_gaussian(int32_t N, const int64_t* dims, const int64_t* ells, uint
 
 int tt_mixed_digits(double tol, int32_t N) { return ttr::mixed_digits(tol, N); }
 
+void tt_debug_inject_device_status(int32_t bits) { g_inject.store(int(bits)); }
+
 __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, const int64_t* dims,
                                                          const int64_t* ranks,
                            const double* const* cores, const double* coeffs, const int64_t* ells,
@@ -606,15 +649,81 @@ __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, 
   };
   if (size_only) return plan_workspace_bytes(build, size_only);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  TTR_TRY(plan_execute(build, workspace, ws_bytes, s));
-  if (tol > 0.0) {
-    std::vector<int64_t> rk(N + 1);
-    TTR_CHECK_CUDA(cudaMemcpyAsync(rk.data(), rk_dev, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, s));
-    TTR_CHECK_CUDA(cudaStreamSynchronize(s));
-    for (int n = 0; n <= N; ++n) out_ranks[n] = rk[n];
-  } else {
-    for (int n = 0; n <= N; ++n) out_ranks[n] = P.ell[n];
+  int dstat = 0;
+  std::vector<int64_t> rk(N + 1);
+  // the ranks are read by a copy enqueued inside the build (before a
+  // stream-ordered free of an owned workspace)
+  BuildFn build_rk = [&](Arena& ar, Schedule& sc) {
+    TTR_TRY(build(ar, sc));
+    if (tol > 0.0) {
+      int64_t* rkd = rk_dev;
+      int64_t* rkh = rk.data();
+      sc.add([rkd, rkh, N](cudaStream_t st) -> int {
+        if (rkd) TTR_CHECK_CUDA(cudaMemcpyAsync(rkh, rkd, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+        return int(TT_OK);
+      });
+    }
+    return int(TT_OK);
+  };
+  TTR_TRY(plan_execute(build_rk, workspace, ws_bytes, s, &dstat));
+  TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  TTR_TRY(status_code(dstat, "tt_round_sum_rand"));
+  for (int n = 0; n <= N; ++n) out_ranks[n] = tol > 0.0 ? rk[n] : P.ell[n];
+  return TT_OK;
+}
+
+static int truncate_common(int32_t N, const int64_t* dims, const int64_t* ranks, double* const* cores, double tol,
+                           int64_t max_rank, int64_t* out_ranks, void* workspace, size_t ws_bytes, void* stream,
+                           size_t* size_only) {
+  if (N < 1 || !dims || !ranks || (!size_only && (!cores || !out_ranks))) {
+    set_error("tt_truncate_lorth: invalid arguments");
+    return TT_EINVAL;
   }
+  if (tol <= 0.0 && max_rank <= 0) {
+    set_error("tt_truncate_lorth: needs tol > 0 or max_rank > 0");
+    return TT_EINVAL;
+  }
+  std::vector<int64_t> I(dims, dims + N), r(ranks, ranks + N + 1);
+  for (int n = 0; n < N; ++n)
+    if (I[n] < 1) { set_error("tt_truncate_lorth: mode sizes must be positive"); return TT_EINVAL; }
+  for (int n = 0; n <= N; ++n)
+    if (r[n] < 1) { set_error("tt_truncate_lorth: ranks must be positive"); return TT_EINVAL; }
+  if (r[0] != 1 || r[N] != 1 || clamp_rank_vector(I, r.data()) != r) {
+    set_error("tt_truncate_lorth: ranks must start and end with 1 and satisfy r_{n-1} <= I_n r_n, r_n <= r_{n-1} I_n");
+    return TT_EINVAL;
+  }
+  for (int n = 1; n < N; ++n)
+    if (r[n] > TT_MAX_RANK) { set_error("tt_truncate_lorth: rank above 1024"); return TT_EUNSUPPORTED; }
+  std::vector<double*> cv(N, nullptr);
+  if (cores) {
+    cv.assign(cores, cores + N);
+    for (auto* c : cv)
+      if (!c) { set_error("tt_truncate_lorth: null core pointer"); return TT_EINVAL; }
+  }
+  int64_t* rk_dev = nullptr;
+  std::vector<int64_t> rk(N + 1);
+  BuildFn build = [&](Arena& ar, Schedule& sc) {
+    if (N == 1) return int(TT_OK);
+    TTR_TRY(plan_truncation(ar, sc, N, I, r, tol, cv.data(), &rk_dev, max_rank));
+    int64_t* rkd = rk_dev;
+    int64_t* rkh = rk.data();
+    sc.add([rkd, rkh, N](cudaStream_t st) -> int {
+      if (rkd) TTR_CHECK_CUDA(cudaMemcpyAsync(rkh, rkd, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+      return int(TT_OK);
+    });
+    return int(TT_OK);
+  };
+  if (size_only) return plan_workspace_bytes(build, size_only);
+  if (N == 1) {
+    out_ranks[0] = out_ranks[1] = 1;
+    return TT_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dstat = 0;
+  TTR_TRY(plan_execute(build, workspace, ws_bytes, s, &dstat));
+  TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  TTR_TRY(status_code(dstat, "tt_truncate_lorth"));
+  for (int n = 0; n <= N; ++n) out_ranks[n] = rk[n];
   return TT_OK;
 }
 
@@ -633,6 +742,19 @@ size_t tt_round_sum_rand_workspace(int32_t N, int32_t K, const int64_t* dims, co
                       nullptr, 0, nullptr, &bytes) != TT_OK)
     return 0;
   return bytes;
+}
+
+int tt_truncate_lorth(int32_t N, const int64_t* dims, const int64_t* ranks, double* const* cores, double tol,
+                      int64_t max_rank, int64_t* out_ranks, void* workspace, size_t workspace_bytes, void* stream) {
+  return truncate_common(N, dims, ranks, cores, tol, max_rank, out_ranks, workspace, workspace_bytes, stream,
+                         nullptr);
+}
+
+size_t tt_truncate_lorth_workspace(int32_t N, const int64_t* dims, const int64_t* ranks, double tol,
+                                   int64_t max_rank) {
+  size_t b = 0;
+  if (truncate_common(N, dims, ranks, nullptr, tol, max_rank, nullptr, nullptr, 0, nullptr, &b) != TT_OK) return 0;
+  return b;
 }
 
 int tt_round_rand(int32_t N, const int64_t* dims, const int64_t* ranks, const double* const* cores,

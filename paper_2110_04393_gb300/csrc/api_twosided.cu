@@ -51,9 +51,16 @@ int colscale_launch(double* M, int64_t rows, int64_t cols, int64_t ld, const dou
   return TT_OK;
 }
 
+// orth: the orthogonalizing restructure (Section 3.3 leaves it open): the
+// distribution runs as a left-to-right sweep that carries the R factor of each
+// core's thin QR into the next core, T_0 = 1,
+//   C_n = (T_{n-1} R_n) x_1 Y_n x_3 L_n,  V(C_n) = Q_n T_n,  X_n = Q_n (n < N),
+//   X_N = (T_{N-1} R_{N-1}) H(Y_N),
+// so the result is the same tensor in left-orthogonal form; with tol > 0 the
+// Section 3.2 truncation follows (ranks into *rk_dev).
 int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const double* const* skL,
                    const double* const* skR, uint64_t seed, int digits, double* const* out, Arena& ar,
-                   Schedule& sc) {
+                   Schedule& sc, bool orth = false, double tol = 0.0, int64_t** rk_dev = nullptr) {
   const int N = P.N, K = P.K;
   // every contraction in FP64, or (digits > 0) as the emulated FP64 product on
   // the tensor cores: both sketches span the projectors' ranges directly, so
@@ -92,7 +99,18 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
   double* sbig = ar.take<double>(std::max<size_t>(svd_scratch_doubles(int(kmax)) * size_t(nb), 1));
   std::vector<std::pair<int64_t, int>> shapes;
   for (int n = 1; n < N; ++n) shapes.push_back({rho[n], int(ell[n])});
+  if (orth)
+    for (int n = 1; n < N; ++n) shapes.push_back({ell[n - 1] * In(n), int(ell[n])});
   const QrPool pool = qr_pool_reserve(ar, shapes);
+  double *Cb = nullptr, *Tf = nullptr, *RT = nullptr;
+  if (orth) {
+    int64_t cmax = 1, rmax = 1;
+    for (int n = 1; n <= N; ++n) cmax = std::max(cmax, ell[n - 1] * In(n) * ell[n]);
+    for (int n = 0; n < N; ++n) rmax = std::max(rmax, ell[n] * S[n]);
+    Cb = ar.take<double>(cmax);
+    Tf = ar.take<double>(kmax * kmax);
+    RT = ar.take<double>(rmax);
+  }
   std::vector<const double*> L(N + 1, nullptr), Rs(N + 1, nullptr);
   for (int n = 1; n <= N; ++n) {
     if (skL) {
@@ -196,9 +214,26 @@ int build_twosided(const SumProblem& P, const std::vector<int64_t>& rho, const d
       ga.push_back(gdesc(P.core(j, n), r1, 1, Lj, ell[n], 1, Zj, ell[n], 1, r0 * In(n), ell[n], r1));
     }
     gemm(ga);
-    gemm({gdesc(Rf[n - 1], S[n - 1], 1, Z, In(n) * ell[n], 1, out[n - 1], In(n) * ell[n], 1, ell[n - 1],
-                   In(n) * ell[n], S[n - 1])});
+    if (!orth) {
+      gemm({gdesc(Rf[n - 1], S[n - 1], 1, Z, In(n) * ell[n], 1, out[n - 1], In(n) * ell[n], 1, ell[n - 1],
+                     In(n) * ell[n], S[n - 1])});
+      continue;
+    }
+    // left factor T_{n-1} R_{n-1} (T_0 = 1)
+    const double* Rl = Rf[n - 1];
+    if (n > 1) {
+      gemm({gdesc(Tf, ell[n - 1], 1, Rf[n - 1], S[n - 1], 1, RT, S[n - 1], 1, ell[n - 1], S[n - 1], ell[n - 1])});
+      Rl = RT;
+    }
+    double* dst = (n < N) ? Cb : out[n - 1];
+    gemm({gdesc(Rl, S[n - 1], 1, Z, In(n) * ell[n], 1, dst, In(n) * ell[n], 1, ell[n - 1], In(n) * ell[n],
+                   S[n - 1])});
+    if (n < N) {
+      const int64_t m = ell[n - 1] * In(n), k = ell[n];
+      qr_plan(sc, qr_view(pool, m, int(k)), Cb, k, 1, out[n - 1], k, 1, Tf, true);
+    }
   }
+  if (orth && tol > 0.0) TTR_TRY(plan_truncation(ar, sc, N, P.I, ell, tol, out, rk_dev, 0));
   return TT_OK;
 }
 
@@ -213,7 +248,7 @@ static int twosided_common(int32_t N, int32_t K, const int64_t* dims, const int6
                            const double* const* cores, const double* coeffs, const int64_t* ells,
                            const int64_t* rhos, const double* const* skL, const double* const* skR, uint64_t seed,
                            int32_t precision, double* const* out, int64_t* out_ranks, void* workspace,
-                           size_t ws_bytes, void* stream, size_t* size_only) {
+                           size_t ws_bytes, void* stream, size_t* size_only, bool orth = false, double tol = 0.0) {
   if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
     set_error("tt_round_twosided: unknown precision mode");
     return TT_EINVAL;
@@ -232,13 +267,29 @@ static int twosided_common(int32_t N, int32_t K, const int64_t* dims, const int6
   if (!size_only && (!out || !out_ranks)) { set_error("null outputs"); return TT_EINVAL; }
   std::vector<double*> outv(N, nullptr);
   if (out) outv.assign(out, out + N);
-  const int digits = (precision == TT_PREC_MIXED) ? mixed_digits(0.0, N) : 0;
+  const int digits = (precision == TT_PREC_MIXED) ? mixed_digits(orth ? tol : 0.0, N) : 0;
+  int64_t* rk_dev = nullptr;
+  std::vector<int64_t> rk(N + 1);
+  const bool trunc = orth && tol > 0.0;
   BuildFn build = [&](Arena& ar, Schedule& sc) {
-    return build_twosided(P, rho, skL, skR, seed, digits, outv.data(), ar, sc);
+    TTR_TRY(build_twosided(P, rho, skL, skR, seed, digits, outv.data(), ar, sc, orth, tol, &rk_dev));
+    if (trunc) {
+      int64_t* rkd = rk_dev;
+      int64_t* rkh = rk.data();
+      sc.add([rkd, rkh, N](cudaStream_t st) -> int {
+        if (rkd) TTR_CHECK_CUDA(cudaMemcpyAsync(rkh, rkd, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+        return int(TT_OK);
+      });
+    }
+    return int(TT_OK);
   };
   if (size_only) return plan_workspace_bytes(build, size_only);
-  TTR_TRY(plan_execute(build, workspace, ws_bytes, static_cast<cudaStream_t>(stream)));
-  for (int n = 0; n <= N; ++n) out_ranks[n] = P.ell[n];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dstat = 0;
+  TTR_TRY(plan_execute(build, workspace, ws_bytes, s, &dstat));
+  TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  TTR_TRY(status_code(dstat, orth ? "tt_round_twosided_orth" : "tt_round_twosided"));
+  for (int n = 0; n <= N; ++n) out_ranks[n] = trunc ? rk[n] : P.ell[n];
   return TT_OK;
 }
 
@@ -256,6 +307,25 @@ size_t tt_round_twosided_workspace(int32_t N, int32_t K, const int64_t* dims, co
   size_t b = 0;
   if (twosided_common(N, K, dims, ranks, nullptr, nullptr, ells, rhos, nullptr, nullptr, 0, precision, nullptr, nullptr,
                       nullptr, 0, nullptr, &b) != TT_OK)
+    return 0;
+  return b;
+}
+
+int tt_round_twosided_orth(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                           const double* const* cores, const double* coeffs, const int64_t* ells,
+                           const int64_t* rhos, const double* const* sketch_left,
+                           const double* const* sketch_right, uint64_t seed, double tol, int32_t precision,
+                           double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
+                           void* stream) {
+  return twosided_common(N, K, dims, ranks, cores, coeffs, ells, rhos, sketch_left, sketch_right, seed, precision,
+                         out, out_ranks, workspace, workspace_bytes, stream, nullptr, true, tol);
+}
+
+size_t tt_round_twosided_orth_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                                        const int64_t* ells, const int64_t* rhos, double tol, int32_t precision) {
+  size_t b = 0;
+  if (twosided_common(N, K, dims, ranks, nullptr, nullptr, ells, rhos, nullptr, nullptr, 0, precision, nullptr, nullptr,
+                      nullptr, 0, nullptr, &b, true, tol) != TT_OK)
     return 0;
   return b;
 }

@@ -567,6 +567,10 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
       tsqr_bind(bb.sh, bb.tw, bb.ti, &w);
       return tsqr_launch(bb.sh, w, A, a_rs, a_cs, Q, q_rs, q_cs, R, s, bb.status);
     });
+  } else {
+    // no fallback above the Householder limit: a failure goes to the run's status word
+    int* const* sp = &sc.dev_status;
+    sc.add([bb, sp](cudaStream_t s) -> int { return or_flag_launch(*sp, bb.status, DEV_QR_FAIL, s); });
   }
 }
 

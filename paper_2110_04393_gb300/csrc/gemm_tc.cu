@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int
     }
   } else {
     // a wait gave up: raise the flag and leave NaN in this CTA's outputs
-    if (tid == 0) atomicExch(err, 1);
+    if (tid == 0) atomicOr(err, DEV_TIMEOUT);
     if (row < d.M)
       for (int j = 0; j < 16; ++j)
         if (c0 + j < d.N)
@@ -719,5 +719,8 @@ extern "C" int tt_gemm_emulated_f64(int64_t M, int64_t N, int64_t K, double alph
     set_error("tt_gemm_emulated_f64: workspace needs " + std::to_string(need) + " bytes");
     return TT_EINVAL;
   }
-  return plan_execute(build, workspace, ws_bytes, s);
+  int dstat = 0;
+  TTR_TRY(plan_execute(build, workspace, ws_bytes, s, &dstat));
+  TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  return status_code(dstat, "tt_gemm_emulated_f64");
 }

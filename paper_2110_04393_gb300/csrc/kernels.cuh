@@ -131,8 +131,11 @@ struct Copy3 {
   int64_t begin;             // prefix of n0*n1*n2 over the batch (set by the planner)
 };
 int copy3_launch(const Copy3* d_descs, int n, int64_t total, cudaStream_t s);
-// dst[0] := 1 if src[0] != 0 (device flags)
-int or_flag_launch(int* dst, const int* src, cudaStream_t s);
+// Bits of a device status word (Schedule::dev_status).
+constexpr int DEV_TIMEOUT = 1;   // a bounded device wait gave up
+constexpr int DEV_QR_FAIL = 2;   // a thin QR produced no orthonormal basis
+// dst[0] |= bit if src[0] != 0 (device flags)
+int or_flag_launch(int* dst, const int* src, int bit, cudaStream_t s);
 int fill_launch(double* p, int64_t n, double v, cudaStream_t s);
 // Adjoint helpers: X = T^{-1} (upper triangular, k x k), A := tril(A) + tril(A, -1)^T, y += x.
 int triu_inverse_launch(const double* T, double* X, int k, cudaStream_t s);

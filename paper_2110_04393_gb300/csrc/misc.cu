@@ -174,14 +174,14 @@ int copy3_launch(const Copy3* d_descs, int n, int64_t total, cudaStream_t s) {
 
 namespace ttr {
 namespace {
-__global__ void or_flag_kernel(int* dst, const int* src) {
-  if (threadIdx.x == 0 && src[0]) dst[0] = 1;
+__global__ void or_flag_kernel(int* dst, const int* src, int bit) {
+  if (threadIdx.x == 0 && src[0]) dst[0] |= bit;
 }
 }  // namespace
-int or_flag_launch(int* dst, const int* src, cudaStream_t s) {
+int or_flag_launch(int* dst, const int* src, int bit, cudaStream_t s) {
   if (!dst || !src) return TT_OK;
   TTR_PREFER_SHARED(or_flag_kernel);
-  or_flag_kernel<<<1, 32, 0, s>>>(dst, src);
+  or_flag_kernel<<<1, 32, 0, s>>>(dst, src, bit);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
   return TT_OK;

@@ -3,10 +3,10 @@
 // allocate device memory.
 //
 // Who needs this: code that runs where a cudaMalloc (or a caching allocator's
-// growth) is not allowed or not safe -- inside a region being captured into a
-// CUDA graph by a framework that forbids allocations there, in real-time
-// loops with a fixed memory budget, or in hosts that hand out device memory only
-// for inputs and outputs. Such callers pass inputs and outputs as usual; the
+// growth) is not allowed or not safe -- real-time loops with a fixed memory
+// budget, plug-ins whose host application hands out device memory only for
+// inputs and outputs, or processes whose device memory is already fully
+// claimed by another allocator. Such callers pass inputs and outputs as usual; the
 // scratch lives in g_scratch below, a file-scope __device__ array of
 // TT_NOALLOC_SCRATCH_BYTES that every GPU which loads this library keeps until
 // the process exits.

@@ -29,7 +29,11 @@ struct Schedule {
     descs.insert(descs.end(), g.begin(), g.end());
     items.push_back([=](cudaStream_t s, const GemmDesc* d) { return gemm_launch(d + off, n, tiles, flops, s); });
   }
-  int* tc_err = nullptr;                        // device flag of the tensor-core GEMMs
+  // Device status word of one run (zeroed at its start): kernels OR in
+  // DEV_TIMEOUT when a bounded wait gives up and DEV_QR_FAIL when a thin QR
+  // could not produce an orthonormal basis; the entry points read it back and
+  // turn it into TT_ETIMEOUT / TT_ESINGULAR.
+  int* dev_status = nullptr;
   int64_t acc_need = 0, ex_need = 0;            // emulated-GEMM accumulators / exponent tags (largest group)
   long long* acc = nullptr;                     // zeroed once per call, left zero by every group
   int* ex = nullptr;                            // zeroed once per call, tagged by epoch
@@ -51,7 +55,7 @@ struct Schedule {
     const size_t off = descs.size();
     const int n = int(g.size());
     descs.insert(descs.end(), g.begin(), g.end());
-    int** errp = &tc_err;
+    int** errp = &dev_status;
     items.push_back([=](cudaStream_t st, const GemmDesc* d) {
       return gemm_tc_launch(d + off, n, tp, s, epoch, flops, *errp, st);
     });
@@ -115,7 +119,15 @@ inline GemmDesc gdesc(const double* A, int64_t a_rs, int64_t a_cs, const double*
 // order on both passes.
 using BuildFn = std::function<int(Arena&, Schedule&)>;
 int plan_workspace_bytes(const BuildFn& build, size_t* bytes);
-int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStream_t s);
+// host_status (may be null): receives the run's device status word by a
+// stream-ordered copy enqueued after the last item (valid once the stream has
+// been synchronized); see status_code.
+int plan_execute(const BuildFn& build, void* workspace, size_t ws_bytes, cudaStream_t s, int* host_status = nullptr);
+// Maps a device status word to a tt_status (TT_OK for 0), setting the error text.
+int status_code(int bits, const char* who);
+// Test hook: bits armed by tt_debug_inject_device_status, consumed (and
+// disarmed) by the next read-back of a device status word.
+int take_injected_status();
 
 // A schedule captured once into a CUDA graph and replayed (no host planning or
 // per-kernel launch cost on replay). The graph owns nothing: the plan keeps the

@@ -26,4 +26,12 @@ int validate_sum(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks
 // Clamps a rank vector like validate_sum does (r_0 = r_N = 1).
 std::vector<int64_t> clamp_rank_vector(const std::vector<int64_t>& I, const int64_t* r);
 
+// Right-to-left truncation (Section 3.2 with Algorithm 2's loop mirrored) of a
+// left-orthogonal TT held in out[0..N-1] at ranks ell (layout (l_{n-1}, I_n,
+// l_n)); tol <= 0: ranks capped by max_rank only; max_rank <= 0: no cap. The
+// decided ranks land in *rk_out (device, N+1) and every core is compacted to
+// them in place.
+int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int64_t>& I, const std::vector<int64_t>& ell,
+                    double tol, double* const* out, int64_t** rk_out, int64_t max_rank);
+
 }  // namespace ttr

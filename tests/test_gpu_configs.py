@@ -1,0 +1,193 @@
+"""Oracle parity of the CUDA path on the workload shapes that the benchmark
+configurations name (Section 4.1 and 4.2 shapes), each compared with the
+oracle on the same sketch:
+
+* the single perturbed TT of Section 4.1 (N = 10, I = 50, Y of rank 10 plus
+  1e-6 E of rank 30), Randomize-then-Orthogonalize with sketch rank 15, the
+  fixed-rank truncation to 10 and the deterministic rounding to rank 10;
+* the batched uneven sums (N = 20, I = 64, K ~ U[2, 30], R ~ U[4, 16],
+  l ~ U[8, 32]) rounded in one captured batch in mixed precision: every
+  problem's rounding error within 1.1x of the oracle's with the same sketch;
+* a scaled-down twin of the large sum (K = 6, N = 8, I = 64, rank 10,
+  redundant structure of rank 30 plus a 1e-8 tail, l = 40, rho = 60,
+  tolerance 1e-6): Randomize-then-Orthogonalize and the orthogonalized
+  Two-Sided rounding, both precisions.
+Bars: FP64 path <= 1e-10 relative Frobenius distance from the oracle's result
+(and equal ranks); mixed path error <= 1.1x the oracle's rounding error."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests._gpu import to_dev, to_host, const_ranks
+
+import paper_2110_04393_gb300 as tt
+
+pytestmark = pytest.mark.gpu
+FP64_TOL = 1e-10
+MIXED_RATIO = 1.1
+
+
+def rel_diff(A, B):
+    return O.diff_norm(A, B) / O.norm(B)
+
+
+# ------------------------------------------------------------------ Section 4.1
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_single_perturbed_tt_randorth_truncation_and_det(seed):
+    Ys = synth.workload_single(seed, N=10, I=50, R=10, R_pert=30, eps=1e-6)
+    dims = O.dims_of(Ys[0])
+    N = len(dims)
+    ell = O.clamp_ranks(dims, const_ranks(N, 15))
+    sk = O.gaussian_sketch_philox(seed, dims, ell)
+    Yd = [to_dev(Y) for Y in Ys]
+    Ysum = O.block_sum(Ys)
+    # Randomize-then-Orthogonalize to rank 15, then the fixed-rank truncation to 10
+    Xg15 = tt.tt_round_sum_rand(Yd, ell, sketch=to_dev(sk), tol=0.0)
+    Xo15 = O.round_sum_randorth(Ys, sk)
+    assert rel_diff(to_host(Xg15), Xo15) <= FP64_TOL
+    Xg10 = to_host(tt.tt_truncate_lorth(Xg15, max_rank=10))
+    Xo10 = O.truncate_left_orthogonal(Xo15, max_rank=10)
+    assert O.ranks_of(Xg10) == O.ranks_of(Xo10) == const_ranks(N, 10)
+    assert rel_diff(Xg10, Xo10) <= FP64_TOL
+    # the device-drawn sketch of the same seed gives the same rounding
+    Xs = to_host(tt.tt_round_sum_rand(Yd, ell, seed=seed, tol=0.0))
+    assert rel_diff(Xs, Xo15) <= FP64_TOL
+    # deterministic rounding to rank 10
+    Xd = to_host(tt.tt_round_det(Yd, max_rank=10))
+    Xdo = O.tt_round_det(Ysum, 0.0, max_rank=10)
+    assert O.ranks_of(Xd) == O.ranks_of(Xdo)
+    assert rel_diff(Xd, Xdo) <= FP64_TOL
+    # Section 4.1: both errors at the perturbation level, deterministic the smaller
+    e_rand = O.diff_norm(Xg10, Ysum) / O.norm(Ysum)
+    e_det = O.diff_norm(Xd, Ysum) / O.norm(Ysum)
+    assert e_det <= e_rand * (1 + 1e-6) and e_rand < 1e-4
+
+
+def test_truncate_lorth_tolerance_matches_oracle():
+    Ys = synth.workload_single(4, N=8, I=20, R=6, R_pert=10, eps=1e-5)
+    dims = O.dims_of(Ys[0])
+    ell = O.clamp_ranks(dims, const_ranks(8, 12))
+    sk = O.gaussian_sketch_philox(4, dims, ell)
+    Xo = O.round_sum_randorth(Ys, sk)
+    for tol, mr in ((1e-3, 0), (1e-8, 0), (1e-8, 8)):
+        Xg = to_host(tt.tt_truncate_lorth(to_dev(Xo), tol=tol, max_rank=mr))
+        Xt = O.truncate_left_orthogonal(Xo, tol, max_rank=mr if mr > 0 else None)
+        assert O.ranks_of(Xg) == O.ranks_of(Xt)
+        assert rel_diff(Xg, Xt) <= FP64_TOL
+        if mr == 0:
+            assert O.diff_norm(Xg, Xo) <= tol * O.norm(Xo) * (1 + 1e-10)
+
+
+# --------------------------------------------------------- batched uneven sums
+
+def _sum_error(X, Ys):
+    """||X - sum_j Y_j|| / ||sum_j Y_j|| from inner products (accurate for the
+    O(1e-3) and larger errors of fixed-rank rounding of generic sums)."""
+    K = len(Ys)
+    G = np.array([[O.inner(Ys[a], Ys[b]) for b in range(K)] for a in range(K)])
+    yy = float(G.sum())
+    xy = sum(O.inner(X, Y) for Y in Ys)
+    xx = O.inner(X, X)
+    return np.sqrt(max(yy - 2 * xy + xx, 0.0) / yy)
+
+
+def test_batched_uneven_sums_mixed_vs_oracle():
+    from bench import batched_problems
+    probs = batched_problems(1)[:16]
+    batch_np, batch_dev = [], []
+    for b, pr in enumerate(probs):
+        Ys = [synth.gaussian_tt(synth.rng_for(130 + b, j), pr["dims"], R) for j, R in enumerate(pr["summand_ranks"])]
+        batch_np.append(Ys)
+        batch_dev.append([to_dev(Y) for Y in Ys])
+    seeds = [17 * b + 3 for b in range(len(probs))]
+    plan = tt.BatchRoundingPlan(probs, precision="mixed", width=4)
+    try:
+        out = plan(batch_dev, seeds=seeds)
+        plan.status()
+        Xg = [to_host(X) for X in out]
+    finally:
+        plan.close()
+    for b, pr in enumerate(probs):
+        ell = tt.clamp_ranks(pr["dims"], pr["ells"])
+        sk = O.gaussian_sketch_philox(seeds[b], pr["dims"], ell)
+        Xo = O.round_sum_randorth(batch_np[b], sk)
+        assert O.ranks_of(Xg[b]) == O.ranks_of(Xo) == ell
+        e_g, e_o = _sum_error(Xg[b], batch_np[b]), _sum_error(Xo, batch_np[b])
+        assert e_g <= MIXED_RATIO * e_o, (b, e_g, e_o)
+
+
+# ------------------------------------------------------- large-sum twin (cfg 5)
+
+def _twin():
+    Ys = synth.workload_sum_structured(5, K=6, N=8, I=64, R=10, m=3, p=1, delta=1e-8)
+    dims = O.dims_of(Ys[0])
+    N = len(dims)
+    ell = O.clamp_ranks(dims, const_ranks(N, 40))
+    rho = O.clamp_ranks(dims, const_ranks(N, 60))
+    return Ys, dims, ell, rho
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_twin_randorth_vs_oracle(precision):
+    Ys, dims, ell, rho = _twin()
+    tol = 1e-6
+    sk = O.gaussian_sketch_philox(11, dims, ell)
+    Ysum = O.block_sum(Ys)
+    Xo = O.truncate_left_orthogonal(O.round_sum_randorth(Ys, sk), tol)
+    Xg = to_host(tt.tt_round_sum_rand([to_dev(Y) for Y in Ys], ell, sketch=to_dev(sk), tol=tol, precision=precision))
+    assert O.ranks_of(Xg) == O.ranks_of(Xo)
+    assert max(O.ranks_of(Xg)) <= 30
+    e_o = O.diff_norm(Xo, Ysum) / O.norm(Ysum)
+    e_g = O.diff_norm(Xg, Ysum) / O.norm(Ysum)
+    assert e_o <= tol
+    if precision == "fp64":
+        assert rel_diff(Xg, Xo) <= FP64_TOL
+    else:
+        assert e_g <= MIXED_RATIO * e_o, (e_g, e_o)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_twin_twosided_orth_vs_oracle(precision):
+    Ys, dims, ell, rho = _twin()
+    tol = 1e-6
+    Lsk = O.gaussian_sketch_philox(12, dims, ell)
+    Rsk = O.gaussian_sketch_philox(13, dims, rho)
+    Ysum = O.block_sum(Ys)
+    Xo = O.round_sum_twosided_orth(Ys, Lsk, Rsk, eps0=tol)
+    Xg = to_host(tt.tt_round_twosided_orth([to_dev(Y) for Y in Ys], ell, rhos=rho, sketch_left=to_dev(Lsk),
+                                           sketch_right=to_dev(Rsk), tol=tol, precision=precision))
+    assert O.ranks_of(Xg) == O.ranks_of(Xo)
+    assert max(O.ranks_of(Xg)) <= 30
+    for n in range(len(Xg) - 1):
+        Vn = O.V(Xg[n])
+        assert np.abs(Vn.T @ Vn - np.eye(Vn.shape[1])).max() < 1e-12
+    e_o = O.diff_norm(Xo, Ysum) / O.norm(Ysum)
+    e_g = O.diff_norm(Xg, Ysum) / O.norm(Ysum)
+    assert e_o <= 2 * tol
+    if precision == "fp64":
+        assert rel_diff(Xg, Xo) <= FP64_TOL
+    else:
+        assert e_g <= MIXED_RATIO * e_o, (e_g, e_o)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_twosided_orth_fixed_rank_is_twosided(precision):
+    """Without a tolerance the restructure returns the Algorithm 6 tensor."""
+    dims = [9, 10, 12, 10, 9]
+    Ys = [synth.gaussian_tt(synth.rng_for(140, j), dims, const_ranks(5, r)) for j, r in enumerate([3, 4, 2])]
+    ell = [1, 5, 6, 6, 5, 1]
+    rho = O.clamp_ranks(dims, [int(np.ceil(1.5 * x)) for x in ell])
+    Lsk = synth.gaussian_tt(synth.rng_for(141), dims, ell)
+    Rsk = synth.gaussian_tt(synth.rng_for(142), dims, rho)
+    Yd = [to_dev(Y) for Y in Ys]
+    Xa = to_host(tt.tt_round_twosided(Yd, ell, rhos=rho, sketch_left=to_dev(Lsk), sketch_right=to_dev(Rsk),
+                                      precision=precision))
+    Xb = to_host(tt.tt_round_twosided_orth(Yd, ell, rhos=rho, sketch_left=to_dev(Lsk), sketch_right=to_dev(Rsk),
+                                           precision=precision))
+    assert O.ranks_of(Xb) == ell
+    assert rel_diff(Xb, Xa) <= (FP64_TOL if precision == "fp64" else 1e-6)
+    Xo = O.round_sum_twosided_orth(Ys, Lsk, Rsk)
+    if precision == "fp64":
+        assert rel_diff(Xb, Xo) <= FP64_TOL

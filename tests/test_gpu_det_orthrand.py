@@ -87,9 +87,10 @@ def test_rand_vs_det_same_accuracy_order_on_low_rank_sum():
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", ["single", "sum"])
 def test_twosided_parity(case, precision):
-    """Algorithm 6 in block-sum form == Algorithm 6 on the formed sum (oracle);
-    the mixed form's products are accurate to ~1e-8 relative (tt_mixed_digits in
-    fixed-rank mode), amplified by at most the conditioning of the bond SVDs."""
+    """Algorithm 6 in block-sum form == Algorithm 6 on the formed sum (oracle)
+    in FP64; the mixed form (products accurate to ~1e-8 relative,
+    tt_mixed_digits in fixed-rank mode) keeps the rounding error within 1.1x of
+    the oracle's."""
     if case == "single":
         dims = [11, 13, 12, 10]
         Ys = [synth.gaussian_tt(synth.rng_for(100), dims, [1, 7, 9, 6, 1])]
@@ -106,7 +107,14 @@ def test_twosided_parity(case, precision):
     Xg = to_host(tt.tt_round_twosided([to_dev(Y) for Y in Ys], ell, rhos=rho, sketch_left=to_dev(Lsk),
                                       sketch_right=to_dev(Rsk), coeffs=coeffs, precision=precision))
     Xo = O.round_sum_twosided(Ys, Lsk, Rsk, coeffs)
-    assert rel_diff(Xg, Xo) <= (FP64_TOL if precision == "fp64" else 1e-5), rel_diff(Xg, Xo)
+    if precision == "fp64":
+        assert rel_diff(Xg, Xo) <= FP64_TOL, rel_diff(Xg, Xo)
+    else:
+        # the benchmark spec's mixed bar: the rounding error within 1.1x of the oracle's
+        Ysum = O.block_sum(Ys, coeffs)
+        e_g = O.diff_norm(Xg, Ysum) / O.norm(Ysum)
+        e_o = O.diff_norm(Xo, Ysum) / O.norm(Ysum)
+        assert e_g <= 1.1 * e_o, (e_g, e_o)
 
 
 def test_twosided_mixed_exact_recovery_and_bad_precision():

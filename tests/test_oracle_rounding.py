@@ -275,6 +275,46 @@ def test_twosided_equals_bondwise_nystrom_and_recovers():
     assert O.diff_norm(X2, Y2) <= 1e-10 * O.norm(Y2)
 
 
+def test_twosided_orth_same_tensor_left_orthogonal_and_truncation_bound():
+    """The orthogonalizing restructure of Algorithm 6 (Section 3.3, reading in
+    round_sum_twosided_orth): the same full tensor as Algorithm 6 built by brute
+    force from the bond-wise Nystrom projectors, left-orthogonal cores, and with
+    a tolerance the Section 3.2 bound ||X_out - X|| <= tol ||X||."""
+    dims = [3, 4, 3, 4]
+    Ys = [_tt(46, dims, [1, 2, 3, 2, 1]), _tt(47, dims, [1, 3, 2, 2, 1])]
+    coeffs = [0.7, -1.3]
+    ell = [1, 3, 4, 3, 1]
+    rho = [1, 4, 5, 4, 1]
+    L, Rk = _tt(48, dims, ell), _tt(49, dims, rho)
+    Ysum = O.block_sum(Ys, coeffs)
+    cores = [c.copy() for c in Ysum]
+    for n in range(1, 4):
+        WL = left_part_bruteforce(L, n).T @ left_part_bruteforce(Ysum, n)
+        WR = right_part_bruteforce(Ysum, n) @ right_part_bruteforce(Rk, n).T
+        P = WR @ np.linalg.pinv(WL @ WR) @ WL
+        cores[n - 1] = np.einsum("aib,bc->aic", cores[n - 1], P)
+    ref = full_from_cores_bruteforce(cores)
+    X = O.round_sum_twosided_orth(Ys, L, Rk, coeffs)
+    assert rel(O.full(X), ref) < 1e-9
+    for n in range(3):
+        Vn = O.V(X[n])
+        assert np.abs(Vn.T @ Vn - np.eye(Vn.shape[1])).max() < 1e-13
+    for tol in (2e-1, 9e-1):
+        Xt = O.round_sum_twosided_orth(Ys, L, Rk, coeffs, eps0=tol)
+        assert O.diff_norm(Xt, X) <= tol * O.norm(X) * (1 + 1e-12)
+    assert sum(O.ranks_of(Xt)) < sum(O.ranks_of(X))
+
+
+def test_twosided_orth_recovers_low_rank_sum():
+    """X + X of rank r <= l <= rho: the restructured Two-Sided result with a
+    tolerance is 2X at rank r (generalized Nystrom identity, Section 3.3)."""
+    dims = [5] * 5
+    Y = _tt(51, dims, _const(5, 3))
+    X = O.round_sum_twosided_orth([Y, Y], _tt(52, dims, _const(5, 4)), _tt(53, dims, _const(5, 6)), eps0=1e-10)
+    assert O.ranks_of(X) == _const(5, 3)
+    assert O.diff_norm(X, synth.scale_tt(Y, 2.0)) <= 1e-10 * O.norm(Y)
+
+
 # ------------------------------------------------- Section 4.1 / Appendix C
 
 def test_accuracy_ordering_perturbed_tt():
