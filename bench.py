@@ -205,7 +205,9 @@ def oracle_leg(Ys, gpu_results, det_result, reps=2):
                      "ratio_to_oracle_error": e / e_o if e_o > 0 else None,
                      "ranks_equal_oracle": oracle.ranks_of(X) == oracle.ranks_of(Xo)}
     if det_result is not None:
-        err["det_fp64"] = {"rounding_error": rounding_error(det_result),
+        e_d = rounding_error(det_result)
+        err["det_fp64"] = {"rounding_error": e_d, "resolved": e_d > 1e-7,
+                           "resolution": "inner-product errors below about 1e-7 read as 0",
                            "note": "deterministic TT-SVD rounding to the same tolerance (the sum is generically "
                                    "of full rank 200, so its error is at the tolerance while the rank-30 "
                                    "randomized rounding's is O(1))"}

@@ -449,6 +449,23 @@ int tt_selftest_tcgen05_bf16(int32_t M, int32_t N, int32_t K, const void* A, con
 void tt_debug_inject_device_status(int32_t bits);
 
 /*
+ * tt_set_qr_mode -- how the thin QRs of later calls (and of plans created
+ * later) run (no counterpart in the paper, which uses a Householder QR; every
+ * mode returns an orthonormal Q with A = Q R):
+ *   0  auto (default): shifted Cholesky QR (Fukaya et al. 2020) as one
+ *      cooperative launch that keeps the row blocks in shared memory, where the
+ *      blocks fit and the grid is co-resident; else as one launch per pass;
+ *   1  shifted Cholesky QR, one launch per pass;
+ *   2  the Householder TSQR fallback for every QR with k <= 96 (the path that
+ *      otherwise runs only when the Cholesky chain breaks down), for testing it.
+ * tt_tsqr_fallback_runs returns how many Householder fallback QRs ran on the
+ * current device since the library was loaded (a device counter).
+ * Errors: TT_EINVAL for an unknown mode; TT_ECUDA.
+ */
+int tt_set_qr_mode(int32_t mode);
+int tt_tsqr_fallback_runs(int64_t* runs);
+
+/*
  * Measurement hooks (no counterpart in the paper; used by the benchmark).
  * tt_prof_enable(1) makes the library record a CUDA event pair on the caller's
  * stream around every grouped-GEMM launch (all contraction steps) and add up the

@@ -54,6 +54,8 @@ SIGNATURES = {
     "tt_sum_plan_status": (c_i32, [c_vp, c_vp]),
     "tt_batch_plan_status": (c_i32, [c_vp, c_vp]),
     "tt_debug_inject_device_status": (None, [c_i32]),
+    "tt_set_qr_mode": (c_i32, [c_i32]),
+    "tt_tsqr_fallback_runs": (c_i32, [P_i64]),
     "tt_sum_plan_host_layout": (c_i32, [c_vp, P_i64, P_i64, P_i64, P_i64]),
     "tt_sum_plan_run_host": (c_i32, [c_vp, c_vp, P_dbl, c_u64, c_vp, P_i64, c_vp]),
     "tt_batch_plan_create": (c_i32, [c_i32, c_vp, c_i32, c_i32, P_vp, c_vp]),

@@ -612,6 +612,23 @@ def debug_inject_device_status(bits):
     nat.lib().tt_debug_inject_device_status(int(bits))
 
 
+QR_AUTO, QR_CHAIN, QR_FORCE_FALLBACK = 0, 1, 2
+
+
+def set_qr_mode(mode):
+    """How later calls run their thin QRs: QR_AUTO (one cooperative launch
+    where it fits), QR_CHAIN (one launch per Cholesky-QR pass) or
+    QR_FORCE_FALLBACK (Householder TSQR for every QR with k <= 96)."""
+    _check(nat.lib().tt_set_qr_mode(int(mode)))
+
+
+def tsqr_fallback_runs():
+    """Householder fallback QRs run on the current device since the library loaded."""
+    v = ctypes.c_int64()
+    _check(nat.lib().tt_tsqr_fallback_runs(ctypes.byref(v)))
+    return int(v.value)
+
+
 def prof_enable(on=True):
     _check(nat.lib().tt_prof_enable(1 if on else 0))
 

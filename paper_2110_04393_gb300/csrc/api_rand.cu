@@ -434,20 +434,25 @@ int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int64_t>& 
     const int rcap = int(max_rank > 0 ? std::min<int64_t>(max_rank, k) : k);
     double* Xn = out[n - 1];
     double* Xp = out[n - 2];
-    qr_plan(sc, qr_view(pool, m, int(k)), Xn, 1, m, b.Qt, k, 1, b.Rb, true);
+    const int64_t mp = ell[n - 2] * I[n - 2];
+    // With a tolerance the QR may certify that nothing can be cut at this bond
+    // and apply the bond's update itself; the general steps below then skip.
+    const QrBufs qb = qr_view(pool, m, int(k));
+    QrCert cert{epsp, rcap, b.rk ? b.rk + (n - 1) : nullptr, Xn, Xp, mp};
+    qr_plan(sc, qb, Xn, 1, m, b.Qt, k, 1, b.Rb, true, epsp ? &cert : nullptr);
+    const int* skip = epsp ? qr_cert_flag(qb) : nullptr;
     sc.add([=](cudaStream_t s) -> int {
-      return svd_trunc_launch(int(k), b.Rb, epsp, rcap, b.G1, b.G2, b.sig, b.rk + (n - 1), s, sbig);
+      return svd_trunc_launch(int(k), b.Rb, epsp, rcap, b.G1, b.G2, b.sig, b.rk + (n - 1), s, sbig, skip);
     });
     // new H(X_n) = (Q G1)^T : column-major m x k view of core n
-    sc.gemm({gdesc(b.Qt, k, 1, b.G1, k, 1, Xn, 1, m, m, k, k)});
+    GemmDesc g1 = gdesc(b.Qt, k, 1, b.G1, k, 1, Xn, 1, m, m, k, k);
+    g1.skip = skip;
+    sc.gemm({g1});
     // V(X_{n-1}) := V(X_{n-1}) G2
-    const int64_t mp = ell[n - 2] * I[n - 2];
-    sc.gemm({gdesc(Xp, k, 1, b.G2, k, 1, b.tmp, k, 1, mp, k, k)});
-    sc.add([=](cudaStream_t s) -> int {
-      if (!Xp) return int(TT_OK);
-      TTR_CHECK_CUDA(cudaMemcpyAsync(Xp, b.tmp, sizeof(double) * mp * k, cudaMemcpyDeviceToDevice, s));
-      return int(TT_OK);
-    });
+    GemmDesc g2 = gdesc(Xp, k, 1, b.G2, k, 1, b.tmp, k, 1, mp, k, k);
+    g2.skip = skip;
+    sc.gemm({g2});
+    sc.add([=](cudaStream_t s) -> int { return copy_if_launch(Xp, b.tmp, mp * k, skip, s); });
   }
   // compact every core to its decided ranks
   for (int n = 1; n <= N; ++n) {
@@ -619,6 +624,25 @@ int tt_sketch_gaussian(int32_t N, const int64_t* dims, const int64_t* ells, uint
 int tt_mixed_digits(double tol, int32_t N) { return ttr::mixed_digits(tol, N); }
 
 void tt_debug_inject_device_status(int32_t bits) { g_inject.store(int(bits)); }
+
+int tt_set_qr_mode(int32_t mode) {
+  if (set_qr_mode(mode) != TT_OK) {
+    set_error("tt_set_qr_mode: mode must be 0 (auto), 1 (multi-launch chain) or 2 (Householder fallback)");
+    return TT_EINVAL;
+  }
+  return TT_OK;
+}
+
+int tt_tsqr_fallback_runs(int64_t* runs) {
+  if (!runs) {
+    set_error("tt_tsqr_fallback_runs: null output");
+    return TT_EINVAL;
+  }
+  long long v = 0;
+  TTR_TRY(tsqr_fallback_runs(&v));
+  *runs = int64_t(v);
+  return TT_OK;
+}
 
 __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, const int64_t* dims,
                                                          const int64_t* ranks,

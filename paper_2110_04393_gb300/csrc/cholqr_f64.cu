@@ -29,6 +29,7 @@
 // flag and otherwise exits at once) recomputes Q and R; above, the flag is
 // reported to the caller. No host synchronization is involved.
 #include <algorithm>
+#include <atomic>
 
 #include "plan.cuh"
 #include "prof.cuh"
@@ -154,6 +155,158 @@ __device__ __forceinline__ void tri_ij(int p, int k, int* i, int* j) {
   while (p >= k - r) { p -= k - r; ++r; }
   *i = r;
   *j = r + p;
+}
+
+// Decision of one pass of the chain on the reduced Gram matrix G (k x k,
+// copy in G0, X is scratch; all three in the calling CTA's shared memory or
+// in global scratch), made by one whole CTA:
+//   * final pass: check G = I to 64 k u (failure raises status[0]) and end;
+//   * a later Gram I + E with ||E||_F <= 1e-8 (only Q wanted, or R may come out
+//     full): Rinv := I - E/2 and the next pass ends the chain;
+//   * else the Cholesky factorization with inverse (retried once with a shift),
+//     Rinv := L^{-T} and R accumulated when asked for; a failure raises
+//     status[0] and ends the chain.
+// Returns after the CTA's last write (callers synchronize before publishing).
+__device__ void cqr_decide(double* G, double* X, double* G0, int k, int64_t m, int pass, bool final_pass,
+                           int unshifted_run, double* Rinv, double* Racc, int fo_r, int* status) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (final_pass) {
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    const double tol = 64.0 * k * 0x1p-53;
+    for (int idx = tid; idx < k * k; idx += nt) {
+      const double dv = G[idx] - (((idx / k) == (idx % k)) ? 1.0 : 0.0);
+      if (!(fabs(dv) <= tol)) bad = 1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (bad) atomicExch(status, 1);
+      atomicExch(status + 2, 1);
+    }
+    return;
+  }
+  if (pass > 0 && (Racc == nullptr || fo_r)) {
+    // The block is already orthonormal to ||E||_F <= 1e-8, E = G - I: the last
+    // pass multiplies by I - E/2 instead of factoring again. When R is wanted
+    // (and allowed to lose its triangular form) it becomes (I + E/2) R: the
+    // correction E R / 2 is ~1e-8 of R or less, so an fp32 product of it keeps R
+    // accurate to float64 rounding.
+    __shared__ double s_red[CQ_THREADS / 32];
+    double e2 = 0.0;
+    for (int idx = tid; idx < k * k; idx += nt) {
+      const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
+      e2 = fma(dv, dv, e2);
+    }
+    for (int off = 16; off; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+    if ((tid & 31) == 0) s_red[tid >> 5] = e2;
+    __syncthreads();
+    __shared__ double s_e2;
+    if (tid == 0) {
+      double t0 = 0.0;
+      for (int w = 0; w < (nt >> 5); ++w) t0 += s_red[w];
+      s_e2 = t0;
+    }
+    __syncthreads();
+    const double tot = s_e2;
+    if (tot <= 1e-16) {                           // ||E||_F <= 1e-8 (false for NaN)
+      for (int idx = tid; idx < k * k; idx += nt) {
+        const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
+        Rinv[idx] = ((idx % (k + 1) == 0) ? 1.0 : 0.0) - 0.5 * dv;
+      }
+      if (Racc) {
+        // X <- E / 2, G0 <- R (the previous factor), then R += (E / 2) R with R
+        // scaled by a power of two near 1 / max|R| for the fp32 product (no
+        // underflow or overflow in fp32 whatever the scale of A)
+        __shared__ int s_emax;
+        if (tid == 0) s_emax = -2000;
+        __syncthreads();
+        int em = -2000;
+        for (int idx = tid; idx < k * k; idx += nt) {
+          X[idx] = 0.5 * (G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0));
+          const double r = Racc[idx];
+          G0[idx] = r;
+          const int e = int((uint64_t(__double_as_longlong(r)) >> 52) & 0x7FF);
+          if (e != 0) em = max(em, e - 1023);
+        }
+        atomicMax(&s_emax, em);
+        __syncthreads();
+        const int sh = s_emax == -2000 ? 0 : -s_emax;                 // R 2^sh has entries below 2
+        const double up = __longlong_as_double((long long)(uint64_t(1023 - sh) << 52));   // 2^{-sh}
+        const double down = __longlong_as_double((long long)(uint64_t(1023 + sh) << 52)); // 2^{sh}
+        // fp32 copies first (conversions run on the FP64 pipe: once per entry),
+        // in the memory of G, which is no longer needed (2 k^2 floats = k^2 doubles)
+        float* Xf = reinterpret_cast<float*>(G);                 // E / 2
+        float* Rf = Xf + k * k;                                  // R 2^sh
+        __syncthreads();
+        for (int idx = tid; idx < k * k; idx += nt) {
+          Xf[idx] = float(X[idx]);
+          Rf[idx] = float(G0[idx] * down);
+        }
+        __syncthreads();
+        for (int idx = tid; idx < k * k; idx += nt) {
+          const int r = idx / k, c = idx % k;
+          float corr = 0.0f;
+          for (int l = 0; l < k; ++l) corr = fmaf(Xf[r * k + l], Rf[l * k + c], corr);
+          Racc[idx] = fma(double(corr), up, G0[idx]);
+        }
+      }
+      if (tid == 0) {
+        status[4] = (tot <= 1e-20) ? 2 : 1;       // 2: ||E||_F <= 1e-10, an fp32 product of E suffices
+        status[1] = 2;
+        status[3] += 1;
+      }
+      return;
+    }
+  }
+  bool ok = chol_with_inverse(G, X, k);
+  bool shifted = false;
+  if (!ok) {
+    __shared__ double s_shift;
+    if (tid == 0) {
+      double tr = 0.0;
+      for (int i = 0; i < k; ++i) tr += G0[i * k + i];
+      s_shift = 11.0 * (double(m) * k + double(k) * (k + 1)) * 0x1p-53 * tr;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < k * k; idx += nt) G[idx] = G0[idx] + (((idx / k) == (idx % k)) ? s_shift : 0.0);
+    __syncthreads();
+    ok = chol_with_inverse(G, X, k);
+    shifted = true;
+  }
+  if (!ok) {                                    // not even the shifted Gram is positive definite
+    if (tid == 0) {
+      atomicExch(status, 1);
+      atomicExch(status + 2, 1);
+    }
+    return;
+  }
+  if (tid == 0) {
+    status[1] = shifted ? 0 : unshifted_run + 1;
+    status[3] += 1;
+  }
+  // Rinv = L^{-T} (upper)
+  for (int idx = tid; idx < k * k; idx += nt) {
+    const int r = idx / k, c = idx % k;
+    Rinv[idx] = (c >= r) ? X[c * k + r] : 0.0;
+  }
+  if (Racc) {
+    if (pass > 0) {
+      for (int idx = tid; idx < k * k; idx += nt) G0[idx] = Racc[idx];
+      __syncthreads();
+      for (int idx = tid; idx < k * k; idx += nt) {
+        const int r = idx / k, c = idx % k;
+        double s = 0.0;
+        for (int j = r; j <= c; ++j) s = fma(G[j * k + r], G0[j * k + c], s);
+        Racc[idx] = (c >= r) ? s : 0.0;
+      }
+    } else {
+      for (int idx = tid; idx < k * k; idx += nt) {
+        const int r = idx / k, c = idx % k;
+        Racc[idx] = (c >= r) ? G[c * k + r] : 0.0;
+      }
+    }
+  }
 }
 
 __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
@@ -298,143 +451,376 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
     G0[j * k + i] = acc;
   }
   __syncthreads();
-  if (final_pass) {
-    __shared__ int bad;
-    if (tid == 0) bad = 0;
-    __syncthreads();
-    const double tol = 64.0 * k * 0x1p-53;
-    for (int idx = tid; idx < k * k; idx += nt) {
-      const double dv = G[idx] - (((idx / k) == (idx % k)) ? 1.0 : 0.0);
-      if (!(fabs(dv) <= tol)) bad = 1;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      if (bad) atomicExch(a.status, 1);
-      atomicExch(a.status + 2, 1);
-    }
-    return;
+  cqr_decide(G, X, G0, k, a.m, a.pass, final_pass, unshifted_run, a.Rinv, a.Racc, a.fo_r, a.status);
+}
+
+// ---------------------------------------------------------------------------
+// The whole chain in one cooperative launch (every CTA of the grid is resident,
+// so the CTAs of a QR can wait for the pass decisions of their last CTA). Each
+// CTA keeps its row block in shared memory across the passes: A is read once
+// and Q written once; the k x k decision runs on the job's last-arriving CTA
+// while the others wait on a released pass counter (bounded: after
+// kCoopWaitNs the waiting CTA raises DEV_TIMEOUT in the run's status word and
+// returns). The final pass needs no wait: its CTAs write Q and leave.
+struct CoopJob {
+  int64_t m;
+  int k, b, P, fo_r;
+  const double* A;
+  int64_t a_rs, a_cs;
+  double* Q;
+  int64_t q_rs, q_cs;
+  double* Gpart;            // (P + groups) x k (k + 1) / 2
+  double* Rinv;             // k x k
+  double* Racc;             // k x k accumulated R, or null
+  int* status;              // [0..4] chain state as CqrPass, [5] final arrival,
+                            // [6, 6 + groups) group arrivals, [6 + groups] released passes
+  int* dev_status;          // the run's status word
+  // Truncation certificate (eps null: off). When the chain ends by the
+  // first-order pass right after its first factorization, the decider bounds
+  // sigma_min(A) >= (1 - ||E||_F) / ||R0^{-1}||_F (A R0^{-1} has Gram I + E);
+  // if that exceeds 2 eps and rcap >= k, no singular value can be cut, so the
+  // bond's truncation step reduces to: Q^T as the new core (written over A,
+  // which every CTA has read by then) and V(X_{n-1}) := V(X_{n-1}) R^T (rows
+  // bp per CTA, in place); *cert := 1 and *rank_out := k tell the general
+  // path to skip.
+  const double* eps;
+  int rcap, bp;
+  int* cert;
+  int64_t* rank_out;
+  double* Aw;               // A itself, written with Q when certified
+  double* Xp;               // mp x k row-major
+  int64_t mp;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red[w];
+  return t;
+}
+
+constexpr unsigned long long kCoopWaitNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Shared memory (doubles) of the cooperative kernel: the row block plus a
+// union of [Rinv | product block] and the decision's [G | X | G0].
+__host__ __device__ inline int64_t coop_smem_doubles(int b, int k) {
+  const int64_t bk = int64_t(b) * k, kk = int64_t(k) * k;
+  return bk + (3 * kk > kk + bk ? 3 * kk : kk + bk);
+}
+
+__global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
+  extern __shared__ double sm[];
+  __shared__ int s_flag;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int k = a.k, b = a.b, lb = blockIdx.x;
+  const int npair = k * (k + 1) / 2;
+  const int ngrp = (a.P + CQ_GROUP - 1) / CQ_GROUP;
+  int* st = a.status;
+  int* released = st + 6 + ngrp;
+  double* T = sm;                       // b x k row block, kept across passes
+  double* U = sm + int64_t(b) * k;      // union
+  const int64_t r0 = int64_t(lb) * b;
+  for (int r = warp; r < b; r += nw) {
+    const int64_t gr = r0 + r;
+    for (int c = lane; c < k; c += 32) T[r * k + c] = (gr < a.m) ? a.A[gr * a.a_rs + c * a.a_cs] : 0.0;
   }
-  if (a.pass > 0 && (a.Racc == nullptr || a.fo_r)) {
-    // The block is already orthonormal to ||E||_F <= 1e-8, E = G - I: the last
-    // pass multiplies by I - E/2 instead of factoring again. When R is wanted
-    // (and allowed to lose its triangular form) it becomes (I + E/2) R: the
-    // correction E R / 2 is ~1e-8 of R or less, so an fp32 product of it keeps R
-    // accurate to float64 rounding.
-    __shared__ double s_red[CQ_THREADS / 32];
-    double e2 = 0.0;
-    for (int idx = tid; idx < k * k; idx += nt) {
-      const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
-      e2 = fma(dv, dv, e2);
-    }
-    for (int off = 16; off; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
-    if ((tid & 31) == 0) s_red[tid >> 5] = e2;
-    __syncthreads();
-    __shared__ double s_e2;
-    if (tid == 0) {
-      double t0 = 0.0;
-      for (int w = 0; w < (nt >> 5); ++w) t0 += s_red[w];
-      s_e2 = t0;
-    }
-    __syncthreads();
-    const double tot = s_e2;
-    if (tot <= 1e-16) {                           // ||E||_F <= 1e-8 (false for NaN)
-      for (int idx = tid; idx < k * k; idx += nt) {
-        const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
-        a.Rinv[idx] = ((idx % (k + 1) == 0) ? 1.0 : 0.0) - 0.5 * dv;
-      }
-      if (a.Racc) {
-        // X <- E / 2, G0 <- R (the previous factor), then R += (E / 2) R with R
-        // scaled by a power of two near 1 / max|R| for the fp32 product (no
-        // underflow or overflow in fp32 whatever the scale of A)
-        __shared__ int s_emax;
-        if (tid == 0) s_emax = -2000;
+  __syncthreads();
+  for (int pass = 0; pass < CQ_MAX_PASSES; ++pass) {
+    bool final_pass = false;
+    int unshifted_run = 0;
+    if (pass > 0) {
+      unshifted_run = __ldcg(st + 1);
+      const int fo_kind = __ldcg(st + 4);
+      const bool first_order = fo_kind != 0;
+      final_pass = (unshifted_run >= 2 || pass == CQ_MAX_PASSES - 1);
+      double* Rs = U;
+      if (fo_kind == 2) {
+        // T := T (I - E/2) = T - T (E/2) with ||E||_F <= 1e-10: the correction
+        // is at most 1e-10 of T, so fp32 products of it (relative error
+        // k 2^-24) keep T accurate to float64 rounding; one fp64 subtraction
+        // per entry, on the FP32 pipe otherwise.
+        float* Cf = reinterpret_cast<float*>(U);                 // E/2, k x k
+        float* Tf = Cf + k * k;                                  // T, b x k
+        for (int i = tid; i < k * k; i += nt)
+          Cf[i] = float(((i % (k + 1) == 0) ? 1.0 : 0.0) - __ldcg(a.Rinv + i));
+        for (int i = tid; i < b * k; i += nt) Tf[i] = float(T[i]);
         __syncthreads();
-        int em = -2000;
-        for (int idx = tid; idx < k * k; idx += nt) {
-          X[idx] = 0.5 * (G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0));
-          const double r = a.Racc[idx];
-          G0[idx] = r;
-          const int e = int((uint64_t(__double_as_longlong(r)) >> 52) & 0x7FF);
-          if (e != 0) em = max(em, e - 1023);
-        }
-        atomicMax(&s_emax, em);
-        __syncthreads();
-        const int sh = s_emax == -2000 ? 0 : -s_emax;                 // R 2^sh has entries below 2
-        const double up = __longlong_as_double((long long)(uint64_t(1023 - sh) << 52));   // 2^{-sh}
-        const double down = __longlong_as_double((long long)(uint64_t(1023 + sh) << 52)); // 2^{sh}
-        // fp32 copies first (conversions run on the FP64 pipe: once per entry),
-        // in the memory of G, which is no longer needed (2 k^2 floats = k^2 doubles)
-        float* Xf = reinterpret_cast<float*>(G);                 // E / 2
-        float* Rf = Xf + k * k;                                  // R 2^sh
-        __syncthreads();
-        for (int idx = tid; idx < k * k; idx += nt) {
-          Xf[idx] = float(X[idx]);
-          Rf[idx] = float(G0[idx] * down);
-        }
-        __syncthreads();
-        for (int idx = tid; idx < k * k; idx += nt) {
-          const int r = idx / k, c = idx % k;
+        for (int i = tid; i < b * k; i += nt) {
+          const int r = i / k, c = i - r * k;
           float corr = 0.0f;
-          for (int l = 0; l < k; ++l) corr = fmaf(Xf[r * k + l], Rf[l * k + c], corr);
-          a.Racc[idx] = fma(double(corr), up, G0[idx]);
+          for (int j = 0; j < k; ++j) corr = fmaf(Tf[r * k + j], Cf[j * k + c], corr);
+          T[i] -= double(corr);
+        }
+        __syncthreads();
+      } else {
+        // T := T Rinv (upper triangular, or the full first-order correction):
+        // one output entry per item, four independent partial sums (FP64
+        // issues a dependent operation only every ~65 cycles)
+        double* T2 = U + k * k;
+        for (int i = tid; i < k * k; i += nt) Rs[i] = __ldcg(a.Rinv + i);
+        __syncthreads();
+        for (int i = tid; i < b * k; i += nt) {
+          const int r = i / k, c = i - r * k;
+          const int jn = first_order ? k : c + 1;
+          const double* tr = T + r * k;
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          int j = 0;
+          for (; j + 4 <= jn; j += 4) {
+            s0 = fma(tr[j], Rs[j * k + c], s0);
+            s1 = fma(tr[j + 1], Rs[(j + 1) * k + c], s1);
+            s2 = fma(tr[j + 2], Rs[(j + 2) * k + c], s2);
+            s3 = fma(tr[j + 3], Rs[(j + 3) * k + c], s3);
+          }
+          for (; j < jn; ++j) s0 = fma(tr[j], Rs[j * k + c], s0);
+          T2[i] = (s0 + s1) + (s2 + s3);
+        }
+        __syncthreads();
+        for (int i = tid; i < b * k; i += nt) T[i] = T2[i];
+        __syncthreads();
+      }
+      if (final_pass) {
+        const bool cert = a.eps != nullptr && first_order && __ldcg(a.cert) != 0;
+        double* qd = cert ? a.Aw : a.Q;
+        const int64_t qr = cert ? a.a_rs : a.q_rs, qc = cert ? a.a_cs : a.q_cs;
+        for (int r = warp; r < b; r += nw) {
+          const int64_t gr = r0 + r;
+          if (gr < a.m)
+            for (int c = lane; c < k; c += 32) qd[gr * qr + c * qc] = T[r * k + c];
+        }
+        if (cert) {
+          // V(X_{n-1}) := V(X_{n-1}) R^T for this CTA's rows (in place)
+          double* Rt = U;                   // R, k x k
+          double* Xr = U + k * k;           // bp x k
+          const int64_t p0 = int64_t(lb) * a.bp;
+          const int64_t rem = a.mp - p0;
+          const int nr = rem <= 0 ? 0 : (rem < a.bp ? int(rem) : a.bp);
+          for (int i = tid; i < k * k; i += nt) Rt[i] = __ldcg(a.Racc + i);
+          for (int i = tid; i < nr * k; i += nt) Xr[i] = a.Xp[p0 * k + i];
+          __syncthreads();
+          for (int i = tid; i < nr * k; i += nt) {
+            const int r = i / k, c = i - r * k;
+            const double* xr = Xr + r * k;
+            const double* rr = Rt + c * k;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int j = 0;
+            for (; j + 4 <= k; j += 4) {
+              s0 = fma(xr[j], rr[j], s0);
+              s1 = fma(xr[j + 1], rr[j + 1], s1);
+              s2 = fma(xr[j + 2], rr[j + 2], s2);
+              s3 = fma(xr[j + 3], rr[j + 3], s3);
+            }
+            for (; j < k; ++j) s0 = fma(xr[j], rr[j], s0);
+            a.Xp[p0 * k + i] = (s0 + s1) + (s2 + s3);
+          }
+        }
+        if (first_order) {
+          // Q = Q1 (I - E/2) with ||E||_F <= 1e-8: orthonormal to O(||E||^2), no check
+          if (lb == 0 && tid == 0) atomicExch(st + 2, 1);
+          return;
         }
       }
-      if (tid == 0) {
-        a.status[4] = 1;
-        a.status[1] = 2;
-        a.status[3] += 1;
+    }
+    // partial Gram of the row block (packed upper triangle), four partial sums
+    double* Gp = a.Gpart + int64_t(lb) * npair;
+    for (int p = tid; p < npair; p += nt) {
+      int i1, j1;
+      tri_ij(p, k, &i1, &j1);
+      double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+      int r = 0;
+      for (; r + 4 <= b; r += 4) {
+        g0 = fma(T[r * k + i1], T[r * k + j1], g0);
+        g1 = fma(T[(r + 1) * k + i1], T[(r + 1) * k + j1], g1);
+        g2 = fma(T[(r + 2) * k + i1], T[(r + 2) * k + j1], g2);
+        g3 = fma(T[(r + 3) * k + i1], T[(r + 3) * k + j1], g3);
       }
-      return;
+      for (; r < b; ++r) g0 = fma(T[r * k + i1], T[r * k + j1], g0);
+      Gp[p] = (g0 + g1) + (g2 + g3);
     }
-  }
-  bool ok = chol_with_inverse(G, X, k);
-  bool shifted = false;
-  if (!ok) {
-    __shared__ double s_shift;
+    // two-level arrival: the last CTA of each group sums its group's partials
+    __threadfence();
+    __syncthreads();
+    const int grp = lb / CQ_GROUP;
+    const int gsize = min(CQ_GROUP, a.P - grp * CQ_GROUP);
     if (tid == 0) {
-      double tr = 0.0;
-      for (int i = 0; i < k; ++i) tr += G0[i * k + i];
-      s_shift = 11.0 * (double(a.m) * k + double(k) * (k + 1)) * 0x1p-53 * tr;
+      const int old = atomicAdd(st + 6 + grp, 1);
+      s_flag = (old == gsize - 1);
+      if (s_flag) st[6 + grp] = 0;
     }
     __syncthreads();
-    for (int idx = tid; idx < k * k; idx += nt) G[idx] = G0[idx] + (((idx / k) == (idx % k)) ? s_shift : 0.0);
-    __syncthreads();
-    ok = chol_with_inverse(G, X, k);
-    shifted = true;
-  }
-  if (!ok) {                                    // not even the shifted Gram is positive definite
-    if (tid == 0) {
-      atomicExch(a.status, 1);
-      atomicExch(a.status + 2, 1);
-    }
-    return;
-  }
-  if (tid == 0) {
-    a.status[1] = shifted ? 0 : unshifted_run + 1;
-    a.status[3] += 1;
-  }
-  // Rinv = L^{-T} (upper)
-  for (int idx = tid; idx < k * k; idx += nt) {
-    const int r = idx / k, c = idx % k;
-    a.Rinv[idx] = (c >= r) ? X[c * k + r] : 0.0;
-  }
-  if (a.Racc) {
-    if (a.pass > 0) {
-      for (int idx = tid; idx < k * k; idx += nt) G0[idx] = a.Racc[idx];
+    bool decider = false;
+    if (s_flag) {
+      __threadfence();
+      double* Gg = a.Gpart + int64_t(a.P + grp) * npair;
+      const double* base = a.Gpart + int64_t(grp) * CQ_GROUP * npair;
+      for (int p = tid; p < npair; p += 2 * nt) {
+        // two entries per pass of the loop: 32 loads in flight per thread
+        const int p2 = p + nt;
+        double u[CQ_GROUP], v[CQ_GROUP];
+#pragma unroll
+        for (int q = 0; q < CQ_GROUP; ++q) {
+          u[q] = q < gsize ? __ldcg(base + int64_t(q) * npair + p) : 0.0;
+          v[q] = (q < gsize && p2 < npair) ? __ldcg(base + int64_t(q) * npair + p2) : 0.0;
+        }
+#pragma unroll
+        for (int w = 1; w < CQ_GROUP; w *= 2)
+#pragma unroll
+          for (int q = 0; q + w < CQ_GROUP; q += 2 * w) {
+            u[q] += u[q + w];
+            v[q] += v[q + w];
+          }
+        Gg[p] = u[0];
+        if (p2 < npair) Gg[p2] = v[0];
+      }
+      __threadfence();
       __syncthreads();
-      for (int idx = tid; idx < k * k; idx += nt) {
-        const int r = idx / k, c = idx % k;
-        double s = 0.0;
-        for (int j = r; j <= c; ++j) s = fma(G[j * k + r], G0[j * k + c], s);
-        a.Racc[idx] = (c >= r) ? s : 0.0;
+      if (tid == 0) {
+        const int old = atomicAdd(st + 5, 1);
+        s_flag = (old == ngrp - 1);
+        if (s_flag) st[5] = 0;
       }
+      __syncthreads();
+      decider = s_flag;
+    }
+    if (decider) {
+      __threadfence();
+      double* G = U;
+      double* X = G + k * k;
+      double* G0 = X + k * k;
+      // at most CQ_GROUP group partials (coop_shape keeps P <= CQ_GROUP^2):
+      // all loads in flight at once, then a fixed pairwise tree
+      for (int p = tid; p < npair; p += nt) {
+        const double* base = a.Gpart + int64_t(a.P) * npair + p;
+        double u[CQ_GROUP];
+#pragma unroll
+        for (int q = 0; q < CQ_GROUP; ++q) u[q] = q < ngrp ? __ldcg(base + int64_t(q) * npair) : 0.0;
+#pragma unroll
+        for (int w = 1; w < CQ_GROUP; w *= 2)
+#pragma unroll
+          for (int q = 0; q + w < CQ_GROUP; q += 2 * w) u[q] += u[q + w];
+        const double acc = u[0];
+        int i, j;
+        tri_ij(p, k, &i, &j);
+        G[i * k + j] = acc;
+        G[j * k + i] = acc;
+        G0[i * k + j] = acc;
+        G0[j * k + i] = acc;
+      }
+      __syncthreads();
+      // certificate inputs, before the decision overwrites G and Rinv
+      __shared__ double s_red[CQ_THREADS / 32];
+      const bool try_cert = a.eps != nullptr && pass == 1 && !final_pass && a.rcap >= k;
+      double e2 = 0.0, ri2 = 0.0;
+      if (try_cert) {
+        double pe = 0.0, pr = 0.0;
+        for (int idx = tid; idx < k * k; idx += nt) {
+          const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
+          const double ri = __ldcg(a.Rinv + idx);
+          pe = fma(dv, dv, pe);
+          pr = fma(ri, ri, pr);
+        }
+        e2 = block_sum(pe, s_red);
+        ri2 = block_sum(pr, s_red);
+      }
+      cqr_decide(G, X, G0, k, a.m, pass, final_pass, unshifted_run, a.Rinv, a.Racc, a.fo_r, st);
+      if (final_pass) return;
+      if (try_cert && tid == 0 && st[4] != 0) {
+        const double lbound = (1.0 - sqrt(e2)) * (1.0 - 1e-6) / sqrt(ri2);
+        if (isfinite(lbound) && ri2 > 0.0 && e2 < 1e-4 && lbound > 2.0 * __ldcg(a.eps)) {
+          *a.cert = 1;
+          *a.rank_out = k;
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) st_release_gpu(released, pass + 1);
     } else {
-      for (int idx = tid; idx < k * k; idx += nt) {
-        const int r = idx / k, c = idx % k;
-        a.Racc[idx] = (c >= r) ? G[c * k + r] : 0.0;
+      if (final_pass) return;
+      if (tid == 0) {
+        const unsigned long long t0 = global_ns();
+        int ok = 1;
+        while (ld_acquire_gpu(released) < pass + 1) {
+          if (global_ns() - t0 > kCoopWaitNs) {
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence();
+        s_flag = ok;
+      }
+      __syncthreads();
+      if (!s_flag) {
+        if (tid == 0) atomicOr(a.dev_status, DEV_TIMEOUT);
+        return;
       }
     }
+    if (__ldcg(st + 2)) return;           // the chain broke down: the Householder fallback takes over
+    __syncthreads();
   }
+}
+
+// Row blocking of the cooperative kernel: about one block per SM; feasible when
+// the shared memory fits and the grid is co-resident.
+bool coop_shape(int64_t m, int k, int* b, int* P, size_t* smem) {
+  if (k > CQ_SMEM_K || k < 1 || m < k) return false;
+  const int nsm = num_sms();
+  const int64_t bb = std::max<int64_t>(4, ceil_div(m, nsm));
+  const size_t bytes = size_t(coop_smem_doubles(int(bb), k)) * sizeof(double);
+  if (bytes > 220 * 1024) return false;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cqr_coop_kernel, CQ_THREADS, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int64_t PP = ceil_div(m, bb);
+  if (nb < 1 || PP > int64_t(nb) * nsm || PP > int64_t(CQ_GROUP) * CQ_GROUP) return false;
+  *b = int(bb);
+  *P = int(PP);
+  *smem = bytes;
+  return true;
+}
+
+int coop_launch(const CoopJob& job, size_t smem, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    TTR_CHECK_CUDA(cudaFuncSetAttribute(cqr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    attr = true;
+  }
+  cudaEvent_t e0;
+  const bool prof = prof_begin(s, &e0);
+  TTR_PREFER_SHARED(cqr_coop_kernel);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(job.P));
+  cfg.blockDim = dim3(CQ_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  TTR_CHECK_CUDA(cudaLaunchKernelEx(&cfg, cqr_coop_kernel, job));
+  prof_count_launch(1);
+  if (prof) prof_end(s, 1, 4.0 * double(job.m) * double(job.k) * double(job.k));
+  return TT_OK;
 }
 
 int cqr_launch(const CqrPass& p, cudaStream_t s) {
@@ -466,7 +852,7 @@ void qr_shape(int64_t m, int k, int* rows, int* P, int* nstat) {
   const int64_t bmax = std::max<int64_t>(1, budget / (2 * int64_t(k)));
   *rows = int(std::min<int64_t>(bmax, std::max<int64_t>(4, ceil_div(m, num_sms()))));
   *P = int(ceil_div(m, *rows));
-  *nstat = 5 + 1 + (*P + 15) / 16;      // [0..4] chain state, then arrival counters
+  *nstat = 5 + 1 + (*P + 15) / 16 + 2;  // [0..4] chain state, arrival counters, released passes, certificate
 }
 }  // namespace
 
@@ -526,15 +912,81 @@ QrBufs qr_reserve(Arena& ar, int64_t m, int k) {
   return qr_view(qr_pool_reserve(ar, {{m, k}}), m, k);
 }
 
+void qr_chain_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q,
+                   int64_t q_rs, int64_t q_cs, double* R, bool r_may_be_full);
+void qr_fallback_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q,
+                      int64_t q_rs, int64_t q_cs, double* R);
+
+static std::atomic<int> g_qr_mode{QR_MODE_AUTO};
+int set_qr_mode(int mode) {
+  if (mode < QR_MODE_AUTO || mode > QR_MODE_FORCE_FALLBACK) return TT_EINVAL;
+  g_qr_mode.store(mode);
+  return TT_OK;
+}
+
+const int* qr_cert_flag(const QrBufs& b) { return b.status ? b.status + b.nstat - 1 : nullptr; }
+
 void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q, int64_t q_rs,
-             int64_t q_cs, double* R, bool r_may_be_full) {
+             int64_t q_cs, double* R, bool r_may_be_full, const QrCert* cert) {
   const QrBufs bb = b;
-  sc.add([bb](cudaStream_t s) -> int {
+  const int mode = g_qr_mode.load();
+  const bool force_fallback = (mode == QR_MODE_FORCE_FALLBACK) && b.k <= TSQR_KMAX;
+  sc.add([bb, force_fallback](cudaStream_t s) -> int {
     if (!bb.status) return int(TT_OK);
     TTR_CHECK_CUDA(cudaMemsetAsync(bb.status, 0, bb.nstat * sizeof(int), s));
     if (bb.ti && bb.ti_n) TTR_CHECK_CUDA(cudaMemsetAsync(bb.ti, 0, bb.ti_n * sizeof(int), s));
+    if (force_fallback) return set_flag_launch(bb.status, s);
     return int(TT_OK);
   });
+  int cb = 0, cP = 0;
+  size_t csm = 0;
+  if (!force_fallback && mode == QR_MODE_AUTO && coop_shape(b.m, b.k, &cb, &cP, &csm)) {
+    CoopJob job{};
+    job.m = b.m;
+    job.k = b.k;
+    job.b = cb;
+    job.P = cP;
+    job.fo_r = r_may_be_full ? 1 : 0;
+    job.A = A;
+    job.a_rs = a_rs;
+    job.a_cs = a_cs;
+    job.Q = Q;
+    job.q_rs = q_rs;
+    job.q_cs = q_cs;
+    job.Gpart = b.Gpart;
+    job.Rinv = b.Rinv;
+    job.Racc = R;
+    job.status = b.status;
+    if (cert && R && r_may_be_full) {
+      const int64_t bp = ceil_div(cert->mp, int64_t(cP));
+      if (bp * b.k + int64_t(b.k) * b.k <= coop_smem_doubles(cb, b.k) - int64_t(cb) * b.k) {
+        job.eps = cert->eps;
+        job.rcap = cert->rcap;
+        job.bp = int(bp);
+        job.cert = b.status ? b.status + b.nstat - 1 : nullptr;
+        job.rank_out = cert->rank_out;
+        job.Aw = cert->Aw;
+        job.Xp = cert->Xp;
+        job.mp = cert->mp;
+      }
+    }
+    int* const* sp = &sc.dev_status;
+    sc.add([job, csm, sp](cudaStream_t s) -> int {
+      if (!job.status) return int(TT_OK);
+      CoopJob j = job;
+      j.dev_status = *sp;
+      return coop_launch(j, csm, s);
+    });
+  }
+  else if (!force_fallback) {
+    qr_chain_plan(sc, b, A, a_rs, a_cs, Q, q_rs, q_cs, R, r_may_be_full);
+  }
+  qr_fallback_plan(sc, b, A, a_rs, a_cs, Q, q_rs, q_cs, R);
+}
+
+// The multi-launch chain: CQ_MAX_PASSES launches of cqr_pass_kernel.
+void qr_chain_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q,
+                   int64_t q_rs, int64_t q_cs, double* R, bool r_may_be_full) {
   CqrPass base{};
   base.m = b.m;
   base.k = b.k;
@@ -560,6 +1012,13 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
     pp.pass = p;
     sc.add([pp](cudaStream_t s) -> int { return cqr_launch(pp, s); });
   }
+}
+
+// Householder TSQR when the chain raised status[0] (k <= 96); above that limit
+// a failure is reported in the run's status word.
+void qr_fallback_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q,
+                      int64_t q_rs, int64_t q_cs, double* R) {
+  const QrBufs bb = b;
   if (b.k <= TSQR_KMAX) {
     // Householder fallback, run only when the device flag is raised
     sc.add([bb, A, a_rs, a_cs, Q, q_rs, q_cs, R](cudaStream_t s) -> int {

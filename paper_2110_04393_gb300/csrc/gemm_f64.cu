@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_f64_kernel(const GemmDesc* 
   __shared__ int s_last;
   const int64_t t = blockIdx.x;
   const GemmDesc& d = descs[find_desc(descs, ndesc, t)];
+  if (d.skip && __ldcg(d.skip) != 0) return;
   int64_t local = t - d.tile_begin;
   const int ntile = int(local % d.nt); local /= d.nt;
   const int mtile = int(local % d.mt); local /= d.mt;

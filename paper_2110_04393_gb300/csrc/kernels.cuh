@@ -39,6 +39,7 @@ struct GemmDesc {
   int64_t split_begin;  // prefix of the split-pass blocks
   int32_t bkc;          // K-chunk width (16, 32, 48 or 64)
   int32_t lx;           // 1: the split pass takes the exponents itself (short K, no exponent pass)
+  const int* skip;      // FP64 GEMM only: when set and *skip != 0 on the device, the descriptor does nothing
 };
 
 constexpr int GEMM_BM = 32, GEMM_BN = 32, GEMM_BK = 16, GEMM_THREADS = 256;
@@ -111,7 +112,8 @@ int tsqr_launch(const TsqrShape& sh, const TsqrWork& w, const double* A, int64_t
 // k > 96 needs global scratch of svd_scratch_doubles(k) doubles (else may be null).
 size_t svd_scratch_doubles(int k);
 int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, double* G1, double* G2,
-                     double* sigma, int64_t* rank_out, cudaStream_t s, double* big = nullptr);
+                     double* sigma, int64_t* rank_out, cudaStream_t s, double* big = nullptr,
+                     const int* skip_if = nullptr);
 // B independent full SVDs (no truncation) in one launch, one block each: job b
 // has k_b = kd[b] (a device array of doubles) <= kmax, R_b, G1_b, G2_b at
 // b * kmax * kmax and sigma_b at b * kmax; kmax > 96 needs B * svd_scratch_doubles(kmax)
@@ -136,7 +138,11 @@ constexpr int DEV_TIMEOUT = 1;   // a bounded device wait gave up
 constexpr int DEV_QR_FAIL = 2;   // a thin QR produced no orthonormal basis
 // dst[0] |= bit if src[0] != 0 (device flags)
 int or_flag_launch(int* dst, const int* src, int bit, cudaStream_t s);
+// dst[0] := 1 (device flag)
+int set_flag_launch(int* dst, cudaStream_t s);
 int fill_launch(double* p, int64_t n, double v, cudaStream_t s);
+// dst[0..n) = src[0..n) unless skip_if is set and *skip_if != 0 (device flag)
+int copy_if_launch(double* dst, const double* src, int64_t n, const int* skip_if, cudaStream_t s);
 // Adjoint helpers: X = T^{-1} (upper triangular, k x k), A := tril(A) + tril(A, -1)^T, y += x.
 int triu_inverse_launch(const double* T, double* X, int k, cudaStream_t s);
 int sym_lower_launch(double* A, int k, cudaStream_t s);

@@ -178,6 +178,32 @@ __global__ void or_flag_kernel(int* dst, const int* src, int bit) {
   if (threadIdx.x == 0 && src[0]) dst[0] |= bit;
 }
 }  // namespace
+__global__ void copy_if_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t n,
+                               const int* skip_if) {
+  if (skip_if && __ldcg(skip_if) != 0) return;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    dst[e] = src[e];
+}
+int copy_if_launch(double* dst, const double* src, int64_t n, const int* skip_if, cudaStream_t s) {
+  if (!dst || !src || n <= 0) return TT_OK;
+  const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4 * num_sms())));
+  TTR_PREFER_SHARED(copy_if_kernel);
+  copy_if_kernel<<<g, 256, 0, s>>>(dst, src, n, skip_if);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+__global__ void set_flag_kernel(int* dst) {
+  if (threadIdx.x == 0) dst[0] = 1;
+}
+int set_flag_launch(int* dst, cudaStream_t s) {
+  if (!dst) return TT_OK;
+  TTR_PREFER_SHARED(set_flag_kernel);
+  set_flag_kernel<<<1, 32, 0, s>>>(dst);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
 int or_flag_launch(int* dst, const int* src, int bit, cudaStream_t s) {
   if (!dst || !src) return TT_OK;
   TTR_PREFER_SHARED(or_flag_kernel);

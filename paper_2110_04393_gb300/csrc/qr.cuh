@@ -44,7 +44,33 @@ QrBufs qr_reserve(Arena& ar, int64_t m, int k);
 // r_may_be_full: R may come out as a full k x k matrix (A = Q R still holds;
 // the first-order last pass then spares a factorization); otherwise R is upper
 // triangular with a nonnegative diagonal.
+// Optional truncation certificate for the thin QR of a right-to-left
+// truncation bond (A = H(X_n)^T, R wanted and allowed full): see CoopJob in
+// cholqr_f64.cu. When the cooperative chain proves sigma_min(A) > 2 eps (and
+// rcap >= k) it writes Q over A (Aw, A's strides), multiplies Xp (mp x k,
+// row-major) by R^T in place, sets *rank_out = k and raises the flag that
+// qr_cert_flag returns; otherwise the flag stays 0 and Q, R are produced as
+// usual. The flag is valid until the pool's next QR starts.
+struct QrCert {
+  const double* eps;
+  int rcap;
+  int64_t* rank_out;
+  double* Aw;
+  double* Xp;
+  int64_t mp;
+};
 void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64_t a_cs, double* Q, int64_t q_rs,
-             int64_t q_cs, double* R, bool r_may_be_full = false);
+             int64_t q_cs, double* R, bool r_may_be_full = false, const QrCert* cert = nullptr);
+const int* qr_cert_flag(const QrBufs& b);
+
+// How qr_plan runs the chain (library-wide, read when a schedule is built):
+// AUTO = one cooperative launch when the row blocks fit in shared memory and
+// the grid is co-resident, else the multi-launch chain; CHAIN = always the
+// multi-launch chain; FORCE_FALLBACK = skip the Cholesky chain and run the
+// Householder TSQR for every QR with k <= 96 (a diagnostic of that path).
+constexpr int QR_MODE_AUTO = 0, QR_MODE_CHAIN = 1, QR_MODE_FORCE_FALLBACK = 2;
+int set_qr_mode(int mode);
+// Number of Householder TSQR fallback runs on the current device since load.
+int tsqr_fallback_runs(long long* out);
 
 }  // namespace ttr

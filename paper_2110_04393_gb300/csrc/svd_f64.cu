@@ -258,7 +258,9 @@ __device__ __forceinline__ void svd_trunc_body(int k, const double* __restrict__
 __global__ void __launch_bounds__(SVD_THREADS) svd_trunc_kernel(int k, const double* __restrict__ R,
                                                                 const double* __restrict__ eps_ptr, int rcap,
                                                                 double* G1, double* G2, double* sigma,
-                                                                int64_t* rank_out, double* big) {
+                                                                int64_t* rank_out, double* big,
+                                                                const int* skip_if) {
+  if (skip_if && __ldcg(skip_if) != 0) return;
   svd_trunc_body(k, R, eps_ptr, rcap, G1, G2, sigma, rank_out, big);
 }
 
@@ -285,7 +287,7 @@ size_t svd_scratch_doubles(int k) {
 }
 
 int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, double* G1, double* G2,
-                     double* sigma, int64_t* rank_out, cudaStream_t s, double* big) {
+                     double* sigma, int64_t* rank_out, cudaStream_t s, double* big, const int* skip_if) {
   if (k < 1 || (k > SVD_SMEM_K && big == nullptr)) {
     set_error("svd_trunc: k out of range or missing scratch");
     return TT_EUNSUPPORTED;
@@ -299,7 +301,7 @@ int svd_trunc_launch(int k, const double* R, const double* eps_ptr, int rcap, do
   }
   TTR_PREFER_SHARED(svd_trunc_kernel);
   svd_trunc_kernel<<<1, SVD_THREADS, smem, s>>>(k, R, eps_ptr, rcap, G1, G2, sigma, rank_out,
-                                                k > SVD_SMEM_K ? big : nullptr);
+                                                k > SVD_SMEM_K ? big : nullptr, skip_if);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
   return TT_OK;

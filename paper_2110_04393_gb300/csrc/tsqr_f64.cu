@@ -133,6 +133,9 @@ __device__ __forceinline__ int level_offset(int P, int l) {
   return off;
 }
 
+// Number of fallback runs (leaf launches that did not skip), for diagnostics.
+__device__ unsigned long long g_tsqr_runs = 0;
+
 __global__ void __launch_bounds__(TQ_THREADS) tsqr_up_kernel(TsqrArgs a) {
   extern __shared__ double smem[];
   const int k = a.k, b = a.b;
@@ -146,6 +149,7 @@ __global__ void __launch_bounds__(TQ_THREADS) tsqr_up_kernel(TsqrArgs a) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int p = blockIdx.x;
   if (a.skip_unless && *a.skip_unless == 0) return;
+  if (p == 0 && tid == 0 && a.skip_unless) atomicAdd(&g_tsqr_runs, 1ull);
 
   // ---- leaf: rows [p*b, p*b + b) of A, zero padded past m
   const int64_t r0 = int64_t(p) * b;
@@ -331,6 +335,13 @@ int tsqr_launch(const TsqrShape& sh, const TsqrWork& w, const double* A, int64_t
     TTR_CHECK_LAUNCH();
   prof_count_launch(1);
   }
+  return TT_OK;
+}
+
+int tsqr_fallback_runs(long long* out) {
+  unsigned long long v = 0;
+  TTR_CHECK_CUDA(cudaMemcpyFromSymbol(&v, g_tsqr_runs, sizeof(v)));
+  *out = (long long)v;
   return TT_OK;
 }
 
