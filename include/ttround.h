@@ -373,6 +373,63 @@ size_t tt_truncate_lorth_workspace(int32_t N, const int64_t* dims, const int64_t
                                    int64_t max_rank);
 
 /*
+ * tt_inner -- inner products <X, Y^(j)> of one TT X with K TTs Y^(j) of the
+ * same mode sizes (Section 2.3): Algorithm 3 (right-to-left partial
+ * contractions) of every Y^(j) against X, run down to the first core, where
+ * the partial contraction W_0 is the 1 x 1 inner product. All K sweeps share
+ * the cores of X: one grouped product per core for the Y^(j) and one for X.
+ *   X: N, dims (host, N), ranks_x (host, N+1), cores_x (host array of N device pointers)
+ *   Y: K, ranks_y (host, K*(N+1)), cores_y (host array of K*N device pointers), as tt_round_sum_rand
+ *   out: device array of K doubles, out[j] = <X, Y^(j)>
+ * tt_norm: ||X|| = sqrt(<X, X>) by the same sweep, into out (device, 1 double).
+ * Both synchronize the stream at the end (device status). Errors: TT_EINVAL,
+ * TT_ENOMEM, TT_ECUDA.
+ */
+int tt_inner(int32_t N, const int64_t* dims, const int64_t* ranks_x, const double* const* cores_x, int32_t K,
+             const int64_t* ranks_y, const double* const* cores_y, double* out, void* workspace,
+             size_t workspace_bytes, void* stream);
+size_t tt_inner_workspace(int32_t N, const int64_t* dims, const int64_t* ranks_x, int32_t K,
+                          const int64_t* ranks_y);
+int tt_norm(int32_t N, const int64_t* dims, const int64_t* ranks, const double* const* cores, double* out,
+            void* workspace, size_t workspace_bytes, void* stream);
+size_t tt_norm_workspace(int32_t N, const int64_t* dims, const int64_t* ranks);
+
+/*
+ * tt_mode_products -- count mode products of TT cores with matrices in one
+ * grouped launch (the factors of a Kronecker-product operator applied core by
+ * core, Section 4.2): for q < count, with shapes[4q..4q+3] = (r0, I, r1, J),
+ *   out_q(a, j, b) = sum_i A_q(j, i) core_q(a, i, b),
+ * A_q a J x I row-major device matrix, core_q (r0, I, r1) and out_q (r0, J, r1)
+ * device arrays in C order (out_q must not overlap core_q or A_q).
+ * Errors: TT_EINVAL, TT_ENOMEM, TT_ECUDA.
+ */
+int tt_mode_products(int32_t count, const int64_t* shapes, const double* const* A, const double* const* cores,
+                     double* const* out, void* workspace, size_t workspace_bytes, void* stream);
+size_t tt_mode_products_workspace(int32_t count, const int64_t* shapes);
+
+/*
+ * tt_round_gram_schmidt -- one Gram-Schmidt step of TT-GMRES (Section 4.2)
+ * as a single call: with W (one TT) and the basis V_1..V_k,
+ *   h_j = <V_j, W> (j = 1..k, tt_inner's sweep),
+ *   Z = W - sum_j h_j V_j rounded by Algorithm 7 (coefficients 1, -h_1, ..,
+ *       -h_k taken from the device, sketch ranks ells, tolerance tol as in
+ *       tt_round_sum_rand, sketch from `sketch` or drawn from seed),
+ *   h_{k+1} = ||Z|| and V_{k+1} = Z / h_{k+1} (Z left as is when ||Z|| = 0).
+ *   W: N, dims, ranks_w (N+1), cores_w (N device pointers)
+ *   basis: k >= 0, ranks_v (k*(N+1)), cores_v (k*N device pointers)
+ *   out, out_ranks: as tt_round_sum_rand (V_{k+1} written compactly)
+ *   h: host, k+1 doubles: h_1..h_k then ||Z||
+ * One host synchronization at the end. Errors: as tt_round_sum_rand.
+ */
+int tt_round_gram_schmidt(int32_t N, const int64_t* dims, const int64_t* ranks_w, const double* const* cores_w,
+                          int32_t k, const int64_t* ranks_v, const double* const* cores_v, const int64_t* ells,
+                          const double* const* sketch, uint64_t seed, double tol, int32_t precision,
+                          double* const* out, int64_t* out_ranks, double* h, void* workspace,
+                          size_t workspace_bytes, void* stream);
+size_t tt_round_gram_schmidt_workspace(int32_t N, const int64_t* dims, const int64_t* ranks_w, int32_t k,
+                                       const int64_t* ranks_v, const int64_t* ells, double tol, int32_t precision);
+
+/*
  * tt_round_sum_rand_noalloc -- tt_round_sum_rand for callers that cannot
  * allocate device memory (no counterpart in the paper: it only changes where the
  * scratch lives). Some callers may not call cudaMalloc at the point of the

@@ -27,6 +27,7 @@ from .rounding import (orthogonalize_rl, orthogonalize_lr, svd_truncated, tt_rou
                        round_sum_twosided, round_sum_twosided_orth, truncate_left_orthogonal, clamp_ranks)
 from .philox import philox4x32_10, gaussian_sketch_philox
 from .adjoint import randorth_fixed_sketch_loss, randorth_adjoint
+from .gmres import apply_term, gram_schmidt_round, tt_gmres, precondition, round_sum, sum_sketch_ranks
 
 __all__ = [
     "H", "V", "from_H", "from_V", "full", "full_bruteforce", "inner", "norm", "diff_norm",
@@ -37,4 +38,5 @@ __all__ = [
     "round_sum_twosided", "round_sum_twosided_orth", "truncate_left_orthogonal", "clamp_ranks",
     "philox4x32_10", "gaussian_sketch_philox",
     "randorth_fixed_sketch_loss", "randorth_adjoint",
+    "apply_term", "gram_schmidt_round", "tt_gmres", "precondition", "round_sum", "sum_sketch_ranks",
 ]

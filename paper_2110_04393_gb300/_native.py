@@ -42,6 +42,15 @@ SIGNATURES = {
     "tt_round_twosided_orth_workspace": (c_size, [c_i32, c_i32, P_i64, P_i64, P_i64, P_i64, c_dbl, c_i32]),
     "tt_truncate_lorth": (c_i32, [c_i32, P_i64, P_i64, P_vp, c_dbl, c_i64, P_i64, c_vp, c_size, c_vp]),
     "tt_truncate_lorth_workspace": (c_size, [c_i32, P_i64, P_i64, c_dbl, c_i64]),
+    "tt_inner": (c_i32, [c_i32, P_i64, P_i64, P_vp, c_i32, P_i64, P_vp, c_vp, c_vp, c_size, c_vp]),
+    "tt_inner_workspace": (c_size, [c_i32, P_i64, P_i64, c_i32, P_i64]),
+    "tt_norm": (c_i32, [c_i32, P_i64, P_i64, P_vp, c_vp, c_vp, c_size, c_vp]),
+    "tt_norm_workspace": (c_size, [c_i32, P_i64, P_i64]),
+    "tt_round_gram_schmidt": (c_i32, [c_i32, P_i64, P_i64, P_vp, c_i32, P_i64, P_vp, P_i64, P_vp, c_u64, c_dbl,
+                                      c_i32, P_vp, P_i64, P_dbl, c_vp, c_size, c_vp]),
+    "tt_round_gram_schmidt_workspace": (c_size, [c_i32, P_i64, P_i64, c_i32, P_i64, P_i64, c_dbl, c_i32]),
+    "tt_mode_products": (c_i32, [c_i32, P_i64, P_vp, P_vp, P_vp, c_vp, c_size, c_vp]),
+    "tt_mode_products_workspace": (c_size, [c_i32, P_i64]),
     "tt_noalloc_scratch_bytes": (c_size, []),
     "tt_round_sum_rand_noalloc": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl,
                                           c_i32, P_vp, P_i64, c_vp]),

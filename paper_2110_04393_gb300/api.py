@@ -593,6 +593,117 @@ def tt_truncate_lorth(cores, *, tol=0.0, max_rank=0, workspace=None, stream=None
     return [work[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)]
 
 
+def _tt_args(cores, name="core"):
+    dims = [int(c.shape[1]) for c in cores]
+    ranks = [int(cores[0].shape[0])] + [int(c.shape[2]) for c in cores]
+    for n, c in enumerate(cores):
+        _check_core(c, f"{name} {n}")
+    return dims, ranks
+
+
+def tt_inner(X, Ys, *, workspace=None, stream=None):
+    """<X, Y_j> for every TT in Ys (Algorithm 3 run to the first core), as a
+    float64 CUDA tensor of len(Ys) values."""
+    N = len(X)
+    device = X[0].device
+    dims, rx = _tt_args(X, "X core")
+    N2, K, dims2, ranks, flat = _sum_args(Ys)
+    if N2 != N or dims2 != dims:
+        raise ValueError("X and Ys need the same order and mode sizes")
+    L = nat.lib()
+    out = torch.empty(K, dtype=torch.float64, device=device)
+    nb = L.tt_inner_workspace(N, _i64(dims), _i64(rx), K, _i64(ranks))
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    _check(L.tt_inner(N, _i64(dims), _i64(rx), _ptrs(X), K, _i64(ranks), _ptrs(flat), ctypes.c_void_p(out.data_ptr()),
+                      wp, wb, _stream(stream, device)))
+    return out
+
+
+def tt_norm(X, *, workspace=None, stream=None):
+    """||X|| (float64 CUDA scalar tensor)."""
+    N = len(X)
+    device = X[0].device
+    dims, r = _tt_args(X)
+    L = nat.lib()
+    out = torch.empty(1, dtype=torch.float64, device=device)
+    nb = L.tt_norm_workspace(N, _i64(dims), _i64(r))
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    _check(L.tt_norm(N, _i64(dims), _i64(r), _ptrs(X), ctypes.c_void_p(out.data_ptr()), wp, wb,
+                     _stream(stream, device)))
+    return out[0]
+
+
+def tt_mode_products(mats, cores, *, workspace=None, stream=None):
+    """[A_q x_2 core_q for q]: out_q(a, j, b) = sum_i A_q(j, i) core_q(a, i, b)
+    for float64 CUDA matrices A_q (J x I) and cores (r0, I, r1), one grouped launch."""
+    if len(mats) != len(cores):
+        raise ValueError("one matrix per core")
+    if not cores:
+        return []
+    device = cores[0].device
+    shapes, outs, amats = [], [], []
+    for q, (A, c) in enumerate(zip(mats, cores)):
+        _check_core(c, f"core {q}")
+        if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2 and A.shape[1] == c.shape[1]):
+            raise ValueError(f"matrix {q}: expected a float64 CUDA (J, I) matrix with I = {c.shape[1]}")
+        A = A.contiguous()
+        amats.append(A)
+        shapes += [int(c.shape[0]), int(c.shape[1]), int(c.shape[2]), int(A.shape[0])]
+        outs.append(torch.empty((int(c.shape[0]), int(A.shape[0]), int(c.shape[2])), dtype=torch.float64,
+                                device=device))
+    L = nat.lib()
+    nb = L.tt_mode_products_workspace(len(cores), _i64(shapes))
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    _check(L.tt_mode_products(len(cores), _i64(shapes), _ptrs(amats), _ptrs(cores), _ptrs(outs), wp, wb,
+                              _stream(stream, device)))
+    return outs
+
+
+def tt_round_gram_schmidt(W, basis, ells, *, tol=0.0, sketch=None, seed=0, precision="fp64", workspace=None,
+                          stream=None):
+    """One Gram-Schmidt step of TT-GMRES (Section 4.2) in one call:
+    h_j = <V_j, W>, Z = round(W - sum_j h_j V_j), V_new = Z / ||Z||.
+    Returns (V_new cores, h as a list of k + 1 floats: h_1..h_k, ||Z||)."""
+    N = len(W)
+    device = W[0].device
+    dims, rw = _tt_args(W, "W core")
+    k = len(basis)
+    rv, fv = [], []
+    for j, V in enumerate(basis):
+        d, r = _tt_args(V, f"basis {j} core")
+        if d != dims:
+            raise ValueError("basis tensors need the mode sizes of W")
+        rv += r
+        fv += list(V)
+    ell = clamp_ranks(dims, ells)
+    out = [torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float64, device=device) for n in range(N)]
+    sk_arr = None
+    if sketch is not None:
+        for n, c in enumerate(sketch):
+            _check_core(c, f"sketch core {n}")
+        sk_arr = _ptrs(sketch)
+    L = nat.lib()
+    prec = _PREC[precision]
+    nb = L.tt_round_gram_schmidt_workspace(N, _i64(dims), _i64(rw), k, _i64(rv), _i64(ell), float(tol), prec)
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    out_ranks = (ctypes.c_int64 * (N + 1))()
+    h = (ctypes.c_double * (k + 1))()
+    _check(L.tt_round_gram_schmidt(N, _i64(dims), _i64(rw), _ptrs(W), k, _i64(rv), _ptrs(fv) if k else None,
+                                   _i64(ell), sk_arr, ctypes.c_uint64(int(seed)), float(tol), prec, _ptrs(out),
+                                   out_ranks, h, wp, wb, _stream(stream, device)))
+    r = [int(x) for x in out_ranks]
+    Vn = [out[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)]
+    return Vn, [float(x) for x in h]
+
+
 def tt_round_rand(Y, ells, **kw):
     """Algorithm 5 (single TT, Randomize-then-Orthogonalize): tt_round_sum_rand with K = 1."""
     if kw.get("coeffs") is not None:

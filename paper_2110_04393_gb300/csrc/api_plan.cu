@@ -22,7 +22,8 @@
 namespace ttr {
 
 int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol, int digits,
-                   double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev, size_t* coeff_off);
+                   double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev, size_t* coeff_off,
+                   const double* coeff_dev);
 int mixed_digits(double tol, int N);
 
 namespace {
@@ -174,7 +175,8 @@ int unit_init(SumUnit* u, int32_t N, int32_t K, const int64_t* dims, const int64
     return TT_ECUDA;
   }
   BuildFn build = [u](Arena& ar, Schedule& sc) {
-    return build_sum_rand(u->P, nullptr, 0, u->tol, u->digits, u->outs.data(), ar, sc, &u->rk_dev, &u->coeff_off);
+    return build_sum_rand(u->P, nullptr, 0, u->tol, u->digits, u->outs.data(), ar, sc, &u->rk_dev, &u->coeff_off,
+                          nullptr);
   };
   return plan_prepare(build, &u->gp);
 }

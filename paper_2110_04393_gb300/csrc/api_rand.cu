@@ -472,7 +472,8 @@ int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int64_t>& 
 constexpr int kSketchDigits = 2;
 
 int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol, int digits,
-                   double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev, size_t* coeff_off) {
+                   double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev, size_t* coeff_off,
+                   const double* coeff_dev) {
   // digits == 0: every contraction in FP64. Else every contraction runs on the
   // tensor cores (emulated GEMM): the core updates and projections with
   // `digits` bf16 digits, the partial contractions of Algorithm 3 with
@@ -519,7 +520,15 @@ int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t
 
   // ---- set-up: counters, W_N = ones, M_0 = coefficients, sketch
   sc.add([=](cudaStream_t s) -> int { return fill_launch(W[N], S[N] * ell[N], 1.0, s); });
-  {
+  if (coeff_dev) {
+    // coefficients computed on the device by earlier steps of the schedule
+    double* m0 = Mb[0];
+    const int Kc = K;
+    sc.add([m0, coeff_dev, Kc](cudaStream_t s) -> int {
+      if (m0) TTR_CHECK_CUDA(cudaMemcpyAsync(m0, coeff_dev, sizeof(double) * Kc, cudaMemcpyDeviceToDevice, s));
+      return int(TT_OK);
+    });
+  } else {
     const size_t off = sc.upload(Mb[0], P.coeffs);
     if (coeff_off) *coeff_off = off;
   }
@@ -669,7 +678,7 @@ __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, 
   std::vector<double*> out_v(N, nullptr);
   if (out) out_v.assign(out, out + N);
   BuildFn build = [&](Arena& ar, Schedule& sc) {
-    return build_sum_rand(P, sketch, seed, tol, digits, out_v.data(), ar, sc, &rk_dev, nullptr);
+    return build_sum_rand(P, sketch, seed, tol, digits, out_v.data(), ar, sc, &rk_dev, nullptr, nullptr);
   };
   if (size_only) return plan_workspace_bytes(build, size_only);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

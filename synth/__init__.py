@@ -33,6 +33,7 @@ __all__ = [
     "workload_sum_structured",
     "workload_batched",
     "sketch_ranks_for",
+    "cookie_operator",
 ]
 
 
@@ -169,3 +170,41 @@ def workload_batched(seed: int, B=256, N=20, I=64, K_range=(2, 30), R_range=(4, 
 def sketch_ranks_for(dims, ell):
     """Target ranks (1, ell, ..., ell, 1) for a TT with the given mode sizes."""
     return [1] + [int(ell)] * (len(dims) - 1) + [1]
+
+
+def cookie_operator(N=5, I1=40, I=8, rho_range=(1.0, 10.0)):
+    """Synthetic stand-in for the parametric "cookie" problem of Section 4.2
+    (its FEM matrices are not available): the operator
+        A = sum_{i=1}^{N} A_{i,1} (x) ... (x) A_{i,N}
+    on a one-dimensional domain of I1 interior nodes (linear finite elements,
+    homogeneous Dirichlet ends) holding N - 1 disjoint "cookie" intervals.
+    A_{1,1} is the stiffness matrix of the whole domain, A_{i,1} (i >= 2) the
+    stiffness assembled over the cells of cookie i - 1 only, A_{i,i} =
+    diag(rho) with I parameter samples spread linearly over rho_range, and
+    every other factor the identity. Returns dict(terms, f, dims): terms[i] is
+    a list of N matrices (None for an identity factor), f the right-hand side
+    (ones over the domain times ones over every parameter) as TT cores."""
+    h = 1.0 / (I1 + 1)
+    ncell = I1 + 1
+
+    def stiffness(cells):
+        K = np.zeros((I1, I1))
+        for c in cells:                      # cell c joins nodes c - 1 and c (1-based interior nodes)
+            a, b = c - 1, c
+            for (p, q, v) in ((a, a, 1.0), (b, b, 1.0), (a, b, -1.0), (b, a, -1.0)):
+                if 1 <= p <= I1 and 1 <= q <= I1:
+                    K[p - 1, q - 1] += v / h
+        return K
+
+    ncook = N - 1
+    width = max(1, ncell // (2 * ncook + 1))
+    cookies = [list(range(1 + (2 * c + 1) * width, 1 + (2 * c + 2) * width)) for c in range(ncook)]
+    rho = np.linspace(rho_range[0], rho_range[1], I)
+    terms = [[stiffness(range(1, ncell + 1))] + [None] * (N - 1)]
+    for i in range(2, N + 1):
+        t = [stiffness(cookies[i - 2])] + [None] * (N - 1)
+        t[i - 1] = np.diag(rho)
+        terms.append(t)
+    dims = [I1] + [I] * (N - 1)
+    f = [np.ones((1, I1, 1)) * h] + [np.ones((1, I, 1)) for _ in range(N - 1)]
+    return {"terms": terms, "f": f, "dims": dims}
