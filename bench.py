@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     p.add_argument("--no-det", action="store_true", help="skip the deterministic comparison")
+    p.add_argument("--no-extra", action="store_true", help="skip the single-TT and adjoint legs")
     p.add_argument("--legs", default="mixed,fp64,twosided,det",
                    help="--config large: comma list of the legs to run (mixed, fp64, twosided, det)")
     p.add_argument("--config", default="sum", choices=["sum", "batched", "large"],
@@ -248,6 +249,65 @@ def run_reference(a):
           flush=True)
 
 
+def _event_ms(torch, fn, reps=10, warm=3):
+    """Median of `reps` CUDA-event timings of fn() after `warm` untimed calls."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def leg_single_tt(tt, torch, dev):
+    """Section 4.1 shape (config 1): Y of rank 10 plus 1e-6 E of rank 30, N = 10,
+    I = 50; Randomize-then-Orthogonalize with sketch rank 15 (captured plan and
+    eager call), the fixed-rank truncation to 10, and the deterministic rounding
+    to rank 10. Latencies in microseconds (inputs resident, warm)."""
+    import synth
+    Ys = synth.workload_single(1, N=10, I=50, R=10, R_pert=30, eps=1e-6)
+    Yd = [[torch.from_numpy(c).to(dev) for c in Y] for Y in Ys]
+    dims = [50] * 10
+    ell = [1] + [15] * 9 + [1]
+    plan = tt.SumRoundingPlan(dims, ranks_of(Ys), ell, tol=0.0, precision="fp64", device=dev)
+    X = plan(Yd, seed=1)
+    out = {"workload": "N=10, I=50, Y rank 10 + 1e-6 E rank 30 (formal rank 40), sketch rank 15, truncation to 10",
+           "rand_plan_us": 1e3 * _event_ms(torch, lambda: plan(Yd, seed=1)),
+           "rand_eager_us": 1e3 * _event_ms(torch, lambda: tt.tt_round_sum_rand(Yd, ell, seed=1)),
+           "truncate_to_10_us": 1e3 * _event_ms(torch, lambda: tt.tt_truncate_lorth(X, max_rank=10)),
+           "det_rank10_us": 1e3 * _event_ms(torch, lambda: tt.tt_round_det(Yd, max_rank=10), reps=5)}
+    plan.close()
+    return out
+
+
+def leg_adjoint_f32(tt, torch, dev):
+    """Config 4: fixed-sketch RandOrth of a TT with N = 16, I = 32, rank 64 to
+    l = 16 with float32 storage: forward and hand-written adjoint (FP32-class
+    products, FP64 QR steps), beside the float64 path. Milliseconds."""
+    import synth
+    N, I, R, ell = 16, 32, 64, 16
+    dims = [I] * N
+    Y = synth.gaussian_tt(synth.rng_for(140, 0), dims, [1] + [R] * (N - 1) + [1])
+    el = tt.clamp_ranks(dims, [1] + [ell] * (N - 1) + [1])
+    Om = synth.gaussian_tt(synth.rng_for(140, 1), dims, el)
+    res = {"workload": "N=16, I=32, rank 64 rounded to l=16, fixed sketch; loss gradient w.r.t. all input cores"}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        Yd = [torch.from_numpy(c).to(dev, dt) for c in Y]
+        Od = [torch.from_numpy(c).to(dev, dt) for c in Om]
+        X = tt.tt_round_rand(Yd, el, sketch=Od, tol=0.0)
+        Xb = [torch.ones_like(c) for c in X]
+        res[name + "_forward_ms"] = _event_ms(torch, lambda: tt.tt_round_rand(Yd, el, sketch=Od, tol=0.0))
+        res[name + "_backward_ms"] = _event_ms(torch, lambda: tt.tt_round_rand_backward(Yd, el, Od, Xb))
+    return res
+
+
 def timed_plan(tt, torch, plan, Yd, steps, warmup, flush, stream, world, dist):
     """Warm-up and timed replays of a captured plan. Returns (ms per step,
     per-kind profile, kernel launches, output ranks); the profile holds the
@@ -438,6 +498,9 @@ def run_ours(a):
                                     "graph_replay": True}
     variants["rand_" + prim + "_eager"] = {"ms_per_step": eager_ms, "tflops_alg": flops / (eager_ms * 1e-3) / 1e12}
     variants["det_fp64"] = det
+    if world == 1 and not a.no_extra:
+        variants["single_tt_cfg1"] = leg_single_tt(tt, torch, dev)
+        variants["adjoint_cfg4"] = leg_adjoint_f32(tt, torch, dev)
     res = {
         "metric": METRIC,
         "value": replica_tflops(flops, t_ms, world),

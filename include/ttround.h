@@ -55,7 +55,9 @@ typedef enum {
 
 typedef enum {
   TT_PREC_FP64 = 0,     /* every step in float64 */
-  TT_PREC_MIXED = 1     /* contractions on the tensor cores (see tt_round_sum_rand) */
+  TT_PREC_MIXED = 1,    /* contractions on the tensor cores (see tt_round_sum_rand) */
+  TT_PREC_MIXED_FULL = 2 /* as TT_PREC_MIXED, the Algorithm 3 contractions with full digits too:
+                            for sums far smaller than their summands (cancelling combinations) */
 } tt_precision;
 
 /* Library version string and the last error message of the calling thread. */
@@ -127,6 +129,11 @@ int tt_round_sum_rand(int32_t N, int32_t K, const int64_t* dims, const int64_t* 
  *     accurate to 1e-3 tol / N (1e-7 / N in fixed-rank mode), 1 <= s <= 8, so
  *     s = 8 (FP64 class) at tol = 1e-8.
  * QR, the small SVD and the truncation stay float64.
+ * The 2-digit Algorithm 3 contractions assume that the sum does not cancel:
+ * their error is relative to the summands, so for a combination far smaller
+ * than its terms (a Gram-Schmidt step, an iterative solver's updates) the
+ * sketch of the result drowns; TT_PREC_MIXED_FULL gives those contractions
+ * the s digits of the others.
  */
 int tt_mixed_digits(double tol, int32_t N);
 size_t tt_round_sum_rand_workspace(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
@@ -249,6 +256,31 @@ int tt_round_rand(int32_t N, const int64_t* dims, const int64_t* ranks, const do
                   const int64_t* ells, const double* const* sketch, uint64_t seed, double tol,
                   int32_t precision, double* const* out, int64_t* out_ranks, void* workspace,
                   size_t workspace_bytes, void* stream);
+
+/*
+ * float32 storage (no counterpart in the paper, which works in FP64): the same
+ * calls for float32 cores, sketch, outputs and cotangents.
+ * tt_round_rand_f32 converts the cores (and the sketch, when given) to float64
+ * on the device, runs tt_round_rand with `precision` (TT_PREC_MIXED: the
+ * tensor-core contractions with tt_mixed_digits(tol, N) digits, FP32 class and
+ * better) and converts the output cores back to float32 (out[n] holds
+ * l_{n-1} I_n l_n floats).
+ * tt_round_rand_backward_f32 does the same around tt_round_rand_backward, with
+ * every product of the adjoint as the emulated tensor-core GEMM with
+ * tt_mixed_digits(0, N) digits (FP32 class); the thin QRs, the triangular
+ * inverses and the QR-backward steps stay FP64.
+ * Arguments, workspace queries and errors as the float64 versions.
+ */
+int tt_round_rand_f32(int32_t N, const int64_t* dims, const int64_t* ranks, const float* const* cores,
+                      const int64_t* ells, const float* const* sketch, uint64_t seed, double tol, int32_t precision,
+                      float* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes, void* stream);
+size_t tt_round_rand_f32_workspace(int32_t N, const int64_t* dims, const int64_t* ranks, const int64_t* ells,
+                                   double tol, int32_t precision);
+int tt_round_rand_backward_f32(int32_t N, const int64_t* dims, const int64_t* ranks, const float* const* cores,
+                               const int64_t* ells, const float* const* sketch, const float* const* xbar,
+                               float* const* ybar, void* workspace, size_t workspace_bytes, void* stream);
+size_t tt_round_rand_backward_f32_workspace(int32_t N, const int64_t* dims, const int64_t* ranks,
+                                            const int64_t* ells);
 
 /*
  * tt_round_det -- deterministic TT-rounding of a sum: the formed TT-sum of

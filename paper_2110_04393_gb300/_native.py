@@ -56,6 +56,11 @@ SIGNATURES = {
                                           c_i32, P_vp, P_i64, c_vp]),
     "tt_round_rand_backward": (c_i32, [c_i32, P_i64, P_i64, P_vp, P_i64, P_vp, P_vp, P_vp, c_vp, c_size, c_vp]),
     "tt_round_rand_backward_workspace": (c_size, [c_i32, P_i64, P_i64, P_i64]),
+    "tt_round_rand_f32": (c_i32, [c_i32, P_i64, P_i64, P_vp, P_i64, P_vp, c_u64, c_dbl, c_i32, P_vp, P_i64, c_vp,
+                                  c_size, c_vp]),
+    "tt_round_rand_f32_workspace": (c_size, [c_i32, P_i64, P_i64, P_i64, c_dbl, c_i32]),
+    "tt_round_rand_backward_f32": (c_i32, [c_i32, P_i64, P_i64, P_vp, P_i64, P_vp, P_vp, P_vp, c_vp, c_size, c_vp]),
+    "tt_round_rand_backward_f32_workspace": (c_size, [c_i32, P_i64, P_i64, P_i64]),
     "tt_sum_plan_create": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_i64, c_dbl, c_i32, P_vp, c_vp]),
     "tt_sum_plan_run": (c_i32, [c_vp, P_vp, P_dbl, c_u64, P_vp, P_i64, c_vp]),
     "tt_sum_plan_destroy": (c_i32, [c_vp]),

@@ -9,7 +9,9 @@ from . import _native as nat
 
 PREC_FP64 = 0
 PREC_MIXED = 1
-_PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED, PREC_FP64: PREC_FP64, PREC_MIXED: PREC_MIXED}
+PREC_MIXED_FULL = 2
+_PREC = {"fp64": PREC_FP64, "mixed": PREC_MIXED, "mixed_full": PREC_MIXED_FULL, PREC_FP64: PREC_FP64,
+         PREC_MIXED: PREC_MIXED, PREC_MIXED_FULL: PREC_MIXED_FULL}
 
 
 class TTError(RuntimeError):
@@ -37,10 +39,10 @@ def _stream(stream, device):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _check_core(t, name):
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 3
+def _check_core(t, name, dtype=torch.float64):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.dim() == 3
             and t.is_contiguous()):
-        raise ValueError(f"{name}: expected a contiguous float64 CUDA tensor of shape (r0, I, r1)")
+        raise ValueError(f"{name}: expected a contiguous {dtype} CUDA tensor of shape (r0, I, r1)")
 
 
 def tt_version() -> str:
@@ -153,38 +155,50 @@ def tt_round_sum_rand(summands, ells, *, tol=0.0, sketch=None, seed=0, coeffs=No
 
 def tt_round_rand_backward(cores, ells, sketch, xbar, *, workspace=None, stream=None):
     """dL/dY for fixed-sketch RandOrth (Algorithm 5, fixed ranks) given
-    xbar = dL/dX_hat for its output cores; returns tensors shaped like cores."""
+    xbar = dL/dX_hat for its output cores; returns tensors shaped like cores.
+    float32 tensors take the float32 entry point (FP32-class products, FP64
+    QR steps)."""
     N = len(cores)
     device = cores[0].device
+    dt = cores[0].dtype
+    f32 = dt == torch.float32
     dims = [int(c.shape[1]) for c in cores]
     ranks = [int(cores[0].shape[0])] + [int(c.shape[2]) for c in cores]
     for n, c in enumerate(cores):
-        _check_core(c, f"core {n}")
+        _check_core(c, f"core {n}", dt)
     ell = clamp_ranks(dims, ells)
     for n in range(N):
         want = (ell[n], dims[n], ell[n + 1])
-        _check_core(xbar[n], f"xbar core {n}")
+        _check_core(xbar[n], f"xbar core {n}", dt)
         if tuple(xbar[n].shape) != want:
             raise ValueError(f"xbar core {n} has shape {tuple(xbar[n].shape)}, expected {want}")
         if n > 0:
-            _check_core(sketch[n], f"sketch core {n}")
+            _check_core(sketch[n], f"sketch core {n}", dt)
             if tuple(sketch[n].shape) != want:
                 raise ValueError(f"sketch core {n} has shape {tuple(sketch[n].shape)}, expected {want}")
     sk = [sketch[n] if n > 0 else xbar[0] for n in range(N)]     # core 1 of the sketch is not used
     ybar = [torch.empty_like(c) for c in cores]
     L = nat.lib()
     dims_a, ranks_a, ell_a = _i64(dims), _i64(ranks), _i64(ell)
-    nbytes = L.tt_round_rand_backward_workspace(N, dims_a, ranks_a, ell_a)
+    if f32:
+        nbytes = L.tt_round_rand_backward_f32_workspace(N, dims_a, ranks_a, ell_a)
+        fn = L.tt_round_rand_backward_f32
+    else:
+        nbytes = L.tt_round_rand_backward_workspace(N, dims_a, ranks_a, ell_a)
+        fn = L.tt_round_rand_backward
+    if nbytes == 0 and N > 1:
+        raise TTError(1, nat.last_error())
     workspace, wp, wb = _workspace(nbytes, device, workspace)
-    _check(L.tt_round_rand_backward(N, dims_a, ranks_a, _ptrs(cores), ell_a, _ptrs(sk), _ptrs(xbar), _ptrs(ybar),
-                                    wp, wb, _stream(stream, device)))
+    _check(fn(N, dims_a, ranks_a, _ptrs(cores), ell_a, _ptrs(sk), _ptrs(xbar), _ptrs(ybar), wp, wb,
+              _stream(stream, device)))
     return ybar
 
 
 class _RandOrthFixedSketch(torch.autograd.Function):
     @staticmethod
     def forward(ctx, ell, sketch, *cores):
-        out = tt_round_rand(list(cores), ell, sketch=sketch, tol=0.0, precision="fp64")
+        prec = "mixed" if cores[0].dtype == torch.float32 else "fp64"
+        out = tt_round_rand(list(cores), ell, sketch=sketch, tol=0.0, precision=prec)
         ctx.save_for_backward(*cores)
         ctx.ell = list(ell)
         ctx.sketch = sketch
@@ -195,15 +209,16 @@ class _RandOrthFixedSketch(torch.autograd.Function):
         cores = ctx.saved_tensors
         ell = clamp_ranks([int(c.shape[1]) for c in cores], ctx.ell)
         xb = [g.contiguous() if g is not None else
-              torch.zeros((ell[n], cores[n].shape[1], ell[n + 1]), dtype=torch.float64, device=cores[0].device)
+              torch.zeros((ell[n], cores[n].shape[1], ell[n + 1]), dtype=cores[0].dtype, device=cores[0].device)
               for n, g in enumerate(gout)]
         ybar = tt_round_rand_backward(list(cores), ctx.ell, ctx.sketch, xb)
         return (None, None, *ybar)
 
 
 def round_rand_fixed_sketch(cores, ells, sketch):
-    """Differentiable fixed-sketch RandOrth (Algorithm 5, fixed ranks, FP64):
-    forward by tt_round_rand, backward by tt_round_rand_backward."""
+    """Differentiable fixed-sketch RandOrth (Algorithm 5, fixed ranks): forward
+    by tt_round_rand, backward by tt_round_rand_backward (float64, or float32
+    cores and sketch with FP32-class products and FP64 QR steps)."""
     return list(_RandOrthFixedSketch.apply(list(ells), list(sketch), *cores))
 
 
@@ -704,10 +719,44 @@ def tt_round_gram_schmidt(W, basis, ells, *, tol=0.0, sketch=None, seed=0, preci
     return Vn, [float(x) for x in h]
 
 
+def _round_rand_f32(Y, ells, *, tol=0.0, sketch=None, seed=0, precision="mixed", workspace=None, stream=None):
+    N = len(Y)
+    device = Y[0].device
+    dims = [int(c.shape[1]) for c in Y]
+    ranks = [int(Y[0].shape[0])] + [int(c.shape[2]) for c in Y]
+    for n, c in enumerate(Y):
+        _check_core(c, f"core {n}", torch.float32)
+    ell = clamp_ranks(dims, ells)
+    sk_arr = None
+    if sketch is not None:
+        for n in range(1, N):
+            _check_core(sketch[n], f"sketch core {n}", torch.float32)
+            if tuple(sketch[n].shape) != (ell[n], dims[n], ell[n + 1]):
+                raise ValueError(f"sketch core {n} has shape {tuple(sketch[n].shape)}")
+        sk_arr = _ptrs([sketch[n] if n > 0 else Y[0] for n in range(N)])
+    out = [torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float32, device=device) for n in range(N)]
+    L = nat.lib()
+    prec = _PREC[precision]
+    nb = L.tt_round_rand_f32_workspace(N, _i64(dims), _i64(ranks), _i64(ell), float(tol), prec)
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    out_ranks = (ctypes.c_int64 * (N + 1))()
+    _check(L.tt_round_rand_f32(N, _i64(dims), _i64(ranks), _ptrs(Y), _i64(ell), sk_arr, ctypes.c_uint64(int(seed)),
+                               float(tol), prec, _ptrs(out), out_ranks, wp, wb, _stream(stream, device)))
+    r = [int(x) for x in out_ranks]
+    return [out[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)]
+
+
 def tt_round_rand(Y, ells, **kw):
-    """Algorithm 5 (single TT, Randomize-then-Orthogonalize): tt_round_sum_rand with K = 1."""
+    """Algorithm 5 (single TT, Randomize-then-Orthogonalize): tt_round_sum_rand
+    with K = 1. float32 cores take the float32 entry point (precision
+    "mixed" by default: FP32-class tensor-core contractions, FP64 QR)."""
     if kw.get("coeffs") is not None:
         raise ValueError("tt_round_rand takes no coefficients")
+    if Y[0].dtype == torch.float32:
+        kw.setdefault("precision", "mixed")
+        return _round_rand_f32(Y, ells, **kw)
     return tt_round_sum_rand([Y], ells, **kw)
 
 

@@ -22,7 +22,7 @@ namespace ttr {
 
 int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol, int digits,
                    double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev, size_t* coeff_off,
-                   const double* coeff_dev);
+                   const double* coeff_dev, int sketch_digits);
 int mixed_digits(double tol, int N);
 
 namespace {
@@ -207,7 +207,7 @@ static int gs_common(int32_t N, const int64_t* dims, const int64_t* ranks_w, con
                      int32_t k, const int64_t* ranks_v, const double* const* cores_v, const int64_t* ells,
                      const double* const* sketch, uint64_t seed, double tol, int32_t precision, double* const* out,
                      int64_t* out_ranks, double* h, void* ws, size_t ws_bytes, void* stream, size_t* size_only) {
-  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED && precision != TT_PREC_MIXED_FULL) {
     set_error("tt_round_gram_schmidt: unknown precision mode");
     return TT_EINVAL;
   }
@@ -240,7 +240,7 @@ static int gs_common(int32_t N, const int64_t* dims, const int64_t* ranks_w, con
   if (sketch)
     for (int n = 1; n < N; ++n)
       if (!sketch[n]) { set_error("null sketch core pointer"); return TT_EINVAL; }
-  const int digits = (precision == TT_PREC_MIXED) ? mixed_digits(tol, N) : 0;
+  const int digits = (precision != TT_PREC_FP64) ? mixed_digits(tol, N) : 0;
   std::vector<double*> outv(N, nullptr);
   if (out) outv.assign(out, out + N);
   int64_t* rk_dev = nullptr;
@@ -257,7 +257,8 @@ static int gs_common(int32_t N, const int64_t* dims, const int64_t* ranks_w, con
       prof_count_launch(1);
       return int(TT_OK);
     });
-    TTR_TRY(build_sum_rand(P, sketch, seed, tol, digits, outv.data(), ar, sc, &rk_dev, nullptr, coef));
+    // the combination cancels (Z is far smaller than W and the h_j V_j): full digits in Algorithm 3 too
+    TTR_TRY(build_sum_rand(P, sketch, seed, tol, digits, outv.data(), ar, sc, &rk_dev, nullptr, coef, digits));
     // ||Z|| and V_{k+1} = Z / ||Z||: with a tolerance the truncation leaves
     // cores 2..N right-orthogonal (norm in core 1, at its decided ranks);
     // without one the result is left-orthogonal (norm in core N)

@@ -23,7 +23,7 @@ namespace ttr {
 
 int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol, int digits,
                    double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev, size_t* coeff_off,
-                   const double* coeff_dev);
+                   const double* coeff_dev, int sketch_digits);
 int mixed_digits(double tol, int N);
 
 namespace {
@@ -69,6 +69,7 @@ struct SumUnit {
   SumProblem P;
   double tol = 0.0;
   int digits = 0;
+  int sketch_digits = -1;
   double* in_buf = nullptr;
   double* out_buf = nullptr;
   std::vector<double*> outs;
@@ -112,7 +113,8 @@ int unit_init(SumUnit* u, int32_t N, int32_t K, const int64_t* dims, const int64
   TTR_TRY(validate_sum(N, K, dims, ranks, nullptr, nullptr, ells, false, &u->P));
   SumProblem& P = u->P;
   u->tol = tol;
-  u->digits = (precision == TT_PREC_MIXED) ? mixed_digits(tol, N) : 0;
+  u->digits = (precision != TT_PREC_FP64) ? mixed_digits(tol, N) : 0;
+  u->sketch_digits = (precision == TT_PREC_MIXED_FULL) ? u->digits : -1;
   std::vector<int64_t> in_sizes, in_off, out_sizes, out_off;
   int64_t tot = 0;
   for (int j = 0; j < K; ++j)
@@ -176,7 +178,7 @@ int unit_init(SumUnit* u, int32_t N, int32_t K, const int64_t* dims, const int64
   }
   BuildFn build = [u](Arena& ar, Schedule& sc) {
     return build_sum_rand(u->P, nullptr, 0, u->tol, u->digits, u->outs.data(), ar, sc, &u->rk_dev, &u->coeff_off,
-                          nullptr);
+                          nullptr, u->sketch_digits);
   };
   return plan_prepare(build, &u->gp);
 }
@@ -409,7 +411,7 @@ int tt_sum_plan_create(int32_t N, int32_t K, const int64_t* dims, const int64_t*
     return TT_EINVAL;
   }
   *plan = nullptr;
-  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED && precision != TT_PREC_MIXED_FULL) {
     set_error("tt_sum_plan_create: unknown precision mode");
     return TT_EINVAL;
   }
@@ -515,7 +517,7 @@ int tt_batch_plan_create(int32_t B, const tt_sum_problem* probs, int32_t precisi
     return TT_EINVAL;
   }
   *plan = nullptr;
-  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED && precision != TT_PREC_MIXED_FULL) {
     set_error("tt_batch_plan_create: unknown precision mode");
     return TT_EINVAL;
   }

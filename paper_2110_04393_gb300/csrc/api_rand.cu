@@ -473,13 +473,16 @@ constexpr int kSketchDigits = 2;
 
 int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol, int digits,
                    double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev, size_t* coeff_off,
-                   const double* coeff_dev) {
+                   const double* coeff_dev, int sketch_digits) {
   // digits == 0: every contraction in FP64. Else every contraction runs on the
   // tensor cores (emulated GEMM): the core updates and projections with
   // `digits` bf16 digits, the partial contractions of Algorithm 3 with
-  // kSketchDigits (their rounding errors only change the sketch: the sketched
-  // core stays in the range of the unfolding).
-  const int dw = digits > 0 ? kSketchDigits : 0;
+  // sketch_digits (< 0: kSketchDigits). Their rounding errors only change the
+  // sketch (the sketched core stays in the range of the unfolding), which is
+  // harmless as long as the sum does not cancel: for a sum far smaller than
+  // its summands (a Gram-Schmidt combination) or a fixed-sketch rounding that
+  // is differentiated, callers pass sketch_digits = digits.
+  const int dw = digits > 0 ? (sketch_digits < 0 ? kSketchDigits : sketch_digits) : 0;
   auto big = [&](std::vector<GemmDesc> g) {
     if (digits > 0) sc.gemm_tc(std::move(g), digits); else sc.gemm(std::move(g));
   };
@@ -661,11 +664,12 @@ __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, 
                            void* stream, size_t* size_only) {
   SumProblem P;
   TTR_TRY(validate_sum(N, K, dims, ranks, cores, coeffs, ells, size_only == nullptr, &P));
-  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED && precision != TT_PREC_MIXED_FULL) {
     set_error("unknown precision mode");
     return TT_EINVAL;
   }
-  const int digits = (precision == TT_PREC_MIXED) ? mixed_digits(tol, N) : 0;
+  const int digits = (precision != TT_PREC_FP64) ? mixed_digits(tol, N) : 0;
+  const int sketch_digits = (precision == TT_PREC_MIXED_FULL) ? digits : -1;
   if (size_only == nullptr) {
     if (!out || !out_ranks) { set_error("null output arrays"); return TT_EINVAL; }
     for (int n = 0; n < N; ++n)
@@ -678,7 +682,8 @@ __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, 
   std::vector<double*> out_v(N, nullptr);
   if (out) out_v.assign(out, out + N);
   BuildFn build = [&](Arena& ar, Schedule& sc) {
-    return build_sum_rand(P, sketch, seed, tol, digits, out_v.data(), ar, sc, &rk_dev, nullptr, nullptr);
+    return build_sum_rand(P, sketch, seed, tol, digits, out_v.data(), ar, sc, &rk_dev, nullptr, nullptr,
+                          sketch_digits);
   };
   if (size_only) return plan_workspace_bytes(build, size_only);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -787,6 +792,97 @@ size_t tt_truncate_lorth_workspace(int32_t N, const int64_t* dims, const int64_t
                                    int64_t max_rank) {
   size_t b = 0;
   if (truncate_common(N, dims, ranks, nullptr, tol, max_rank, nullptr, nullptr, 0, nullptr, &b) != TT_OK) return 0;
+  return b;
+}
+
+// float32 storage at the boundary: cores (and sketch) converted to float64 on
+// the device, the rounding of tt_round_rand, the result converted back.
+static int rand_f32_common(int32_t N, const int64_t* dims, const int64_t* ranks, const float* const* cores,
+                           const int64_t* ells, const float* const* sketch, uint64_t seed, double tol,
+                           int32_t precision, float* const* out, int64_t* out_ranks, void* workspace,
+                           size_t ws_bytes, void* stream, size_t* size_only) {
+  SumProblem P;
+  TTR_TRY(validate_sum(N, 1, dims, ranks, nullptr, nullptr, ells, false, &P));
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED && precision != TT_PREC_MIXED_FULL) {
+    set_error("unknown precision mode");
+    return TT_EINVAL;
+  }
+  if (!size_only) {
+    if (!cores || !out || !out_ranks) { set_error("null core or output arrays"); return TT_EINVAL; }
+    for (int n = 0; n < N; ++n)
+      if (!cores[n] || !out[n]) { set_error("null core pointer"); return TT_EINVAL; }
+    if (sketch)
+      for (int n = 1; n < N; ++n)
+        if (!sketch[n]) { set_error("null sketch core pointer"); return TT_EINVAL; }
+  }
+  const int digits = (precision != TT_PREC_FP64) ? mixed_digits(tol, N) : 0;
+  int64_t* rk_dev = nullptr;
+  std::vector<int64_t> rk(N + 1);
+  BuildFn build = [&](Arena& ar, Schedule& sc) {
+    SumProblem Q = P;
+    std::vector<double*> Yd(N), Od(N, nullptr), Xo(N);
+    std::vector<int64_t> ny(N), nx(N);
+    for (int n = 0; n < N; ++n) {
+      ny[n] = P.R[n] * P.I[n] * P.R[n + 1];
+      nx[n] = P.ell[n] * P.I[n] * P.ell[n + 1];
+      Yd[n] = ar.take<double>(ny[n]);
+      Xo[n] = ar.take<double>(nx[n]);
+      if (n > 0) Od[n] = ar.take<double>(nx[n]);   // sized whether or not a sketch is given
+      Q.cores[n] = Yd[n];
+    }
+    for (int n = 0; n < N; ++n) {
+      const float* yc = size_only ? nullptr : cores[n];
+      const float* oc = (size_only || !sketch || n == 0) ? nullptr : sketch[n];
+      double *yd = Yd[n], *od = Od[n];
+      const int64_t a = ny[n], b = nx[n];
+      sc.add([=](cudaStream_t s) -> int {
+        TTR_TRY(cvt_f32_f64_launch(yc, yd, a, s));
+        return cvt_f32_f64_launch(oc, od, b, s);
+      });
+    }
+    std::vector<const double*> Oc(Od.begin(), Od.end());
+    // the fixed-sketch rounding itself (what its adjoint differentiates): full digits in Algorithm 3 too
+    TTR_TRY(build_sum_rand(Q, sketch ? Oc.data() : nullptr, seed, tol, digits, Xo.data(), ar, sc, &rk_dev, nullptr,
+                           nullptr, digits));
+    for (int n = 0; n < N; ++n) {
+      float* o = size_only ? nullptr : out[n];
+      const double* x = Xo[n];
+      const int64_t b = nx[n];
+      sc.add([=](cudaStream_t s) -> int { return cvt_f64_f32_launch(x, o, b, s); });
+    }
+    if (tol > 0.0) {
+      int64_t* rkd = rk_dev;
+      int64_t* rkh = rk.data();
+      sc.add([rkd, rkh, N](cudaStream_t st) -> int {
+        if (rkd) TTR_CHECK_CUDA(cudaMemcpyAsync(rkh, rkd, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+        return int(TT_OK);
+      });
+    }
+    return int(TT_OK);
+  };
+  if (size_only) return plan_workspace_bytes(build, size_only);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dstat = 0;
+  TTR_TRY(plan_execute(build, workspace, ws_bytes, s, &dstat));
+  TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  TTR_TRY(status_code(dstat, "tt_round_rand_f32"));
+  for (int n = 0; n <= N; ++n) out_ranks[n] = tol > 0.0 ? rk[n] : P.ell[n];
+  return TT_OK;
+}
+
+int tt_round_rand_f32(int32_t N, const int64_t* dims, const int64_t* ranks, const float* const* cores,
+                      const int64_t* ells, const float* const* sketch, uint64_t seed, double tol, int32_t precision,
+                      float* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes, void* stream) {
+  return rand_f32_common(N, dims, ranks, cores, ells, sketch, seed, tol, precision, out, out_ranks, workspace,
+                         workspace_bytes, stream, nullptr);
+}
+
+size_t tt_round_rand_f32_workspace(int32_t N, const int64_t* dims, const int64_t* ranks, const int64_t* ells,
+                                   double tol, int32_t precision) {
+  size_t b = 0;
+  if (rand_f32_common(N, dims, ranks, nullptr, ells, nullptr, 0, tol, precision, nullptr, nullptr, nullptr, 0,
+                      nullptr, &b) != TT_OK)
+    return 0;
   return b;
 }
 

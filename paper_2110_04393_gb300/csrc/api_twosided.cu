@@ -249,7 +249,7 @@ static int twosided_common(int32_t N, int32_t K, const int64_t* dims, const int6
                            const int64_t* rhos, const double* const* skL, const double* const* skR, uint64_t seed,
                            int32_t precision, double* const* out, int64_t* out_ranks, void* workspace,
                            size_t ws_bytes, void* stream, size_t* size_only, bool orth = false, double tol = 0.0) {
-  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED && precision != TT_PREC_MIXED_FULL) {
     set_error("tt_round_twosided: unknown precision mode");
     return TT_EINVAL;
   }
@@ -267,7 +267,7 @@ static int twosided_common(int32_t N, int32_t K, const int64_t* dims, const int6
   if (!size_only && (!out || !out_ranks)) { set_error("null outputs"); return TT_EINVAL; }
   std::vector<double*> outv(N, nullptr);
   if (out) outv.assign(out, out + N);
-  const int digits = (precision == TT_PREC_MIXED) ? mixed_digits(orth ? tol : 0.0, N) : 0;
+  const int digits = (precision != TT_PREC_FP64) ? mixed_digits(orth ? tol : 0.0, N) : 0;
   int64_t* rk_dev = nullptr;
   std::vector<int64_t> rk(N + 1);
   const bool trunc = orth && tol > 0.0;

@@ -141,6 +141,9 @@ int or_flag_launch(int* dst, const int* src, int bit, cudaStream_t s);
 // dst[0] := 1 (device flag)
 int set_flag_launch(int* dst, cudaStream_t s);
 int fill_launch(double* p, int64_t n, double v, cudaStream_t s);
+// float32 <-> float64 conversion of n entries (device arrays)
+int cvt_f32_f64_launch(const float* src, double* dst, int64_t n, cudaStream_t s);
+int cvt_f64_f32_launch(const double* src, float* dst, int64_t n, cudaStream_t s);
 // dst[0..n) = src[0..n) unless skip_if is set and *skip_if != 0 (device flag)
 int copy_if_launch(double* dst, const double* src, int64_t n, const int* skip_if, cudaStream_t s);
 // Adjoint helpers: X = T^{-1} (upper triangular, k x k), A := tril(A) + tril(A, -1)^T, y += x.

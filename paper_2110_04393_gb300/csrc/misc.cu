@@ -178,6 +178,32 @@ __global__ void or_flag_kernel(int* dst, const int* src, int bit) {
   if (threadIdx.x == 0 && src[0]) dst[0] |= bit;
 }
 }  // namespace
+__global__ void cvt_f32_f64_kernel(const float* __restrict__ src, double* __restrict__ dst, int64_t n) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    dst[e] = double(src[e]);
+}
+__global__ void cvt_f64_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    dst[e] = float(src[e]);
+}
+int cvt_f32_f64_launch(const float* src, double* dst, int64_t n, cudaStream_t s) {
+  if (!src || !dst || n <= 0) return TT_OK;
+  const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4 * num_sms())));
+  TTR_PREFER_SHARED(cvt_f32_f64_kernel);
+  cvt_f32_f64_kernel<<<g, 256, 0, s>>>(src, dst, n);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+int cvt_f64_f32_launch(const double* src, float* dst, int64_t n, cudaStream_t s) {
+  if (!src || !dst || n <= 0) return TT_OK;
+  const unsigned g = unsigned(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4 * num_sms())));
+  TTR_PREFER_SHARED(cvt_f64_f32_kernel);
+  cvt_f64_f32_kernel<<<g, 256, 0, s>>>(src, dst, n);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
 __global__ void copy_if_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t n,
                                const int* skip_if) {
   if (skip_if && __ldcg(skip_if) != 0) return;

@@ -59,6 +59,8 @@ def tt_gmres(terms, Minv, f, *, tol=1e-8, maxit=30, ell_cap=40, round_tol=None, 
     cores) to relative residual tol. Returns (x cores, residual estimates per
     iteration, Krylov vector ranks per iteration)."""
     rt = 0.1 * tol if round_tol is None else round_tol
+    # the Krylov combinations cancel: in mixed precision their sketches take full digits too
+    sum_prec = "mixed_full" if precision == "mixed" else precision
     dims = [int(c.shape[1]) for c in f]
     count = [seed0]
 
@@ -79,7 +81,7 @@ def tt_gmres(terms, Minv, f, *, tol=1e-8, maxit=30, ell_cap=40, round_tol=None, 
         Y = precondition(Minv, V[k])
         summands = apply_terms(terms, Y)
         W = api.tt_round_sum_rand(summands, _sketch_ranks(summands, dims, ell_cap), tol=rt, seed=seed(),
-                                  precision=precision)
+                                  precision=sum_prec)
         W = [c.contiguous() for c in W]
         Vn, h = api.tt_round_gram_schmidt(W, V, _sketch_ranks([W] + V, dims, ell_cap), tol=rt, seed=seed(),
                                           precision=precision)
@@ -105,5 +107,5 @@ def tt_gmres(terms, Minv, f, *, tol=1e-8, maxit=30, ell_cap=40, round_tol=None, 
     for i in range(m - 1, -1, -1):              # back substitution with the rotated triangle
         y[i] = (g[i] - sum(R[i][j] * y[j] for j in range(i + 1, m))) / R[i][i]
     U = api.tt_round_sum_rand(V[:m], _sketch_ranks(V[:m], dims, ell_cap), coeffs=y, tol=rt, seed=seed(),
-                              precision=precision)
+                              precision=sum_prec)
     return precondition(Minv, [c.contiguous() for c in U]), res, ranks

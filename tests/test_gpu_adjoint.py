@@ -85,3 +85,64 @@ def test_directional_central_difference():
         g = to_host(tt.tt_round_rand_backward(cores, el, Omd, to_dev(Xbar)))
         an = sum(float(np.sum(a * v)) for a, v in zip(g, Vd))
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (trial, fd, an)
+
+
+# ------------------------------------------------------------- float32 (cfg 4)
+
+def _f32(cores):
+    return [torch.from_numpy(np.ascontiguousarray(c, dtype=np.float32)).cuda() for c in cores]
+
+
+def _as64(cores):
+    return [np.asarray(c, dtype=np.float32).astype(np.float64) for c in cores]
+
+
+def test_f32_forward_and_adjoint_at_cfg4_size():
+    """N = 16, I = 32, R = 64 rounded to l = 16 with float32 storage: the
+    forward and the adjoint within 1e-4 of the oracle's FP64 results on the
+    same (float32-rounded) inputs and sketch."""
+    N, I, R, ell, rT = 16, 32, 64, 16, 8
+    dims, Y, el, Om, T = _case(N, I, R, ell, rT, 140)
+    Y32, Om32 = _as64(Y), _as64(Om)
+    Xg = tt.tt_round_rand(_f32(Y), el, sketch=_f32(Om), tol=0.0)
+    assert all(c.dtype == torch.float32 for c in Xg)
+    Xg64 = [c.double().cpu().numpy() for c in Xg]
+    Xo = O.round_randorth(Y32, Om32)
+    assert O.diff_norm(Xg64, Xo) <= 1e-4 * O.norm(Xo)
+    # the cotangent of the GPU's own output cores (their QR gauge is the one the
+    # backward recomputes; the gradient itself does not depend on the gauge)
+    EL, ER = _environments(Xg64, T)
+    Xbar = [np.einsum("ac,cid,bd->aib", EL[n], T[n], ER[n + 1]) for n in range(N)]
+    Yb = tt.tt_round_rand_backward(_f32(Y), el, _f32(Om), _f32(Xbar))
+    assert all(c.dtype == torch.float32 for c in Yb)
+    Yo = randorth_adjoint(Y32, Om32, T)
+    assert _rel([c.double().cpu().numpy() for c in Yb], Yo) <= 1e-4
+
+
+def test_f32_autograd_and_directional_fd():
+    N, I, R, ell, rT = 6, 8, 5, 3, 2
+    dims, Y, el, Om, T = _case(N, I, R, ell, rT, 141)
+    Y32, Om32 = _as64(Y), _as64(Om)
+    cores = [c.requires_grad_(True) for c in _f32(Y)]
+    X = tt.round_rand_fixed_sketch(cores, el, _f32(Om))
+    Td = [c.float() for c in to_dev(T)]
+    E = torch.ones((1, 1), dtype=torch.float32, device="cuda")
+    for x, t in zip(X, Td):
+        E = torch.einsum("ab,aic,bid->cd", E, x, t)
+    E[0, 0].backward()
+    g = [c.grad.double().cpu().numpy() for c in cores]
+    assert _rel(g, randorth_adjoint(Y32, Om32, T)) <= 1e-4
+    # FP64 central differences (h = 1e-6) of the FP64 GPU forward on the rounded inputs
+    Omd, Td64 = to_dev(Om32), to_dev(T)
+    rng = np.random.default_rng(6)
+    for trial in range(2):
+        V = [rng.standard_normal(c.shape) for c in Y]
+        h = 1e-6
+
+        def L(sign):
+            Yp = [torch.from_numpy(c + sign * h * v).cuda() for c, v in zip(Y32, V)]
+            return float(_inner_torch(tt.tt_round_rand(Yp, el, sketch=Omd, tol=0.0), Td64))
+
+        fd = (L(1.0) - L(-1.0)) / (2 * h)
+        an = sum(float(np.sum(a * v)) for a, v in zip(g, V))
+        assert abs(fd - an) <= 1e-4 * max(1.0, abs(fd)), (trial, fd, an)
