@@ -579,10 +579,12 @@ def run_batched(a):
                 for pr in probs)
     in_bytes = sum(c.numel() * 8 for Ys in batch for Y in Ys for c in Y)
     t0 = time.perf_counter()
-    width, tune = tt.tune_batch_width(probs, batch, precision="mixed", candidates=(16, 64, 256), reps=1)
+    (width, qr_ctas), tune = tt.tune_batch_schedule(probs, batch, precision="mixed", widths=(1, 2, 4),
+                                                    qr_ctas=(4, 8, 16), reps=1,
+                                                    cache_path=os.path.join(ROOT, ".bench", "batch_tuning.json"))
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
-    plan = tt.BatchRoundingPlan(probs, precision="mixed", width=width)
+    plan = tt.BatchRoundingPlan(probs, precision="mixed", width=width, qr_ctas=qr_ctas)
     t_plan = time.perf_counter() - t0
     for w in range(a.warmup):
         plan(batch, seeds=[1000 * w + b for b in range(len(probs))])
@@ -607,8 +609,9 @@ def run_batched(a):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (mixed: emulated FP64 tensor-core contractions)",
         "data": "synthetic", "config": dict(BATCHED, inputs_gb=in_bytes / 1e9, l2="inputs larger than L2",
                                             algorithmic_gflop=flops / 1e9),
-        "schedule": {"width": width, "tuning_ms": tune, "tuning_s": t_tune, "plan_s": t_plan,
-                     "launches_per_step": plan.launches},
+        "schedule": {"fused": plan.fused, "width": width, "qr_ctas": qr_ctas,
+                     "tuning_ms": {f"width={w},qr_ctas={q}": v for (w, q), v in tune.items()},
+                     "tuning_s": t_tune, "plan_s": t_plan, "launches_per_step": plan.launches},
         "input_read_gbs": gbs, "input_read_frac_of_hbm": gbs / hbm, "clocks": clk.summary()}), flush=True)
     plan.close()
 

@@ -218,16 +218,15 @@ int tt_sum_plan_run_host(tt_sum_plan* plan, const double* h_in, const double* co
 
 /*
  * Batched plans: B independent sum roundings (the uneven sums of TT-GMRES,
- * Section 4.2) in one CUDA graph. Problem b (its N, K, dims, ranks K x (N+1),
- * ells N+1 and tol, as for tt_sum_plan_create) runs on chain b mod width of the
- * graph; the chains are independent, so the kernels of different problems run
- * concurrently and fill each other's idle SMs. width (1..B) is a schedule
- * parameter that changes no result (tt_batch_plan_* callers may tune it).
+ * Section 4.2) in one CUDA graph. Problem b is given by its N, K, dims, ranks
+ * K x (N+1), ells N+1 and tol, as for tt_sum_plan_create; how the problems are
+ * scheduled (grouped launches over many problems, or one schedule per problem
+ * on parallel chains) is described at tt_batch_plan_create_sched.
+ * tt_batch_plan_create(..., width, ...) takes the default schedule for width.
  * tt_batch_plan_run: cores = the problems' core pointer arrays concatenated
  * (problem b: K_b*N_b device pointers as in tt_sum_plan_run), seeds = B sketch
  * seeds (host; NULL = 0, 1, ..., B-1), out = the problems' N_b output pointers
  * concatenated, out_ranks = the problems' N_b+1 ranks concatenated (host).
- * Every problem's result is bit-wise that of tt_round_sum_rand with its seed.
  * The call waits for the stream only if some problem has tol > 0.
  */
 typedef struct {
@@ -240,6 +239,32 @@ typedef struct {
 typedef struct tt_batch_plan tt_batch_plan;
 int tt_batch_plan_create(int32_t B, const tt_sum_problem* probs, int32_t precision, int32_t width,
                          tt_batch_plan** plan, void* stream);
+/*
+ * Schedule of a batched plan (tt_batch_plan_create uses {width, 8, -1}):
+ *   fused = 1 (or -1 with every problem at fixed ranks, tol <= 0, and target
+ *   ranks <= 96): the problems are split into `width` groups of consecutive
+ *   problems; each group runs as ONE chain of grouped launches -- every launch
+ *   covers all problems of its group (the Algorithm 3 products of every
+ *   summand of every problem, all sketch cores, every core update, sketch and
+ *   projection, and each bond's thin QRs as one batched Cholesky-QR chain of
+ *   6 launches with about qr_ctas CTAs per QR) -- so a group takes a few
+ *   hundred launches whatever its size; the groups' chains run concurrently.
+ *   Results equal tt_round_sum_rand's with the same seed to rounding (the
+ *   grouped products and the batched QR sum in another order); a batched QR
+ *   that breaks down is reported as TT_ESINGULAR (no Householder fallback).
+ *   fused = 0 (or -1 otherwise): one schedule per problem, problem b on chain
+ *   b mod width, results bit-wise those of tt_round_sum_rand.
+ * width and qr_ctas change no mathematics (the autotuner of the Python
+ * binding tries several).
+ */
+typedef struct {
+  int32_t width;
+  int32_t qr_ctas;
+  int32_t fused;
+} tt_batch_schedule;
+int tt_batch_plan_create_sched(int32_t B, const tt_sum_problem* probs, int32_t precision,
+                               const tt_batch_schedule* sched, tt_batch_plan** plan, void* stream);
+int tt_batch_plan_is_fused(const tt_batch_plan* plan);
 int tt_batch_plan_run(tt_batch_plan* plan, const double* const* cores, const uint64_t* seeds, double* const* out,
                       int64_t* out_ranks, void* stream);
 int tt_batch_plan_destroy(tt_batch_plan* plan);

@@ -73,6 +73,8 @@ SIGNATURES = {
     "tt_sum_plan_host_layout": (c_i32, [c_vp, P_i64, P_i64, P_i64, P_i64]),
     "tt_sum_plan_run_host": (c_i32, [c_vp, c_vp, P_dbl, c_u64, c_vp, P_i64, c_vp]),
     "tt_batch_plan_create": (c_i32, [c_i32, c_vp, c_i32, c_i32, P_vp, c_vp]),
+    "tt_batch_plan_create_sched": (c_i32, [c_i32, c_vp, c_i32, c_vp, P_vp, c_vp]),
+    "tt_batch_plan_is_fused": (c_i32, [c_vp]),
     "tt_batch_plan_run": (c_i32, [c_vp, P_vp, c_vp, P_vp, P_i64, c_vp]),
     "tt_batch_plan_destroy": (c_i32, [c_vp]),
     "tt_batch_plan_launches": (c_i64, [c_vp]),

@@ -330,12 +330,19 @@ class _SumProblem(ctypes.Structure):
                 ("tol", ctypes.c_double)]
 
 
-class BatchRoundingPlan:
-    """B independent sum roundings captured in one CUDA graph (problem b on
-    chain b mod width). problems: list of dicts with keys dims, summand_ranks
-    (K lists of N+1 ranks), ells (N+1) and optionally tol (default 0)."""
+class _BatchSchedule(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("qr_ctas", ctypes.c_int32), ("fused", ctypes.c_int32)]
 
-    def __init__(self, problems, *, precision="mixed", width=1, device=None, stream=None):
+
+class BatchRoundingPlan:
+    """B independent sum roundings captured in one CUDA graph. problems: list
+    of dicts with keys dims, summand_ranks (K lists of N+1 ranks), ells (N+1)
+    and optionally tol (default 0). Schedule (no effect on the mathematics):
+    fused=-1 groups the launches of all problems (fixed ranks) into `width`
+    chains with about qr_ctas CTAs per thin QR; fused=0 runs one schedule per
+    problem on `width` chains (see tt_batch_plan_create_sched)."""
+
+    def __init__(self, problems, *, precision="mixed", width=1, qr_ctas=8, fused=-1, device=None, stream=None):
         self.device = torch.device(device or "cuda")
         self.problems = []
         keep = []
@@ -350,10 +357,17 @@ class BatchRoundingPlan:
             arr[b] = _SumProblem(len(dims), len(R), a_d, a_r, a_e, tol)
             self.problems.append(dict(dims=dims, summand_ranks=R, ell=ell, tol=tol))
         self.width = int(width)
+        self.qr_ctas = int(qr_ctas)
+        sched = _BatchSchedule(self.width, self.qr_ctas, int(fused))
         h = ctypes.c_void_p()
-        _check(nat.lib().tt_batch_plan_create(len(problems), ctypes.cast(arr, ctypes.c_void_p), _PREC[precision],
-                                              self.width, ctypes.byref(h), _stream(stream, self.device)))
+        _check(nat.lib().tt_batch_plan_create_sched(len(problems), ctypes.cast(arr, ctypes.c_void_p),
+                                                    _PREC[precision], ctypes.byref(sched), ctypes.byref(h),
+                                                    _stream(stream, self.device)))
         self._h = h
+
+    @property
+    def fused(self):
+        return bool(nat.lib().tt_batch_plan_is_fused(self._h))
 
     @property
     def launches(self):
@@ -407,31 +421,67 @@ class BatchRoundingPlan:
 _TUNED = {}
 
 
-def tune_batch_width(problems, batch, *, precision="mixed", candidates=(8, 32, 128), reps=2, stream=None):
-    """Autotuner of the batched schedule: captures the batch at each candidate
-    width, times `reps` replays with CUDA events and returns (best width,
-    {width: ms}); the choice is cached per problem set in this process."""
-    key = (precision, tuple((tuple(p["dims"]), tuple(tuple(r) for r in p["summand_ranks"]), tuple(p["ells"]),
-                             float(p.get("tol", 0.0))) for p in problems))
+def _problem_key(problems, precision):
+    import hashlib
+    txt = repr((precision, [(tuple(p["dims"]), tuple(tuple(r) for r in p["summand_ranks"]), tuple(p["ells"]),
+                             float(p.get("tol", 0.0))) for p in problems]))
+    return hashlib.sha1(txt.encode()).hexdigest()
+
+
+def tune_batch_schedule(problems, batch, *, precision="mixed", widths=(1, 2, 4), qr_ctas=(4, 8, 16), reps=2,
+                        cache_path=None, stream=None):
+    """Autotuner of the batched schedule: captures the batch for every
+    (width, qr_ctas) candidate of the fused grouped-launch schedule, times
+    `reps` replays with CUDA events and returns ((width, qr_ctas), {candidate:
+    ms}). The choice is cached per problem set (sha1 of the shapes, ranks and
+    precision) in this process and, with cache_path, in that JSON file."""
+    import json
+    import os
+    key = _problem_key(problems, precision)
     if key in _TUNED:
         return _TUNED[key]
+    if cache_path and os.path.exists(cache_path):
+        try:
+            db = json.load(open(cache_path))
+            if key in db:
+                best = tuple(db[key]["best"])
+                _TUNED[key] = (best, {tuple(map(int, k.split(","))): v for k, v in db[key]["ms"].items()})
+                return _TUNED[key]
+        except (ValueError, KeyError, OSError):
+            pass
     B = len(problems)
     times = {}
-    for w in sorted({max(1, min(int(c), B)) for c in candidates}):
-        plan = BatchRoundingPlan(problems, precision=precision, width=w)
-        plan(batch)                                   # warm-up replay
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            plan(batch)
-        e1.record()
-        torch.cuda.synchronize()
-        times[w] = e0.elapsed_time(e1) / reps
-        plan.close()
+    for w in sorted({max(1, min(int(c), B)) for c in widths}):
+        for q in sorted({int(c) for c in qr_ctas}):
+            plan = BatchRoundingPlan(problems, precision=precision, width=w, qr_ctas=q)
+            plan(batch)                                   # warm-up replay
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                plan(batch)
+            e1.record()
+            torch.cuda.synchronize()
+            times[(w, q)] = e0.elapsed_time(e1) / reps
+            plan.close()
     best = min(times, key=times.get)
     _TUNED[key] = (best, times)
+    if cache_path:
+        try:
+            db = json.load(open(cache_path)) if os.path.exists(cache_path) else {}
+        except (ValueError, OSError):
+            db = {}
+        db[key] = {"best": list(best), "ms": {f"{w},{q}": t for (w, q), t in times.items()}}
+        os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
+        json.dump(db, open(cache_path, "w"), indent=1)
     return _TUNED[key]
+
+
+def tune_batch_width(problems, batch, *, precision="mixed", candidates=(1, 2, 4), reps=2, stream=None):
+    """tune_batch_schedule over the width only (qr_ctas = 8): (best width, {width: ms})."""
+    (w, _), times = tune_batch_schedule(problems, batch, precision=precision, widths=candidates, qr_ctas=(8,),
+                                        reps=reps, stream=stream)
+    return w, {k[0]: v for k, v in times.items()}
 
 
 def _sum_args(summands):

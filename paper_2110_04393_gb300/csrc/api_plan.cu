@@ -21,6 +21,8 @@
 
 namespace ttr {
 
+int build_sum_rand_batch(const std::vector<SumProblem>& Ps, const uint64_t* seeds_dev, int digits, int qr_ctas,
+                         const std::vector<std::vector<double*>>& outs, Arena& ar, Schedule& sc);
 int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t seed, double tol, int digits,
                    double* const* out, Arena& ar, Schedule& sc, int64_t** rk_dev, size_t* coeff_off,
                    const double* coeff_dev, int sketch_digits);
@@ -389,6 +391,277 @@ int unit_graph_run(UnitGraph* g, cudaStream_t s, int64_t* const* out_ranks) {
   return TT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Fused batches: groups of consecutive problems, each rounded by one schedule
+// of grouped launches (build_sum_rand_batch); one gather and one scatter
+// launch per group; the groups run on parallel branches of one graph.
+struct FusedUnit {
+  std::vector<SumProblem> P;
+  std::vector<std::vector<double*>> outs;
+  int digits = 0, qr_ctas = 8;
+  double* in_buf = nullptr;
+  double* out_buf = nullptr;
+  void* tables = nullptr;
+  CopyBlock* gblocks = nullptr;
+  CopyBlock* sblocks = nullptr;
+  int64_t* in_off = nullptr;
+  int64_t* out_off = nullptr;
+  int ngb = 0, nsb = 0;
+  size_t src0 = 0, dst0 = 0, b0 = 0;     // first core pointer, output pointer and seed of the group
+  GraphPlan gp;
+  int* h_status = nullptr;
+};
+
+struct FusedGraph {
+  std::vector<FusedUnit*> units;
+  int B = 0;
+  size_t n_src = 0, n_dst = 0;           // pointers staged per run
+  size_t stage_bytes = 0;
+  void* d_stage = nullptr;
+  void* h_stage = nullptr;
+  int* h_status = nullptr;
+  cudaEvent_t staged = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<ProfPair> prof;
+  int64_t kernels = 0;
+  std::vector<std::vector<int64_t>> ell;   // per problem, the clamped sketch ranks
+  std::vector<int> N, K;
+};
+
+void fused_free(FusedGraph* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (auto& q : g->prof) {
+    cudaEventDestroy(q.e0);
+    cudaEventDestroy(q.e1);
+  }
+  for (FusedUnit* u : g->units) {
+    plan_free(&u->gp);
+    if (u->in_buf) cudaFree(u->in_buf);
+    if (u->out_buf) cudaFree(u->out_buf);
+    if (u->tables) cudaFree(u->tables);
+    delete u;
+  }
+  g->units.clear();
+  if (g->d_stage) cudaFree(g->d_stage);
+  if (g->h_stage) cudaFreeHost(g->h_stage);
+  if (g->h_status) cudaFreeHost(g->h_status);
+  if (g->staged) cudaEventDestroy(g->staged);
+  *g = FusedGraph{};
+}
+
+int fused_unit_init(FusedUnit* u, const std::vector<SumProblem>& probs, size_t b0, size_t b1, size_t src0,
+                    size_t dst0, int digits, int qr_ctas, const uint64_t* seeds_dev) {
+  u->P.assign(probs.begin() + b0, probs.begin() + b1);
+  u->digits = digits;
+  u->qr_ctas = qr_ctas;
+  u->src0 = src0;
+  u->dst0 = dst0;
+  u->b0 = b0;
+  std::vector<int64_t> in_sizes, in_off, out_sizes, out_off;
+  int64_t it = 0, ot = 0;
+  for (const SumProblem& P : u->P) {
+    for (int j = 0; j < P.K; ++j)
+      for (int n = 1; n <= P.N; ++n) {
+        in_off.push_back(it);
+        in_sizes.push_back(P.r(j, n - 1) * P.I[n - 1] * P.r(j, n));
+        it += in_sizes.back();
+      }
+    for (int n = 1; n <= P.N; ++n) {
+      out_off.push_back(ot);
+      out_sizes.push_back(P.ell[n - 1] * P.I[n - 1] * P.ell[n]);
+      ot += out_sizes.back();
+    }
+  }
+  if (cudaMalloc(&u->in_buf, sizeof(double) * std::max<int64_t>(it, 1)) != cudaSuccess ||
+      cudaMalloc(&u->out_buf, sizeof(double) * std::max<int64_t>(ot, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("batch plan: buffer allocation failed");
+    return TT_ENOMEM;
+  }
+  size_t ci = 0, oi = 0;
+  u->outs.clear();
+  for (SumProblem& P : u->P) {
+    P.cores.assign(size_t(P.K) * P.N, nullptr);
+    for (size_t c = 0; c < size_t(P.K) * P.N; ++c) P.cores[c] = u->in_buf + in_off[ci++];
+    std::vector<double*> o(P.N);
+    for (int n = 0; n < P.N; ++n) o[n] = u->out_buf + out_off[oi++];
+    u->outs.push_back(o);
+  }
+  const auto gb = copy_blocks(in_sizes), sb = copy_blocks(out_sizes);
+  u->ngb = int(gb.size());
+  u->nsb = int(sb.size());
+  const size_t gbb = align256(sizeof(CopyBlock) * std::max<size_t>(gb.size(), 1));
+  const size_t sbb = align256(sizeof(CopyBlock) * std::max<size_t>(sb.size(), 1));
+  const size_t iob = align256(sizeof(int64_t) * std::max<size_t>(in_off.size(), 1));
+  const size_t oob = align256(sizeof(int64_t) * std::max<size_t>(out_off.size(), 1));
+  if (cudaMalloc(&u->tables, gbb + sbb + iob + oob) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("batch plan: table allocation failed");
+    return TT_ENOMEM;
+  }
+  char* t = static_cast<char*>(u->tables);
+  u->gblocks = reinterpret_cast<CopyBlock*>(t);
+  u->sblocks = reinterpret_cast<CopyBlock*>(t + gbb);
+  u->in_off = reinterpret_cast<int64_t*>(t + gbb + sbb);
+  u->out_off = reinterpret_cast<int64_t*>(t + gbb + sbb + iob);
+  if ((!gb.empty() && cudaMemcpy(u->gblocks, gb.data(), sizeof(CopyBlock) * gb.size(), cudaMemcpyHostToDevice)) ||
+      (!sb.empty() && cudaMemcpy(u->sblocks, sb.data(), sizeof(CopyBlock) * sb.size(), cudaMemcpyHostToDevice)) ||
+      (!in_off.empty() &&
+       cudaMemcpy(u->in_off, in_off.data(), sizeof(int64_t) * in_off.size(), cudaMemcpyHostToDevice)) ||
+      (!out_off.empty() &&
+       cudaMemcpy(u->out_off, out_off.data(), sizeof(int64_t) * out_off.size(), cudaMemcpyHostToDevice))) {
+    set_error("batch plan: table upload failed");
+    return TT_ECUDA;
+  }
+  BuildFn build = [u, seeds_dev](Arena& ar, Schedule& sc) {
+    return build_sum_rand_batch(u->P, seeds_dev, u->digits, u->qr_ctas, u->outs, ar, sc);
+  };
+  return plan_prepare(build, &u->gp);
+}
+
+int fused_create(FusedGraph* g, int32_t B, const tt_sum_problem* probs, int32_t precision, int width, int qr_ctas) {
+  std::vector<SumProblem> P(B);
+  for (int b = 0; b < B; ++b) {
+    const int rc = validate_sum(probs[b].N, probs[b].K, probs[b].dims, probs[b].ranks, nullptr, nullptr,
+                                probs[b].ells, false, &P[b]);
+    if (rc != TT_OK) {
+      set_error("tt_batch_plan_create: problem " + std::to_string(b) + ": " + tt_last_error());
+      return rc;
+    }
+    g->ell.push_back(P[b].ell);
+    g->N.push_back(P[b].N);
+    g->K.push_back(P[b].K);
+    g->n_src += size_t(P[b].K) * P[b].N;
+    g->n_dst += size_t(P[b].N);
+  }
+  g->B = B;
+  int maxN = 1;
+  for (const auto& p : P) maxN = std::max(maxN, p.N);
+  const int digits = (precision != TT_PREC_FP64) ? mixed_digits(0.0, maxN) : 0;
+  g->stage_bytes = align256(sizeof(double*) * (g->n_src + g->n_dst) + sizeof(uint64_t) * size_t(B));
+  const int nu = std::max(1, std::min(width, B));
+  if (cudaMalloc(&g->d_stage, g->stage_bytes) != cudaSuccess ||
+      cudaMallocHost(&g->h_stage, g->stage_bytes) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&g->h_status), sizeof(int) * size_t(nu)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->staged, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("batch plan: staging allocation failed");
+    return TT_ENOMEM;
+  }
+  std::memset(g->h_stage, 0, g->stage_bytes);
+  const char* ds = static_cast<const char*>(g->d_stage);
+  const uint64_t* seeds = reinterpret_cast<const uint64_t*>(ds + sizeof(double*) * (g->n_src + g->n_dst));
+  size_t src = 0, dst = 0;
+  for (int u = 0; u < nu; ++u) {
+    const size_t b0 = size_t(B) * u / nu, b1 = size_t(B) * (u + 1) / nu;
+    FusedUnit* fu = new FusedUnit;
+    g->units.push_back(fu);
+    fu->h_status = g->h_status + u;
+    *fu->h_status = 0;
+    TTR_TRY(fused_unit_init(fu, P, b0, b1, src, dst, digits, qr_ctas, seeds + b0));
+    for (size_t b = b0; b < b1; ++b) {
+      src += size_t(P[b].K) * P[b].N;
+      dst += size_t(P[b].N);
+    }
+  }
+  auto emit = [g, ds](FusedUnit* u, cudaStream_t cs) -> int {
+    const double* const* srcp = reinterpret_cast<const double* const*>(ds) + u->src0;
+    double* const* dstp = reinterpret_cast<double* const*>(ds + sizeof(double*) * g->n_src) + u->dst0;
+    StageFn pro = [u, srcp](cudaStream_t s) -> int {
+      if (u->ngb > 0) {
+        TTR_PREFER_SHARED(gather_kernel);
+        gather_kernel<<<unsigned(u->ngb), 256, 0, s>>>(u->gblocks, srcp, u->in_off, u->in_buf);
+        TTR_CHECK_LAUNCH();
+        prof_count_launch(1);
+      }
+      return int(TT_OK);
+    };
+    StageFn epi = [u, dstp](cudaStream_t s) -> int {
+      if (u->nsb > 0) {
+        TTR_PREFER_SHARED(scatter_kernel);
+        scatter_kernel<<<unsigned(u->nsb), 256, 0, s>>>(u->sblocks, u->out_buf, u->out_off, dstp, nullptr, nullptr);
+        TTR_CHECK_LAUNCH();
+        prof_count_launch(1);
+      }
+      TTR_CHECK_CUDA(cudaMemcpyAsync(u->h_status, u->gp.sc->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+      return int(TT_OK);
+    };
+    return plan_emit(u->gp, pro, epi, cs);
+  };
+  auto body = [&](cudaStream_t cs) -> int {
+    if (g->units.size() == 1) return emit(g->units[0], cs);
+    const int w = int(g->units.size());
+    std::vector<cudaStream_t> chains(w, nullptr);
+    std::vector<cudaEvent_t> ev(w + 1, nullptr);
+    int rc = TT_OK;
+    for (auto& e : ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = TT_ECUDA;
+    for (auto& c : chains)
+      if (cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess) rc = TT_ECUDA;
+    if (rc == TT_OK && cudaEventRecord(ev[w], cs) != cudaSuccess) rc = TT_ECUDA;
+    for (int i = 0; rc == TT_OK && i < w; ++i)
+      if (cudaStreamWaitEvent(chains[i], ev[w], 0) != cudaSuccess) rc = TT_ECUDA;
+    for (int i = 0; rc == TT_OK && i < w; ++i) rc = emit(g->units[i], chains[i]);
+    for (int i = 0; rc == TT_OK && i < w; ++i)
+      if (cudaEventRecord(ev[i], chains[i]) != cudaSuccess || cudaStreamWaitEvent(cs, ev[i], 0) != cudaSuccess)
+        rc = TT_ECUDA;
+    if (rc == TT_ECUDA) set_error("batch plan: fork / join of the capture failed");
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    for (auto& c : chains)
+      if (c) cudaStreamDestroy(c);
+    return rc;
+  };
+  return capture_graph(body, &g->exec, &g->prof, &g->kernels);
+}
+
+int fused_status(const FusedGraph* g, const char* who) {
+  int bits = 0;
+  for (size_t u = 0; u < g->units.size(); ++u) bits |= g->h_status[u];
+  return status_code(bits, who);
+}
+
+int fused_run(FusedGraph* g, const double* const* cores, const uint64_t* seeds, double* const* out,
+              int64_t* out_ranks, cudaStream_t s) {
+  TTR_CHECK_CUDA(cudaEventSynchronize(g->staged));
+  char* hs = static_cast<char*>(g->h_stage);
+  for (size_t i = 0; i < g->n_src; ++i)
+    if (!cores[i]) {
+      set_error("tt_batch_plan_run: null core pointer");
+      return TT_EINVAL;
+    }
+  for (size_t i = 0; i < g->n_dst; ++i)
+    if (!out[i]) {
+      set_error("tt_batch_plan_run: null output core pointer");
+      return TT_EINVAL;
+    }
+  std::memcpy(hs, cores, sizeof(double*) * g->n_src);
+  std::memcpy(hs + sizeof(double*) * g->n_src, out, sizeof(double*) * g->n_dst);
+  uint64_t* hsd = reinterpret_cast<uint64_t*>(hs + sizeof(double*) * (g->n_src + g->n_dst));
+  for (int b = 0; b < g->B; ++b) hsd[b] = seeds ? seeds[b] : uint64_t(b);
+  TTR_CHECK_CUDA(cudaMemcpyAsync(g->d_stage, g->h_stage, g->stage_bytes, cudaMemcpyHostToDevice, s));
+  TTR_CHECK_CUDA(cudaEventRecord(g->staged, s));
+  TTR_CHECK_CUDA(cudaGraphLaunch(g->exec, s));
+  {
+    static thread_local int inj = 0;
+    inj = take_injected_status();
+    if (inj != 0) {
+      FusedUnit* u0 = g->units[0];
+      TTR_CHECK_CUDA(cudaMemcpyAsync(u0->gp.sc->dev_status, &inj, sizeof(int), cudaMemcpyHostToDevice, s));
+      TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+      TTR_CHECK_CUDA(cudaMemcpyAsync(u0->h_status, u0->gp.sc->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+  }
+  size_t ri = 0;
+  for (int b = 0; b < g->B; ++b)
+    for (int n = 0; n <= g->N[b]; ++n) out_ranks[ri++] = g->ell[b][n];
+  if (prof_on()) {
+    TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+    TTR_TRY(prof_replayed(g->prof, g->kernels));
+  }
+  return TT_OK;
+}
+
 }  // namespace
 }  // namespace ttr
 
@@ -399,6 +672,8 @@ struct tt_sum_plan {
 };
 struct tt_batch_plan {
   UnitGraph g;
+  FusedGraph f;
+  bool fused = false;
   std::vector<int> N, K;
 };
 
@@ -510,16 +785,42 @@ int tt_sum_plan_destroy(tt_sum_plan* p) {
 
 int64_t tt_sum_plan_launches(const tt_sum_plan* p) { return p ? p->g.kernels : 0; }
 
-int tt_batch_plan_create(int32_t B, const tt_sum_problem* probs, int32_t precision, int32_t width,
-                         tt_batch_plan** plan, void* stream) {
-  if (!plan || B < 1 || !probs || width < 1) {
-    set_error("tt_batch_plan_create: need B >= 1 problems, width >= 1 and a plan pointer");
+int tt_batch_plan_create_sched(int32_t B, const tt_sum_problem* probs, int32_t precision,
+                               const tt_batch_schedule* sched, tt_batch_plan** plan, void* stream) {
+  if (!plan || B < 1 || !probs || !sched || sched->width < 1) {
+    set_error("tt_batch_plan_create: need B >= 1 problems, a schedule with width >= 1 and a plan pointer");
     return TT_EINVAL;
   }
   *plan = nullptr;
-  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED && precision != TT_PREC_MIXED_FULL) {
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED) {
     set_error("tt_batch_plan_create: unknown precision mode");
     return TT_EINVAL;
+  }
+  const int width = sched->width;
+  // fused grouped launches need fixed ranks and target ranks the batched QR takes
+  bool can_fuse = true;
+  for (int b = 0; b < B; ++b) {
+    if (probs[b].tol > 0.0) can_fuse = false;
+    if (probs[b].ells)
+      for (int n = 1; n < probs[b].N; ++n)
+        if (probs[b].ells[n] > 96) can_fuse = false;
+  }
+  if (sched->fused == 1 && !can_fuse) {
+    set_error("tt_batch_plan_create: the fused schedule needs fixed ranks (tol <= 0) and target ranks <= 96");
+    return TT_EUNSUPPORTED;
+  }
+  if (sched->fused != 0 && can_fuse) {
+    tt_batch_plan* p = new tt_batch_plan;
+    p->fused = true;
+    const int rc = fused_create(&p->f, B, probs, precision, width, sched->qr_ctas > 0 ? sched->qr_ctas : 8);
+    if (rc != TT_OK) {
+      fused_free(&p->f);
+      delete p;
+      return rc;
+    }
+    (void)stream;
+    *plan = p;
+    return TT_OK;
   }
   tt_batch_plan* p = new tt_batch_plan;
   int rc = TT_OK;
@@ -543,12 +844,19 @@ int tt_batch_plan_create(int32_t B, const tt_sum_problem* probs, int32_t precisi
   return TT_OK;
 }
 
+int tt_batch_plan_create(int32_t B, const tt_sum_problem* probs, int32_t precision, int32_t width,
+                         tt_batch_plan** plan, void* stream) {
+  tt_batch_schedule sc{width, 8, -1};
+  return tt_batch_plan_create_sched(B, probs, precision, &sc, plan, stream);
+}
+
 int tt_batch_plan_run(tt_batch_plan* p, const double* const* cores, const uint64_t* seeds, double* const* out,
                       int64_t* out_ranks, void* stream) {
   if (!p || !cores || !out || !out_ranks) {
     set_error("tt_batch_plan_run: null argument");
     return TT_EINVAL;
   }
+  if (p->fused) return fused_run(&p->f, cores, seeds, out, out_ranks, static_cast<cudaStream_t>(stream));
   TTR_CHECK_CUDA(cudaEventSynchronize(p->g.staged));
   std::vector<int64_t*> rk(p->g.units.size());
   size_t ci = 0, oi = 0, ri = 0;
@@ -570,17 +878,20 @@ int tt_batch_plan_status(tt_batch_plan* p, void* stream) {
     return TT_EINVAL;
   }
   TTR_CHECK_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  if (p->fused) return fused_status(&p->f, "tt_batch_plan_run");
   return unit_graph_status(&p->g, "tt_batch_plan_run");
 }
 
 int tt_batch_plan_destroy(tt_batch_plan* p) {
   if (!p) return TT_OK;
   cudaDeviceSynchronize();
-  unit_graph_free(&p->g);
+  if (p->fused) fused_free(&p->f);
+  else unit_graph_free(&p->g);
   delete p;
   return TT_OK;
 }
 
-int64_t tt_batch_plan_launches(const tt_batch_plan* p) { return p ? p->g.kernels : 0; }
+int64_t tt_batch_plan_launches(const tt_batch_plan* p) { return p ? (p->fused ? p->f.kernels : p->g.kernels) : 0; }
+int tt_batch_plan_is_fused(const tt_batch_plan* p) { return p && p->fused ? 1 : 0; }
 
 }  // extern "C"

@@ -598,6 +598,175 @@ int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t
   return TT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Many independent sum roundings (fixed ranks) rounded together: the same
+// steps as build_sum_rand for every problem, but each step is ONE grouped
+// launch over all problems (the Algorithm 3 products of every summand of every
+// problem, then every sketch, every core update, ...), and the thin QRs of a
+// step run as one batched Cholesky-QR chain. Problems of different orders are
+// aligned at their last core in the right-to-left sweep and at their first core
+// in the left-to-right sweep. seeds_dev: B device seeds (sketches drawn on the
+// device); outs[b]: problem b's N_b output cores (l_{n-1} I_n l_n doubles).
+int build_sum_rand_batch(const std::vector<SumProblem>& Ps, const uint64_t* seeds_dev, int digits, int qr_ctas,
+                         const std::vector<std::vector<double*>>& outs, Arena& ar, Schedule& sc) {
+  const int B = int(Ps.size());
+  const int dw = digits > 0 ? kSketchDigits : 0;
+  auto group = [&](std::vector<GemmDesc> g, int d) {
+    if (g.empty()) return;
+    if (d > 0) sc.gemm_tc(std::move(g), d); else sc.gemm(std::move(g));
+  };
+  struct Buf {
+    std::vector<double*> W, skw;
+    double *Z, *X, *Ys, *Mb[2];
+    double *q0, *q1, *qg, *qr;    // thin-QR scratch, reused by every bond
+  };
+  std::vector<Buf> bf(B);
+  int maxN = 0;
+  int64_t wn_tot = 0, m0_tot = 0;
+  std::vector<int64_t> mmax(B, 1);
+  for (int b = 0; b < B; ++b) {
+    const SumProblem& P = Ps[b];
+    maxN = std::max(maxN, P.N);
+    wn_tot += P.S[P.N] * P.ell[P.N];
+    for (int n = 0; n < P.N; ++n) mmax[b] = std::max(mmax[b], P.ell[n] * P.S[n]);
+    m0_tot += mmax[b];
+  }
+  // W_N (= ones) and M_0 (= the unit coefficients) of all problems live in two
+  // contiguous blocks filled once
+  double* wn_all = ar.take<double>(size_t(std::max<int64_t>(wn_tot, 1)));
+  double* m0_all = ar.take<double>(size_t(std::max<int64_t>(m0_tot, 1)));
+  int64_t wo = 0, mo = 0;
+  std::vector<SketchJob> sj;
+  int64_t sk_max = 1;
+  for (int b = 0; b < B; ++b) {
+    const SumProblem& P = Ps[b];
+    const int N = P.N;
+    Buf& f = bf[b];
+    f.W.assign(N + 1, nullptr);
+    for (int n = 1; n < N; ++n) f.W[n] = ar.take<double>(size_t(P.S[n] * P.ell[n]));
+    f.W[N] = wn_all ? wn_all + wo : nullptr;
+    wo += P.S[N] * P.ell[N];
+    int64_t zmax = 1, xmax = 1, ymax = 1;
+    for (int n = 2; n <= N; ++n) zmax = std::max(zmax, P.S[n - 1] * P.I[n - 1] * P.ell[n]);
+    for (int n = 1; n <= N; ++n) xmax = std::max(xmax, P.ell[n - 1] * P.I[n - 1] * P.S[n]);
+    for (int n = 1; n < N; ++n) ymax = std::max(ymax, P.ell[n - 1] * P.I[n - 1] * P.ell[n]);
+    f.Z = ar.take<double>(size_t(zmax));
+    f.X = ar.take<double>(size_t(xmax));
+    f.Ys = ar.take<double>(size_t(ymax));
+    f.Mb[0] = m0_all ? m0_all + mo : nullptr;
+    mo += mmax[b];
+    f.Mb[1] = ar.take<double>(size_t(mmax[b]));
+    int64_t qm = 1, qgm = 1, qk = 1;
+    for (int n = 1; n < N; ++n) {
+      const int64_t m = P.ell[n - 1] * P.I[n - 1], k = P.ell[n];
+      qm = std::max(qm, m * k);
+      qgm = std::max(qgm, qr_batch_gram_doubles(m, int(k), qr_ctas));
+      qk = std::max(qk, k * k);
+    }
+    f.q0 = ar.take<double>(size_t(qm));
+    f.q1 = ar.take<double>(size_t(qm));
+    f.qg = ar.take<double>(size_t(qgm));
+    f.qr = ar.take<double>(size_t(qk));
+    f.skw.assign(N + 1, nullptr);
+    for (int n = 2; n <= N; ++n) {
+      const int64_t a = P.ell[n - 1], c = P.ell[n], In = P.I[n - 1];
+      f.skw[n] = ar.take<double>(size_t(a * In * c));
+      sj.push_back(sketch_job(f.skw[n], a, In, c, n - 1, seeds_dev ? seeds_dev + b : nullptr));
+      sk_max = std::max(sk_max, a * In * c);
+    }
+  }
+  // ---- set-up: ones, all sketch cores in one launch
+  {
+    const int64_t a = wn_tot, c = m0_tot;
+    sc.add([=](cudaStream_t s) -> int {
+      TTR_TRY(fill_launch(wn_all, a, 1.0, s));
+      return fill_launch(m0_all, c, 1.0, s);
+    });
+  }
+  if (!sj.empty()) {
+    const size_t bytes = sj.size() * sizeof(SketchJob);
+    double* d_sj = ar.take<double>(size_t(ceil_div(int64_t(bytes), 8)));
+    std::vector<double> raw(size_t(ceil_div(int64_t(bytes), 8)), 0.0);
+    std::memcpy(raw.data(), sj.data(), bytes);
+    sc.upload(d_sj, raw);
+    const int nj = int(sj.size());
+    sc.add([=](cudaStream_t s) -> int {
+      return sketch_batch_launch(reinterpret_cast<const SketchJob*>(d_sj), nj, sk_max, s);
+    });
+  }
+  // ---- right-to-left partial contractions, aligned at the last core
+  for (int t = 0; t + 2 <= maxN; ++t) {
+    std::vector<GemmDesc> ga, gb;
+    for (int b = 0; b < B; ++b) {
+      const SumProblem& P = Ps[b];
+      const int n = P.N - t;
+      if (n < 2) continue;
+      const Buf& f = bf[b];
+      const int64_t In = P.I[n - 1];
+      for (int j = 0; j < P.K; ++j) {
+        const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
+        double* Zj = f.Z ? f.Z + P.o(j, n - 1) * In * P.ell[n] : nullptr;
+        const double* Wj = f.W[n] ? f.W[n] + P.o(j, n) * P.ell[n] : nullptr;
+        ga.push_back(gdesc(P.core(j, n), r1, 1, Wj, P.ell[n], 1, Zj, P.ell[n], 1, r0 * In, P.ell[n], r1));
+      }
+      gb.push_back(gdesc(f.Z, In * P.ell[n], 1, f.skw[n], 1, In * P.ell[n], f.W[n - 1], P.ell[n - 1], 1, P.S[n - 1],
+                         P.ell[n - 1], In * P.ell[n]));
+    }
+    group(ga, dw);
+    group(gb, dw);
+  }
+  // ---- left-to-right sweep, aligned at the first core
+  for (int n = 1; n <= maxN; ++n) {
+    std::vector<GemmDesc> gc, gd, ge;
+    std::vector<QrBatchJob> qj;
+    for (int b = 0; b < B; ++b) {
+      const SumProblem& P = Ps[b];
+      if (n > P.N) continue;
+      const Buf& f = bf[b];
+      const int N = P.N;
+      const int64_t In = P.I[n - 1];
+      const double* Mp = f.Mb[(n - 1) & 1];
+      double* Mn = f.Mb[n & 1];
+      for (int j = 0; j < P.K; ++j) {
+        const int64_t r0 = P.r(j, n - 1), r1 = P.r(j, n);
+        if (digits > 0) {
+          GemmDesc d = gdesc(P.core(j, n), 1, In * r1, Mp ? Mp + P.o(j, n - 1) : nullptr, 1, P.S[n - 1],
+                             f.X ? f.X + P.o(j, n) : nullptr, P.S[n], In * P.S[n], In * r1, P.ell[n - 1], r0);
+          d.c_rdiv = r1;
+          d.c_rs2 = 1;
+          gc.push_back(d);
+        } else {
+          GemmDesc d = gdesc(Mp ? Mp + P.o(j, n - 1) : nullptr, P.S[n - 1], 1, P.core(j, n), In * r1, 1,
+                             f.X ? f.X + P.o(j, n) : nullptr, In * P.S[n], 1, P.ell[n - 1], r1, r0);
+          d.batch = int32_t(In);
+          d.a_bs = 0;
+          d.b_bs = r1;
+          d.c_bs = P.S[n];
+          gc.push_back(d);
+        }
+      }
+      double* dst = (n < N) ? f.Ys : outs[b][N - 1];
+      gd.push_back(gdesc(f.X, P.S[n], 1, f.W[n], P.ell[n], 1, dst, P.ell[n], 1, P.ell[n - 1] * In, P.ell[n], P.S[n]));
+      if (n == N) continue;
+      const int64_t m = P.ell[n - 1] * In, k = P.ell[n];
+      double* Qn = outs[b][n - 1];
+      QrBatchJob q{f.Ys, k, 1, Qn, k, 1, m, int(k)};
+      q.has_scratch = true;
+      q.buf0 = f.q0;
+      q.buf1 = f.q1;
+      q.gpart = f.qg;
+      q.rinv = f.qr;
+      qj.push_back(q);
+      ge.push_back(gdesc(Qn, 1, k, f.X, P.S[n], 1, Mn, P.S[n], 1, k, P.S[n], m));
+    }
+    group(gc, digits);
+    group(gd, digits);
+    if (!qj.empty()) TTR_TRY(qr_batch_plan(ar, sc, qj, qr_ctas));
+    group(ge, digits);
+  }
+  return TT_OK;
+}
+
 // Digits of the mixed path. Errors of the Algorithm 3 contractions compound over
 // the N-step recursion and enter the kept subspace directly when the sum is
 // redundant, so the per-product target is 1e-3 tol / N (1e-7 / N in fixed-rank

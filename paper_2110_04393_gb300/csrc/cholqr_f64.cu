@@ -30,6 +30,7 @@
 // reported to the caller. No host synchronization is involved.
 #include <algorithm>
 #include <atomic>
+#include <cstring>
 
 #include "plan.cuh"
 #include "prof.cuh"
@@ -309,7 +310,7 @@ __device__ void cqr_decide(double* G, double* X, double* G0, int k, int64_t m, i
   }
 }
 
-__global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
+__device__ __forceinline__ void cqr_pass_body(const CqrPass& a, const int blk) {
   extern __shared__ double sm[];
   __shared__ int s_last;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   double* T2 = T + b * k;         // b x k
   double* Rs = T2 + b * k;        // k x k (shared when small)
   const double* Rin = (a.pass == 0) ? nullptr : a.Rinv;
-  const int64_t r0 = int64_t(blockIdx.x) * b;
+  const int64_t r0 = int64_t(blk) * b;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int r = warp; r < b; r += nw) {
     const int64_t gr = r0 + r;
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   }
   // partial Gram, upper triangle packed row-wise (npair entries)
   const int npair = k * (k + 1) / 2;
-  double* Gp = a.Gpart + int64_t(blockIdx.x) * npair;
+  double* Gp = a.Gpart + int64_t(blk) * npair;
   for (int p = tid; p < npair; p += 2 * nt) {
     int i1, j1, i2 = 0, j2 = 0;
     tri_ij(p, k, &i1, &j1);
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   // partials (block order) into a group partial; the last group sums those.
   __threadfence();
   __syncthreads();
-  const int grp = blockIdx.x / CQ_GROUP;
+  const int grp = blk / CQ_GROUP;
   const int ngrp = (a.P + CQ_GROUP - 1) / CQ_GROUP;
   const int gsize = min(CQ_GROUP, a.P - grp * CQ_GROUP);
   if (tid == 0) {
@@ -452,6 +453,25 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) {
   }
   __syncthreads();
   cqr_decide(G, X, G0, k, a.m, a.pass, final_pass, unshifted_run, a.Rinv, a.Racc, a.fo_r, a.status);
+}
+
+__global__ void __launch_bounds__(CQ_THREADS) cqr_pass_kernel(CqrPass a) { cqr_pass_body(a, int(blockIdx.x)); }
+
+// One pass of many independent chains in one launch: job j owns CTAs
+// [begin[j], begin[j + 1]) (begin has njobs + 1 entries); every job's own
+// pass index is replaced by `pass`.
+__global__ void __launch_bounds__(CQ_THREADS) cqr_pass_batch_kernel(const CqrPass* __restrict__ jobs,
+                                                                   const int* __restrict__ begin, int njobs,
+                                                                   int pass) {
+  const int t = int(blockIdx.x);
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(begin + mid) <= t) lo = mid; else hi = mid - 1;
+  }
+  CqrPass a = jobs[lo];
+  a.pass = pass;
+  cqr_pass_body(a, t - __ldg(begin + lo));
 }
 
 // ---------------------------------------------------------------------------
@@ -1012,6 +1032,116 @@ void qr_chain_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs,
     pp.pass = p;
     sc.add([pp](cudaStream_t s) -> int { return cqr_launch(pp, s); });
   }
+}
+
+namespace {
+__global__ void qr_batch_fold_kernel(const int* __restrict__ status, const int* __restrict__ soff, int njobs,
+                                     int* dev_status) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < njobs; j += gridDim.x * blockDim.x)
+    if (__ldcg(status + soff[j]) != 0) atomicOr(dev_status, DEV_QR_FAIL);
+}
+}  // namespace
+
+static void qr_batch_shape(int64_t m, int k, int ctas_per_job, int* rows, int* P) {
+  const int64_t budget = 28000 - int64_t(k) * k;
+  const int64_t bmax = std::max<int64_t>(1, budget / (2 * int64_t(k)));
+  *rows = int(std::min<int64_t>(bmax, std::max<int64_t>(4, ceil_div(m, std::max(1, ctas_per_job)))));
+  *P = int(ceil_div(m, *rows));
+}
+
+int64_t qr_batch_gram_doubles(int64_t m, int k, int ctas_per_job) {
+  int rows, P;
+  qr_batch_shape(m, k, ctas_per_job, &rows, &P);
+  return int64_t(P + (P + 15) / 16) * k * k;
+}
+
+int qr_batch_plan(Arena& ar, Schedule& sc, const std::vector<QrBatchJob>& jobs, int ctas_per_job) {
+  const int nj = int(jobs.size());
+  if (nj == 0) return TT_OK;
+  std::vector<CqrPass> tab(nj);
+  std::vector<int> begin(nj + 1, 0), soff(nj, 0);
+  int64_t tot_status = 0;
+  size_t smem = 0;
+  for (int j = 0; j < nj; ++j) {
+    const QrBatchJob& q = jobs[j];
+    if (q.k < 1 || q.k > CQ_SMEM_K || q.m < q.k) {
+      set_error("batched thin QR: needs k <= 96 and m >= k");
+      return TT_EUNSUPPORTED;
+    }
+    const int k = q.k;
+    int rows, P;
+    qr_batch_shape(q.m, k, ctas_per_job, &rows, &P);
+    const int ngrp = (P + 15) / 16;
+    CqrPass& a = tab[j];
+    a = CqrPass{};
+    a.m = q.m;
+    a.k = k;
+    a.b = rows;
+    a.P = P;
+    a.A = q.A;
+    a.a_rs = q.a_rs;
+    a.a_cs = q.a_cs;
+    a.buf[0] = q.has_scratch ? q.buf0 : ar.take<double>(size_t(q.m) * k);
+    a.buf[1] = q.has_scratch ? q.buf1 : ar.take<double>(size_t(q.m) * k);
+    a.Q = q.Q;
+    a.q_rs = q.q_rs;
+    a.q_cs = q.q_cs;
+    a.Gpart = q.has_scratch ? q.gpart : ar.take<double>(size_t(P + ngrp) * k * k);
+    a.Rinv = q.has_scratch ? q.rinv : ar.take<double>(size_t(k) * k);
+    a.Racc = nullptr;
+    a.fo_r = 0;
+    a.big = nullptr;
+    soff[j] = int(tot_status);
+    tot_status += 5 + 1 + ngrp;
+    begin[j + 1] = begin[j] + P;
+    smem = std::max(smem, std::max<size_t>(size_t(2) * rows * k + size_t(k) * k, size_t(3) * k * k) * sizeof(double));
+  }
+  int* status = ar.take<int>(size_t(tot_status));
+  for (int j = 0; j < nj; ++j) {
+    tab[j].status = status ? status + soff[j] : nullptr;
+    tab[j].counter = status ? status + soff[j] + 5 : nullptr;
+  }
+  // the job table, CTA prefixes and status offsets, uploaded with the schedule
+  const size_t tb = tab.size() * sizeof(CqrPass), bb = begin.size() * sizeof(int), ob = soff.size() * sizeof(int);
+  double* d_tab = ar.take<double>(ceil_div(int64_t(tb), 8));
+  double* d_begin = ar.take<double>(ceil_div(int64_t(bb), 8));
+  double* d_soff = ar.take<double>(ceil_div(int64_t(ob), 8));
+  auto pack = [](const void* src, size_t bytes) {
+    std::vector<double> v(size_t(ceil_div(int64_t(bytes), 8)), 0.0);
+    std::memcpy(v.data(), src, bytes);
+    return v;
+  };
+  sc.upload(d_tab, pack(tab.data(), tb));
+  sc.upload(d_begin, pack(begin.data(), bb));
+  sc.upload(d_soff, pack(soff.data(), ob));
+  const int total = begin[nj];
+  int* const* sp = &sc.dev_status;
+  sc.add([=](cudaStream_t st) -> int {
+    if (!status) return int(TT_OK);
+    TTR_CHECK_CUDA(cudaMemsetAsync(status, 0, size_t(tot_status) * sizeof(int), st));
+    static bool attr = false;
+    if (!attr) {
+      TTR_CHECK_CUDA(
+          cudaFuncSetAttribute(cqr_pass_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+      attr = true;
+    }
+    TTR_PREFER_SHARED(cqr_pass_batch_kernel);
+    for (int p = 0; p < CQ_MAX_PASSES; ++p) {
+      cudaEvent_t e0;
+      const bool prof = prof_begin(st, &e0);
+      cqr_pass_batch_kernel<<<unsigned(total), CQ_THREADS, smem, st>>>(
+          reinterpret_cast<const CqrPass*>(d_tab), reinterpret_cast<const int*>(d_begin), nj, p);
+      TTR_CHECK_LAUNCH();
+      prof_count_launch(1);
+      if (prof) prof_end(st, 1, 0.0);
+    }
+    qr_batch_fold_kernel<<<unsigned(std::max<int64_t>(1, ceil_div(nj, 256))), 256, 0, st>>>(
+        status, reinterpret_cast<const int*>(d_soff), nj, *sp);
+    TTR_CHECK_LAUNCH();
+    prof_count_launch(1);
+    return int(TT_OK);
+  });
+  return TT_OK;
 }
 
 // Householder TSQR when the chain raised status[0] (k <= 96); above that limit

@@ -150,6 +150,18 @@ int copy_if_launch(double* dst, const double* src, int64_t n, const int* skip_if
 int triu_inverse_launch(const double* T, double* X, int k, cudaStream_t s);
 int sym_lower_launch(double* A, int k, cudaStream_t s);
 int axpy_launch(double* y, const double* x, int64_t n, cudaStream_t s);
+// A sketch core to draw in a batch: entries E = r0 I r1 of core index core_index
+// with the Definition 3.1 scale stdv, seed read from device memory.
+struct SketchJob {
+  double* out;
+  int64_t E;
+  int core_index;
+  double stdv;
+  const uint64_t* seed;
+};
+SketchJob sketch_job(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, const uint64_t* seed_dev);
+// Every job of the device table in one launch (same values as sketch_launch).
+int sketch_batch_launch(const SketchJob* d_jobs, int njobs, int64_t max_entries, cudaStream_t s);
 // seed_dev (may be null): read the seed from device memory instead (graph replays).
 int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, uint64_t seed,
                   const uint64_t* seed_dev, cudaStream_t s);

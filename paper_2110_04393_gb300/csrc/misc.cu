@@ -1,6 +1,7 @@
 // Elementwise kernels: constant fill, the counter-based Gaussian sketch of
 // Definition 3.1, the truncation threshold and rank-dependent core compaction.
 #include <algorithm>
+#include <cmath>
 
 #include "kernels.cuh"
 #include "prof.cuh"
@@ -36,6 +37,19 @@ __device__ __forceinline__ double u52(uint32_t a, uint32_t b) {
   return (double(bits) + 0.5) * 0x1p-52;
 }
 
+// Entries 2p and 2p + 1 of a sketch core: Box-Muller on one Philox output.
+__device__ __forceinline__ void sketch_pair(double* out, int64_t E, int64_t p, int core_index, uint32_t k0,
+                                            uint32_t k1, double stdv) {
+  uint32_t c[4] = {uint32_t(uint64_t(p)), uint32_t(uint64_t(p) >> 32), uint32_t(core_index), 0x7474726Eu};
+  philox4x32_10(c, k0, k1);
+  const double u1 = u52(c[0], c[1]), u2 = u52(c[2], c[3]);
+  const double rad = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  out[2 * p] = rad * cs * stdv;
+  if (2 * p + 1 < E) out[2 * p + 1] = rad * sn * stdv;
+}
+
 __global__ void sketch_kernel(double* out, int64_t E, int core_index, uint32_t k0, uint32_t k1, double stdv,
                               const uint64_t* seed_dev) {
   if (seed_dev) {                       // seed of this run, written by the host before a graph replay
@@ -45,16 +59,18 @@ __global__ void sketch_kernel(double* out, int64_t E, int core_index, uint32_t k
   }
   const int64_t npairs = (E + 1) / 2;
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < npairs;
-       p += int64_t(gridDim.x) * blockDim.x) {
-    uint32_t c[4] = {uint32_t(uint64_t(p)), uint32_t(uint64_t(p) >> 32), uint32_t(core_index), 0x7474726Eu};
-    philox4x32_10(c, k0, k1);
-    const double u1 = u52(c[0], c[1]), u2 = u52(c[2], c[3]);
-    const double rad = sqrt(-2.0 * log(u1));
-    double sn, cs;
-    sincospi(2.0 * u2, &sn, &cs);
-    out[2 * p] = rad * cs * stdv;
-    if (2 * p + 1 < E) out[2 * p + 1] = rad * sn * stdv;
-  }
+       p += int64_t(gridDim.x) * blockDim.x)
+    sketch_pair(out, E, p, core_index, k0, k1, stdv);
+}
+
+// Many sketch cores at once: job blockIdx.y, its pairs over blockIdx.x.
+__global__ void sketch_batch_kernel(const SketchJob* __restrict__ jobs) {
+  const SketchJob j = jobs[blockIdx.y];
+  const uint64_t sd = *j.seed;
+  const int64_t npairs = (j.E + 1) / 2;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < npairs;
+       p += int64_t(gridDim.x) * blockDim.x)
+    sketch_pair(j.out, j.E, p, j.core_index, uint32_t(sd), uint32_t(sd >> 32), j.stdv);
 }
 
 __global__ void norm_eps_kernel(const double* x, int64_t n, double tol, int N, double* eps_out) {
@@ -96,6 +112,30 @@ int fill_launch(double* p, int64_t n, double v, cudaStream_t s) {
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
   return TT_OK;
+}
+
+int sketch_batch_launch(const SketchJob* d_jobs, int njobs, int64_t max_entries, cudaStream_t s) {
+  if (njobs <= 0) return TT_OK;
+  if (njobs > 65535) {
+    set_error("batched sketch: at most 65535 cores per launch");
+    return TT_EUNSUPPORTED;
+  }
+  const unsigned gx = unsigned(std::max<int64_t>(1, std::min<int64_t>(ceil_div((max_entries + 1) / 2, 256), 16)));
+  TTR_PREFER_SHARED(sketch_batch_kernel);
+  sketch_batch_kernel<<<dim3(gx, unsigned(njobs)), 256, 0, s>>>(d_jobs);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  return TT_OK;
+}
+
+SketchJob sketch_job(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, const uint64_t* seed_dev) {
+  SketchJob j{};
+  j.out = out;
+  j.E = r0 * I * r1;
+  j.core_index = core_index;
+  j.stdv = 1.0 / std::sqrt(double(r0) * double(I) * double(r1));
+  j.seed = seed_dev;
+  return j;
 }
 
 int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index, uint64_t seed,

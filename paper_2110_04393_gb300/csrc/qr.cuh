@@ -70,6 +70,29 @@ const int* qr_cert_flag(const QrBufs& b);
 // Householder TSQR for every QR with k <= 96 (a diagnostic of that path).
 constexpr int QR_MODE_AUTO = 0, QR_MODE_CHAIN = 1, QR_MODE_FORCE_FALLBACK = 2;
 int set_qr_mode(int mode);
+// Many independent thin QRs (Q only, k <= 96): one multi-launch Cholesky-QR
+// chain (CQ_MAX_PASSES launches) covering every job, each job on about
+// ctas_per_job CTAs, scratch taken from ar. A job whose chain breaks down
+// raises DEV_QR_FAIL in the run's status word (there is no Householder
+// fallback for batched jobs). Q must not alias A.
+struct QrBatchJob {
+  const double* A;
+  int64_t a_rs, a_cs;
+  double* Q;
+  int64_t q_rs, q_cs;
+  int64_t m;
+  int k;
+  // optional scratch (else taken from the arena): two m x k blocks, the
+  // partial Gram matrices (qr_batch_gram_doubles) and a k x k factor
+  bool has_scratch = false;   // the four pointers below are given (they may be null while sizing)
+  double* buf0 = nullptr;
+  double* buf1 = nullptr;
+  double* gpart = nullptr;
+  double* rinv = nullptr;
+};
+int qr_batch_plan(Arena& ar, Schedule& sc, const std::vector<QrBatchJob>& jobs, int ctas_per_job);
+// Doubles of partial Gram matrices that a batched job of shape (m, k) needs.
+int64_t qr_batch_gram_doubles(int64_t m, int k, int ctas_per_job);
 // Number of Householder TSQR fallback runs on the current device since load.
 int tsqr_fallback_runs(long long* out);
 

@@ -1,5 +1,7 @@
-"""Batched plans: uneven independent sum roundings in one graph, every problem
-bit-wise equal to the eager entry point with its seed, at several chain widths."""
+"""Batched plans: uneven independent sum roundings in one graph. The
+per-problem schedule is bit-wise the eager entry point with its seed; the fused
+schedule (grouped launches over all problems, batched thin QRs) equals it to
+rounding, with a launch count that does not grow with the number of problems."""
 import numpy as np
 import pytest
 import torch
@@ -32,8 +34,8 @@ def _problems():
 @pytest.mark.parametrize("width", [1, 2, 5])
 def test_batch_matches_eager_bitwise(precision, width):
     probs, data = _problems()
-    plan = tt.BatchRoundingPlan(probs, precision=precision, width=width)
-    assert plan.launches > 0
+    plan = tt.BatchRoundingPlan(probs, precision=precision, width=width, fused=0)
+    assert plan.launches > 0 and not plan.fused
     seeds = [11, 12, 13, 14, 15]
     for rep in range(2):
         res = plan(data, seeds=seeds)
@@ -46,7 +48,64 @@ def test_batch_matches_eager_bitwise(precision, width):
     plan.close()
 
 
-def test_tune_batch_width_returns_a_candidate():
+def _fixed_rank(probs):
+    return [dict(p, tol=0.0) for p in probs]
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("width,qr_ctas", [(1, 8), (2, 4), (5, 16)])
+def test_fused_batch_matches_eager(precision, width, qr_ctas):
     probs, data = _problems()
-    best, times = tt.tune_batch_width(probs, data, precision="mixed", candidates=(1, 5), reps=1)
-    assert best in (1, 5) and set(times) == {1, 5}
+    probs = _fixed_rank(probs)
+    plan = tt.BatchRoundingPlan(probs, precision=precision, width=width, qr_ctas=qr_ctas)
+    assert plan.fused
+    seeds = [21, 22, 23, 24, 25]
+    for rep in range(2):
+        res = plan(data, seeds=seeds)
+        plan.status()
+        for b, (pr, Ys) in enumerate(zip(probs, data)):
+            Xe = tt.tt_round_sum_rand(Ys, pr["ells"], seed=seeds[b], precision=precision)
+            assert [tuple(x.shape) for x in res[b]] == [tuple(y.shape) for y in Xe]
+            assert _rel_full(res[b], Xe) <= 1e-10, (rep, b)
+    plan.close()
+
+
+def _rel_full(X, Y):
+    """Relative distance of the two TT's as tensors (orthogonalized difference TT)."""
+    import oracle as O
+    from tests._gpu import to_host
+    a, b = to_host(X), to_host(Y)
+    return O.diff_norm(a, b) / O.norm(b)
+
+
+def test_fused_launch_count_does_not_grow_with_the_batch():
+    probs, data = _problems()
+    probs = _fixed_rank(probs)
+    one = tt.BatchRoundingPlan(probs[:1], precision="mixed", width=1)
+    many = tt.BatchRoundingPlan(probs * 8, precision="mixed", width=1)
+    try:
+        assert many.fused and one.fused
+        maxN = max(len(p["dims"]) for p in probs)
+        assert many.launches <= 40 * maxN + 20, many.launches
+    finally:
+        one.close()
+        many.close()
+
+
+def test_fused_schedule_refuses_a_tolerance():
+    probs, data = _problems()
+    with pytest.raises(tt.TTError):
+        tt.BatchRoundingPlan(probs, precision="mixed", fused=1)
+
+
+def test_tune_batch_schedule_returns_a_candidate(tmp_path):
+    probs, data = _problems()
+    probs = _fixed_rank(probs)
+    cache = str(tmp_path / "tune.json")
+    best, times = tt.tune_batch_schedule(probs, data, precision="mixed", widths=(1, 2), qr_ctas=(4, 8), reps=1,
+                                         cache_path=cache)
+    assert best in times and set(times) == {(1, 4), (1, 8), (2, 4), (2, 8)}
+    import json
+    assert json.load(open(cache))
+    w, t = tt.tune_batch_width(probs, data, precision="mixed", candidates=(1, 5), reps=1)
+    assert w in (1, 5)
