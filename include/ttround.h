@@ -487,6 +487,31 @@ size_t tt_round_gram_schmidt_workspace(int32_t N, const int64_t* dims, const int
                                        const int64_t* ranks_v, const int64_t* ells, double tol, int32_t precision);
 
 /*
+ * tt_round_sum_rand_sharded -- Algorithm 7 with the summands sharded over
+ * ranks (no counterpart in the paper; its block form makes it direct): every
+ * rank passes its own summands (K, ranks, cores, coeffs of its share) with the
+ * same dims, ells, sketch / seed, tol and precision. The right-to-left
+ * partial contractions are per summand and stay local; in the left-to-right
+ * sweep the partial sketch V(X_n) [W^{(j)}_n]_j of the rank's summands
+ * (l_{n-1} I_n l_n doubles, device) and finally the partial last core are
+ * summed over the ranks by `allreduce`, after which every rank repeats the same
+ * thin QR and truncation on identical data and the local projections
+ * M^{(j)}_n. Every rank ends with the whole rounded tensor in out.
+ *   allreduce(buf, count, stream, ctx): must replace buf (device, count
+ *   doubles) by its sum over the ranks, stream-ordered on `stream` (e.g. an
+ *   NCCL all-reduce enqueued on it), with the same summation order on every
+ *   rank; nonzero return = failure (TT_ECUDA). It is called from the calling
+ *   thread while the library enqueues its work.
+ * Other arguments and errors as tt_round_sum_rand.
+ */
+typedef int (*tt_allreduce_fn)(double* buf, size_t count, void* stream, void* ctx);
+int tt_round_sum_rand_sharded(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                              const double* const* cores, const double* coeffs, const int64_t* ells,
+                              const double* const* sketch, uint64_t seed, double tol, int32_t precision,
+                              double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
+                              void* stream, tt_allreduce_fn allreduce, void* ctx);
+
+/*
  * tt_round_sum_rand_noalloc -- tt_round_sum_rand for callers that cannot
  * allocate device memory (no counterpart in the paper: it only changes where the
  * scratch lives). Some callers may not call cudaMalloc at the point of the
@@ -578,6 +603,18 @@ void tt_debug_inject_device_status(int32_t bits);
  */
 int tt_set_qr_mode(int32_t mode);
 int tt_tsqr_fallback_runs(int64_t* runs);
+
+/*
+ * tt_set_gemm_mode -- how the emulated-FP64 tensor-core products of later calls
+ * (and plans created later) run (no counterpart in the paper): 2 = fused, the
+ * digit split done by the product kernel straight into shared memory (the
+ * exponents scanned there too for an unsplit K <= 512, else one exponent pass
+ * first); 1 = three passes, the digit planes written to and re-read from
+ * global memory; 0 (default) = fused for groups whose planes would exceed
+ * 64 MB, else three passes. The results are bit-identical.
+ * Errors: TT_EINVAL for an unknown mode.
+ */
+int tt_set_gemm_mode(int32_t mode);
 
 /*
  * Measurement hooks (no counterpart in the paper; used by the benchmark).

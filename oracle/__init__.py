@@ -23,7 +23,7 @@ from .tt import (H, V, from_H, from_V, full, full_bruteforce, inner, norm, diff_
                  block_sum, merge_left, merge_right, ranks_of, dims_of)
 from .rounding import (orthogonalize_rl, orthogonalize_lr, svd_truncated, tt_round_det,
                        partial_contractions_rl, partial_contractions_lr,
-                       round_orthrand, round_randorth, round_twosided, round_sum_randorth,
+                       round_orthrand, round_randorth, round_twosided, round_sum_randorth, round_sum_randorth_sharded,
                        round_sum_twosided, round_sum_twosided_orth, truncate_left_orthogonal, clamp_ranks)
 from .philox import philox4x32_10, gaussian_sketch_philox
 from .adjoint import randorth_fixed_sketch_loss, randorth_adjoint
@@ -34,7 +34,7 @@ __all__ = [
     "block_sum", "merge_left", "merge_right", "ranks_of", "dims_of",
     "orthogonalize_rl", "orthogonalize_lr", "svd_truncated", "tt_round_det",
     "partial_contractions_rl", "partial_contractions_lr",
-    "round_orthrand", "round_randorth", "round_twosided", "round_sum_randorth",
+    "round_orthrand", "round_randorth", "round_twosided", "round_sum_randorth", "round_sum_randorth_sharded",
     "round_sum_twosided", "round_sum_twosided_orth", "truncate_left_orthogonal", "clamp_ranks",
     "philox4x32_10", "gaussian_sketch_philox",
     "randorth_fixed_sketch_loss", "randorth_adjoint",

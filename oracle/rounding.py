@@ -211,6 +211,44 @@ def round_sum_randorth(Ys, R, coeffs=None):
     return X
 
 
+def round_sum_randorth_sharded(Ys_local, R, allreduce, coeffs=None):
+    """Algorithm 7 with the summands spread over ranks (the block form of
+    Section 3.4 makes this direct): a rank holds Ys_local (its summands and
+    their coefficients). The partial contractions W^{(j)} and the projections
+    M^{(j)}_n are per summand and stay local; the sketch Y_n = Z_n [W^{(j)}_n]_j
+    and the last core are sums over summands, so each rank forms its part and
+    allreduce(array) -> array returns the sum over the ranks; every rank then
+    takes the same QR. Returns the whole rounded tensor on every rank."""
+    s = len(Ys_local)
+    N = len(Ys_local[0])
+    if coeffs is None:
+        coeffs = [1.0] * s
+    Ys = [[c * Y[0]] + list(Y[1:]) for c, Y in zip(coeffs, Ys_local)]
+    W = [partial_contractions_rl(Y, R) for Y in Ys]
+    X = [None] * N
+    Xn = np.concatenate([Y[0] for Y in Ys], axis=2)
+    if N == 1:
+        return [allreduce(sum(Y[0] for Y in Ys))]
+    for n in range(1, N):
+        I = Xn.shape[1]
+        Z = V(Xn)
+        Wstack = np.concatenate([W[j][n] for j in range(s)], axis=0)
+        Ysk = allreduce(Z @ Wstack)
+        Q, _ = np.linalg.qr(Ysk)
+        X[n - 1] = from_V(Q, I)
+        M = Q.T @ Z
+        cols = np.cumsum([0] + [Y[n - 1].shape[2] for Y in Ys])
+        Mj = [M[:, cols[j]:cols[j + 1]] for j in range(s)]
+        Inext = Ys[0][n].shape[1]
+        if n < N - 1:
+            blocks = [from_H(Mj[j] @ H(Ys[j][n]), Inext) for j in range(s)]
+            Xn = np.concatenate(blocks, axis=2)
+        else:
+            Xn = allreduce(sum(from_H(Mj[j] @ H(Ys[j][N - 1]), Inext) for j in range(s)))
+    X[N - 1] = Xn
+    return X
+
+
 def round_orthrand(Y, Omegas):
     """Algorithm 4 (Orthogonalize-then-Randomize): Y := OrthogonalizeRL(Y);
     X_1 = Y_1; for n = 1..N-1: Z_n = V(X_n); Y_n = Z_n Omega_n (Omega_n an

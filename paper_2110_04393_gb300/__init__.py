@@ -14,17 +14,18 @@ from __future__ import annotations
 from .api import (tt_version, tt_sketch_gaussian, tt_round_sum_rand, tt_round_rand, TTError,
                   tt_round_det, tt_round_orthrand, tt_orthrand_omega_ranks, tt_round_twosided,
                   tt_round_twosided_orth, tt_truncate_lorth, tt_inner, tt_norm, tt_round_gram_schmidt,
-                  tt_mode_products,
+                  tt_mode_products, tt_round_sum_rand_sharded,
                   tt_gemm_emulated_f64, SumRoundingPlan, BatchRoundingPlan, tune_batch_width, tune_batch_schedule, tt_round_rand_backward, clamp_ranks,
                   round_rand_fixed_sketch, debug_inject_device_status, set_qr_mode, tsqr_fallback_runs,
-                  QR_AUTO, QR_CHAIN, QR_FORCE_FALLBACK, prof_enable, prof_reset, prof_read, prof_read_kind,
+                  QR_AUTO, QR_CHAIN, QR_FORCE_FALLBACK, set_gemm_mode, GEMM_AUTO, GEMM_FUSED, GEMM_THREE_PASS, prof_enable, prof_reset, prof_read, prof_read_kind,
                   PREC_FP64, PREC_MIXED)
 from .costs import flops_sum_randorth, bytes_sum_randorth
 
 __all__ = ["tt_version", "tt_sketch_gaussian", "tt_round_sum_rand", "tt_round_rand", "TTError",
            "tt_round_det", "tt_round_orthrand", "tt_orthrand_omega_ranks", "tt_round_twosided",
            "tt_round_twosided_orth", "tt_truncate_lorth", "tt_inner", "tt_norm", "tt_round_gram_schmidt",
-           "tt_mode_products",
+           "tt_mode_products", "tt_round_sum_rand_sharded",
            "tt_gemm_emulated_f64", "SumRoundingPlan", "BatchRoundingPlan", "tune_batch_width", "tune_batch_schedule", "tt_round_rand_backward", "round_rand_fixed_sketch", "clamp_ranks",
            "PREC_FP64", "PREC_MIXED", "debug_inject_device_status", "set_qr_mode",
-           "tsqr_fallback_runs", "QR_AUTO", "QR_CHAIN", "QR_FORCE_FALLBACK", "flops_sum_randorth", "bytes_sum_randorth"]
+           "tsqr_fallback_runs", "QR_AUTO", "QR_CHAIN", "QR_FORCE_FALLBACK", "set_gemm_mode",
+           "GEMM_AUTO", "GEMM_FUSED", "GEMM_THREE_PASS", "flops_sum_randorth", "bytes_sum_randorth"]

@@ -51,6 +51,8 @@ SIGNATURES = {
     "tt_round_gram_schmidt_workspace": (c_size, [c_i32, P_i64, P_i64, c_i32, P_i64, P_i64, c_dbl, c_i32]),
     "tt_mode_products": (c_i32, [c_i32, P_i64, P_vp, P_vp, P_vp, c_vp, c_size, c_vp]),
     "tt_mode_products_workspace": (c_size, [c_i32, P_i64]),
+    "tt_round_sum_rand_sharded": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl,
+                                          c_i32, P_vp, P_i64, c_vp, c_size, c_vp, c_vp, c_vp]),
     "tt_noalloc_scratch_bytes": (c_size, []),
     "tt_round_sum_rand_noalloc": (c_i32, [c_i32, c_i32, P_i64, P_i64, P_vp, P_dbl, P_i64, P_vp, c_u64, c_dbl,
                                           c_i32, P_vp, P_i64, c_vp]),
@@ -69,6 +71,7 @@ SIGNATURES = {
     "tt_batch_plan_status": (c_i32, [c_vp, c_vp]),
     "tt_debug_inject_device_status": (None, [c_i32]),
     "tt_set_qr_mode": (c_i32, [c_i32]),
+    "tt_set_gemm_mode": (c_i32, [c_i32]),
     "tt_tsqr_fallback_runs": (c_i32, [P_i64]),
     "tt_sum_plan_host_layout": (c_i32, [c_vp, P_i64, P_i64, P_i64, P_i64]),
     "tt_sum_plan_run_host": (c_i32, [c_vp, c_vp, P_dbl, c_u64, c_vp, P_i64, c_vp]),

@@ -153,6 +153,62 @@ def tt_round_sum_rand(summands, ells, *, tol=0.0, sketch=None, seed=0, coeffs=No
     return res
 
 
+_ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _DeviceView:
+    """A float64 device buffer handed to Python through __cuda_array_interface__."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+def tt_round_sum_rand_sharded(summands, ells, allreduce, *, tol=0.0, sketch=None, seed=0, coeffs=None,
+                              precision="fp64", workspace=None, stream=None):
+    """Algorithm 7 with this rank's share of the summands (tt_round_sum_rand_sharded):
+    allreduce(tensor, stream) must replace the float64 CUDA tensor by its sum
+    over the ranks, ordered on `stream` (a torch.cuda.ExternalStream), e.g.
+    torch.distributed.all_reduce under that stream. Returns the whole rounded
+    tensor (the same on every rank)."""
+    K = len(summands)
+    N = len(summands[0])
+    device = summands[0][0].device
+    N2, K2, dims, ranks, flat = _sum_args(summands)
+    ell = clamp_ranks(dims, ells)
+    out = [torch.empty((ell[n], dims[n], ell[n + 1]), dtype=torch.float64, device=device) for n in range(N)]
+    sk_arr = _ptrs(sketch) if sketch is not None else None
+    co = (ctypes.c_double * K)(*[float(c) for c in coeffs]) if coeffs is not None else None
+    err = []
+
+    def cb(ptr, count, strm, ctx):
+        try:
+            t = torch.as_tensor(_DeviceView(ptr, count), device=device)
+            allreduce(t, torch.cuda.ExternalStream(int(strm) if strm else 0, device=device))
+            return 0
+        except Exception as e:          # reported through the library's status
+            err.append(e)
+            return 1
+
+    fn = _ALLREDUCE_FN(cb)
+    L = nat.lib()
+    prec = _PREC[precision]
+    dims_a, ranks_a, ell_a = _i64(dims), _i64(ranks), _i64(ell)
+    nb = L.tt_round_sum_rand_workspace(N, K, dims_a, ranks_a, ell_a, float(tol), prec)
+    if nb == 0:
+        raise TTError(1, nat.last_error())
+    workspace, wp, wb = _workspace(nb, device, workspace)
+    out_ranks = (ctypes.c_int64 * (N + 1))()
+    rc = L.tt_round_sum_rand_sharded(N, K, dims_a, ranks_a, _ptrs(flat), co, ell_a, sk_arr,
+                                     ctypes.c_uint64(int(seed)), float(tol), prec, _ptrs(out), out_ranks, wp, wb,
+                                     _stream(stream, device), ctypes.cast(fn, ctypes.c_void_p), None)
+    if err:
+        raise err[0]
+    _check(rc)
+    r = [int(x) for x in out_ranks]
+    return [out[n].view(-1)[:r[n] * dims[n] * r[n + 1]].view(r[n], dims[n], r[n + 1]) for n in range(N)]
+
+
 def tt_round_rand_backward(cores, ells, sketch, xbar, *, workspace=None, stream=None):
     """dL/dY for fixed-sketch RandOrth (Algorithm 5, fixed ranks) given
     xbar = dL/dX_hat for its output cores; returns tensors shaped like cores.
@@ -830,6 +886,15 @@ def set_qr_mode(mode):
     where it fits), QR_CHAIN (one launch per Cholesky-QR pass) or
     QR_FORCE_FALLBACK (Householder TSQR for every QR with k <= 96)."""
     _check(nat.lib().tt_set_qr_mode(int(mode)))
+
+
+GEMM_AUTO, GEMM_THREE_PASS, GEMM_FUSED = 0, 1, 2
+
+
+def set_gemm_mode(mode):
+    """GEMM_AUTO (fused for groups with large digit planes), GEMM_THREE_PASS or
+    GEMM_FUSED; bit-identical results."""
+    _check(nat.lib().tt_set_gemm_mode(int(mode)))
 
 
 def tsqr_fallback_runs():

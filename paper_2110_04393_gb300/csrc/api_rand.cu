@@ -27,6 +27,9 @@
 namespace ttr {
 
 static thread_local std::string g_err;
+// the all-reduce hook of the current tt_round_sum_rand_sharded call (this thread)
+static thread_local tt_allreduce_fn g_allreduce = nullptr;
+static thread_local void* g_allreduce_ctx = nullptr;
 void set_error(const std::string& msg) { g_err = msg; }
 
 // Arena regions plus the schedule's own regions (partials, descriptors,
@@ -587,6 +590,23 @@ int build_sum_rand(const SumProblem& P, const double* const* sketch_in, uint64_t
     if (digits > 0) sc.gemm_tc(gc, digits); else sc.gemm(gc);
     double* dst = (n < N) ? Ys : out[N - 1];
     big({gdesc(X, S[n], 1, W[n], ell[n], 1, dst, ell[n], 1, ell[n - 1] * In(n), ell[n], S[n])});
+    if (P.allreduce) {
+      // summand-sharded rounding: the sketch (and the last core) of this rank's
+      // summands is summed over the ranks before the QR, which every rank then
+      // repeats on identical data
+      const tt_allreduce_fn fn = P.allreduce;
+      void* ctx = P.allreduce_ctx;
+      const size_t cnt = size_t(ell[n - 1] * In(n) * ell[n]);
+      sc.add([fn, ctx, dst, cnt](cudaStream_t s) -> int {
+        if (!dst) return int(TT_OK);
+        const int rc = fn(dst, cnt, static_cast<void*>(s), ctx);
+        if (rc != 0) {
+          set_error("the all-reduce callback of the sharded rounding returned " + std::to_string(rc));
+          return TT_ECUDA;
+        }
+        return int(TT_OK);
+      });
+    }
     if (n == N) break;
     const int64_t m = ell[n - 1] * In(n), k = ell[n];
     double* Qn = out[n - 1];
@@ -814,6 +834,14 @@ int tt_set_qr_mode(int32_t mode) {
   return TT_OK;
 }
 
+int tt_set_gemm_mode(int32_t mode) {
+  if (set_gemm_mode(mode) != TT_OK) {
+    set_error("tt_set_gemm_mode: mode must be 0 (automatic), 1 (three-pass) or 2 (fused)");
+    return TT_EINVAL;
+  }
+  return TT_OK;
+}
+
 int tt_tsqr_fallback_runs(int64_t* runs) {
   if (!runs) {
     set_error("tt_tsqr_fallback_runs: null output");
@@ -836,6 +864,10 @@ __attribute__((visibility("hidden"))) int sum_rand_common(int32_t N, int32_t K, 
   if (precision != TT_PREC_FP64 && precision != TT_PREC_MIXED && precision != TT_PREC_MIXED_FULL) {
     set_error("unknown precision mode");
     return TT_EINVAL;
+  }
+  if (size_only == nullptr) {
+    P.allreduce = g_allreduce;
+    P.allreduce_ctx = g_allreduce_ctx;
   }
   const int digits = (precision != TT_PREC_FP64) ? mixed_digits(tol, N) : 0;
   const int sketch_digits = (precision == TT_PREC_MIXED_FULL) ? digits : -1;
@@ -932,6 +964,24 @@ static int truncate_common(int32_t N, const int64_t* dims, const int64_t* ranks,
   TTR_TRY(status_code(dstat, "tt_truncate_lorth"));
   for (int n = 0; n <= N; ++n) out_ranks[n] = rk[n];
   return TT_OK;
+}
+
+int tt_round_sum_rand_sharded(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks,
+                              const double* const* cores, const double* coeffs, const int64_t* ells,
+                              const double* const* sketch, uint64_t seed, double tol, int32_t precision,
+                              double* const* out, int64_t* out_ranks, void* workspace, size_t workspace_bytes,
+                              void* stream, tt_allreduce_fn allreduce, void* ctx) {
+  if (!allreduce) {
+    set_error("tt_round_sum_rand_sharded: null all-reduce callback");
+    return TT_EINVAL;
+  }
+  g_allreduce = allreduce;
+  g_allreduce_ctx = ctx;
+  const int rc = sum_rand_common(N, K, dims, ranks, cores, coeffs, ells, sketch, seed, tol, precision, out,
+                                 out_ranks, workspace, workspace_bytes, stream, nullptr);
+  g_allreduce = nullptr;
+  g_allreduce_ctx = nullptr;
+  return rc;
 }
 
 int tt_round_sum_rand(int32_t N, int32_t K, const int64_t* dims, const int64_t* ranks, const double* const* cores,

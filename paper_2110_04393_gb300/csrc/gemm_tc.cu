@@ -36,6 +36,7 @@
 // short) one bulk copy brings the s planes of A and one those of B into shared
 // memory (completion on an mbarrier); one thread issues the MMAs.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include <string>
@@ -582,6 +583,302 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int
   if (warp == 0) tc::tmem_dealloc(taddr, ncols);
 }
 
+// ---- fused: exponents, digit split and products in one launch. The tile's
+// rows of A and columns of B are scanned for their largest exponents over all
+// of K (every CTA of a split-K tile finds the same ones, so their integer
+// partials still add exactly), then every K-chunk is split by all threads
+// straight into the shared-memory planes the MMAs read (the layout the
+// three-pass form copies in), so no digit plane goes through global memory.
+// Same arithmetic as the three-pass form: bit-identical results.
+__global__ void __launch_bounds__(TC_THREADS, 1) gemm_tcf_kernel(TcArgs args, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int s = args.s;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail, s_last, s_issued;
+  __shared__ int Er[TC_BM], Ec[TC_BN];
+
+  const int64_t t = blockIdx.x;
+  const GemmDesc d = args.descs[find_desc(args.descs, args.ndesc, t, 0)];
+  const int bk = d.bkc;
+  const uint32_t pA = uint32_t(TC_BM * bk * 2), pB = uint32_t(TC_BN * bk * 2);   // plane bytes
+  uint8_t* As = smem;                                  // s planes of 128 x bk bf16
+  uint8_t* Bs = smem + s * pA;                         // s planes of 32 x bk bf16
+  int64_t local = t - d.tile_begin;
+  const int ntile = int(local % d.nt); local /= d.nt;
+  const int mtile = int(local % d.mt); local /= d.mt;
+  const int ks = int(local % d.ksplit);
+  const int64_t bidx = local / d.ksplit;
+  const int64_t m0 = int64_t(mtile) * TC_BM, n0 = int64_t(ntile) * TC_BN;
+  const int64_t cps = d.kchunk / bk;                   // chunks per split
+  const int64_t kc_begin = int64_t(ks) * cps;
+  const int64_t kc_end = min(d.nkc, kc_begin + cps);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ncols = tc::tmem_cols_for((2 * s - 1) * TC_BN);   // levels 2 .. 2s
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, ncols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    s_fail = 0;
+  }
+  const double* Ab = d.A + bidx * d.a_bs;
+  const double* Bb = d.B + bidx * d.b_bs;
+  for (int i = tid; i < TC_BM + TC_BN; i += TC_THREADS) {
+    if (i < TC_BM) Er[i] = -1;
+    else Ec[i - TC_BM] = -1;
+  }
+  __syncthreads();
+  if (!d.lx) {
+    // exponents from the tags of this launch's exponent pass
+    for (int i = tid; i < TC_BM + TC_BN; i += TC_THREADS) {
+      if (i < TC_BM) {
+        const int64_t r = m0 + i;
+        Er[i] = r < d.M ? decode_exp(__ldcg(d.ex_row + bidx * d.M + r), args.epoch) : 0;
+      } else {
+        const int64_t c = n0 + (i - TC_BM);
+        Ec[i - TC_BM] = c < d.N ? decode_exp(__ldcg(d.ex_col + bidx * d.N + c), args.epoch) : 0;
+      }
+    }
+  } else {
+    // largest exponent codes (dexp) of the 128 rows of A and the 32 columns of B over all of K
+    if (d.a_cs == 1) {                                   // rows contiguous along K: a warp per row
+      for (int r = warp; r < TC_BM; r += TC_THREADS / 32) {
+        int mx = -1;
+        if (m0 + r < d.M)
+          for (int64_t k = lane; k < d.K; k += 32) mx = max(mx, dexp(__ldg(Ab + (m0 + r) * d.a_rs + k)));
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) Er[r] = mx;
+      }
+    } else {                                             // lanes along the rows, warps along K
+      int mx[TC_BM / 32];
+#pragma unroll
+      for (int u = 0; u < TC_BM / 32; ++u) mx[u] = -1;
+      for (int64_t k = warp; k < d.K; k += TC_THREADS / 32)
+#pragma unroll
+        for (int u = 0; u < TC_BM / 32; ++u) {
+          const int64_t r = m0 + lane + 32 * u;
+          if (r < d.M) mx[u] = max(mx[u], dexp(__ldg(Ab + r * d.a_rs + k * d.a_cs)));
+        }
+#pragma unroll
+      for (int u = 0; u < TC_BM / 32; ++u) atomicMax(&Er[lane + 32 * u], mx[u]);
+    }
+    if (d.b_rs == 1) {                                   // columns contiguous along K: a warp per column
+      for (int c = warp; c < TC_BN; c += TC_THREADS / 32) {
+        int mx = -1;
+        if (n0 + c < d.N)
+          for (int64_t k = lane; k < d.K; k += 32) mx = max(mx, dexp(__ldg(Bb + k + (n0 + c) * d.b_cs)));
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) Ec[c] = mx;
+      }
+    } else {                                             // lanes along the columns, warps along K
+      int mx = -1;
+      const int64_t c = n0 + lane;
+      if (c < d.N)
+        for (int64_t k = warp; k < d.K; k += TC_THREADS / 32)
+          mx = max(mx, dexp(__ldg(Bb + k * d.b_rs + c * d.b_cs)));
+      atomicMax(&Ec[lane], mx);
+    }
+    __syncthreads();
+    for (int i = tid; i < TC_BM + TC_BN; i += TC_THREADS) {
+      int* e = i < TC_BM ? &Er[i] : &Ec[i - TC_BM];
+      const int m = *e;
+      *e = m < 0 ? 0 : (m == kExNonFinite ? kNonFinite : m - kExBias + 2);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+
+  const uint32_t taddr = tmem_base;
+
+  // epilogue roles: TMEM lane quadrant q (warp % 4), column half ch
+  const int q = warp & 3, ch = warp >> 2;
+  long long accH[16], accL[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) { accH[j] = 0; accL[j] = 0; }
+  uint32_t mph = 0;
+
+  for (int64_t kc = kc_begin; kc < kc_end; ++kc) {
+    // ---- the chunk's s planes of A and of B, split by every thread into shared
+    //      memory: core matrices of 8 rows x 8 k, a lane holds one row and a k pair
+    {
+      const int64_t k0 = kc * bk;
+      const int kgs = bk / 8;
+      const int cmA = (TC_BM / 8) * kgs, cmB = (TC_BN / 8) * kgs;
+      const int cr = lane >> 2, ck = (lane & 3) * 2;
+      for (int cm = warp; cm < cmA + cmB; cm += TC_THREADS / 32) {
+        const bool sa = cm < cmA;
+        const int c2 = sa ? cm : cm - cmA;
+        const int rg = c2 / kgs, kg = c2 - rg * kgs;
+        const int rt = rg * 8 + cr;                       // row of the operand tile
+        const int64_t k = k0 + kg * 8 + ck;
+        double x0 = 0.0, x1 = 0.0;
+        int E;
+        if (sa) {
+          const int64_t r = m0 + rt;
+          if (r < d.M) {
+            const double* p = Ab + r * d.a_rs + k * d.a_cs;
+            if (k < d.K) x0 = __ldg(p);
+            if (k + 1 < d.K) x1 = __ldg(p + d.a_cs);
+          }
+          E = Er[rt];
+        } else {
+          const int64_t c = n0 + rt;
+          if (c < d.N) {
+            const double* p = Bb + k * d.b_rs + c * d.b_cs;
+            if (k < d.K) x0 = __ldg(p);
+            if (k + 1 < d.K) x1 = __ldg(p + d.b_rs);
+          }
+          E = Ec[rt];
+        }
+        int d0[8], d1[8];
+        digits(x0, E, s, d0);
+        digits(x1, E, s, d1);
+        uint8_t* dst = (sa ? As : Bs) + tc::canon_off_w(rt, kg * 8 + ck, bk);
+        const uint32_t plane = sa ? pA : pB;
+#pragma unroll
+        for (int q2 = 0; q2 < 8; ++q2) {
+          if (q2 >= s) break;
+          *reinterpret_cast<__nv_bfloat162*>(dst + q2 * plane) =
+              __floats2bfloat162_rn(int_to_float_small(d0[q2]), int_to_float_small(d1[q2]));
+        }
+      }
+    }
+    tc::fence_async_smem();                              // generic stores -> the tensor core's view
+    __syncthreads();
+    const bool loaded = true;
+
+    // ---- one thread issues every kept digit-pair product of this chunk (only
+    //      after its own wait saw the copy complete); every thread then waits
+    //      for the issued products before anything else touches TMEM or smem
+    if (tid == 0) s_issued = loaded ? 1 : 0;
+    if (tid == 0 && loaded) {
+      tc::fence_after_sync();
+      // B planes are contiguous, i.e. one K-major operand of 32 s rows: the MMA
+      // of A digit p against it (N = 32 s) adds d_p e_q into columns
+      // (p + q - 2) 32, the region of level p + q. The p = 1 chain starts the
+      // kept levels 2 .. s + 1 (columns below 32 s); columns from 32 s on hold
+      // levels above s + 1, which are never read.
+      const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
+      const uint32_t idesc_s = tc::idesc_bf16_f32(TC_BM, TC_BN * s);
+      const int steps = bk / 16;
+      for (int p = 1; p <= s; ++p)
+        for (int st = 0; st < steps; ++st)
+          tc::mma_bf16(taddr + uint32_t((p - 1) * TC_BN), tc::smem_desc(a0 + (p - 1) * pA + 256 * st, 128, 16 * bk),
+                       tc::smem_desc(b0 + 256 * st, 128, 16 * bk), idesc_s, (p == 1 && st == 0) ? 0u : 1u);
+      tc::mma_commit(&mbar);
+    }
+    __syncthreads();
+    if (s_issued) {
+      if (!tc::mbar_wait_bounded(&mbar, mph, kPolls)) {
+        atomicExch(&s_fail, 1);
+        tc::mbar_wait_bounded(&mbar, mph, kPolls);    // let the MMAs in flight finish (bounded)
+      }
+      mph ^= 1;
+    }
+    tc::fence_after_sync();
+    __syncthreads();
+    if (s_fail) break;
+    // ---- exact level sums -> int64 accumulators (TMEM lane q*32+lane, columns
+    //      ch*16..+16); levels are read four at a time, then one wait
+    const uint32_t tl = taddr + (uint32_t(q * 32) << 16) + uint32_t(ch * 16);
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      if (2 + 4 * g > s + 1) break;
+      uint32_t v[64];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int L = 2 + 4 * g + u;
+        if (L <= s + 1) tc::tmem_ld16_nowait(tl + uint32_t((L - 2) * TC_BN), v + 16 * u);
+        else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[16 * u + j] = 0u;
+        }
+      }
+      tc::tmem_wait_ld64(v);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int L = 2 + 4 * g + u;
+        if (L > s + 1) break;
+        const int sh = 7 * (3 - u);                 // 7 (5 - L) for H, 7 (9 - L) for Lo
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const long long iv = (long long)float_to_int_small(__uint_as_float(v[16 * u + j])) << sh;
+          if (g == 0) accH[j] += iv; else accL[j] += iv;
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+
+  const int rr = q * 32 + lane;
+  const int64_t row = m0 + rr;
+  const int64_t c0 = n0 + ch * 16;
+  const int64_t row_off = d.c_rdiv > 0 ? (row / d.c_rdiv) * d.c_rs + (row % d.c_rdiv) * d.c_rs2 : row * d.c_rs;
+  double* const crow = d.C + bidx * d.c_bs + row_off;
+  const bool plain = (d.alpha == 1.0 && d.beta == 0.0);
+  auto store = [&](int j, long long H, long long Lo) {
+    store_out(crow + (c0 + j) * d.c_cs, H, Lo, Er[rr], Ec[ch * 16 + j], plain, d.alpha, d.beta);
+  };
+  if (!s_fail) {
+    if (d.ksplit == 1) {
+      if (row < d.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < d.N) store(j, accH[j], accL[j]);
+      }
+    } else {
+      // integer partials meet in L2; the last CTA of the tile rounds and writes C
+      const int64_t tile_id = (bidx * d.mt + mtile) * d.nt + ntile;
+      unsigned long long* acc = reinterpret_cast<unsigned long long*>(d.acc) + tile_id * (2 * TC_BM * TC_BN);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int cc = ch * 16 + j;
+        if (accH[j]) atomicAdd(acc + cc * TC_BM + rr, (unsigned long long)accH[j]);
+        if (accL[j]) atomicAdd(acc + TC_BM * TC_BN + cc * TC_BM + rr, (unsigned long long)accL[j]);
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        const int old = atomicAdd(d.cnt + tile_id, 1);
+        s_last = (old == d.ksplit - 1);
+        if (s_last) d.cnt[tile_id] = 0;
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int cc = ch * 16 + j;
+          accH[j] = (long long)__ldcg(acc + cc * TC_BM + rr);
+          accL[j] = (long long)__ldcg(acc + TC_BM * TC_BN + cc * TC_BM + rr);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int cc = ch * 16 + j;
+          acc[cc * TC_BM + rr] = 0;
+          acc[TC_BM * TC_BN + cc * TC_BM + rr] = 0;
+          if (row < d.M && c0 + j < d.N) store(j, accH[j], accL[j]);
+        }
+      }
+    }
+  } else {
+    // a wait gave up: raise the flag and leave NaN in this CTA's outputs
+    if (tid == 0) atomicOr(err, DEV_TIMEOUT);
+    if (row < d.M)
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j < d.N)
+          d.C[bidx * d.c_bs + row_off + (c0 + j) * d.c_cs] = __longlong_as_double(0x7FF8000000000000LL);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, ncols);
+}
+
 }  // namespace
 
 int tc_digits_for_accuracy(double rel) {
@@ -591,8 +888,35 @@ int tc_digits_for_accuracy(double rel) {
   return s;
 }
 
+static std::atomic<int> g_gemm_mode{0};
+int set_gemm_mode(int mode) {
+  if (mode < 0 || mode > 2) return TT_EINVAL;
+  g_gemm_mode.store(mode);
+  return TT_OK;
+}
+
+// Above this many bytes of digit planes a group runs fused: writing and
+// re-reading the planes through HBM then costs more than splitting inside the
+// product kernel (measured: fused wins on the batched sums' GB-sized groups and
+// loses on the 10 MB groups of a single sum, where the separate split kernel's
+// many warps hide the latency better).
+constexpr int64_t kFusedPlaneBytes = int64_t(64) << 20;
+
 void gemm_tc_prepare(std::vector<GemmDesc>& g, int s, int target_ctas, TcPlan* plan, long long* acc_base,
                      int* ex_base, int* cbase, uint8_t* plane_base) {
+  const int mode = g_gemm_mode.load();
+  bool fused = mode == 2;
+  if (mode == 0) {
+    int64_t pl_est = 0;
+    for (const auto& d : g) {
+      const int64_t K1 = std::max<int64_t>(d.K, 1);
+      pl_est += int64_t(d.batch) * (ceil_div(std::max<int64_t>(d.M, 1), TC_BM) * TC_BM +
+                                    ceil_div(std::max<int64_t>(d.N, 1), TC_BN) * TC_BN) *
+                ceil_div(K1, 16) * 16 * s * 2;
+    }
+    fused = pl_est > kFusedPlaneBytes;
+  }
+  plan->fused = fused;
   int64_t t = 0, eb = 0, sb = 0, acc = 0, ex = 0, c = 0, pl = 0;
   int64_t tiles_total = 0;
   for (auto& d : g) {
@@ -624,23 +948,40 @@ void gemm_tc_prepare(std::vector<GemmDesc>& g, int s, int target_ctas, TcPlan* p
     d.tile_begin = t;
     t += base * d.ksplit;
     d.exp_begin = eb;
-    const int64_t kb = ceil_div(K1, EX_IN);
-    if (d.K > kLocalExpK)
-      eb += int64_t(d.batch) *
-            (ceil_div(std::max<int64_t>(d.M, 1), EX_OUT) + ceil_div(std::max<int64_t>(d.N, 1), EX_OUT)) * kb;
-    d.lx = d.K <= kLocalExpK ? 1 : 0;
     d.split_begin = sb;
-    sb += int64_t(d.batch) * (int64_t(d.mt) * 4 + d.nt) * (d.lx ? 1 : d.nkc);
-    d.ex_row = ex_base ? ex_base + ex : nullptr;
-    ex += int64_t(d.batch) * d.M;
-    d.ex_col = ex_base ? ex_base + ex : nullptr;
-    ex += int64_t(d.batch) * d.N;
-    const int64_t pa_bytes = int64_t(d.batch) * d.mt * d.nkc * s * (TC_BM * d.bkc * 2);
-    const int64_t pb_bytes = int64_t(d.batch) * d.nt * d.nkc * s * (TC_BN * d.bkc * 2);
-    d.pa = plane_base ? plane_base + pl : nullptr;
-    pl += pa_bytes;
-    d.pb = plane_base ? plane_base + pl : nullptr;
-    pl += pb_bytes;
+    d.lx = d.K <= kLocalExpK ? 1 : 0;
+    d.ex_row = d.ex_col = nullptr;
+    d.pa = d.pb = nullptr;
+    if (fused) {
+      // the product kernel scans its own rows / columns when that is one short
+      // pass (no K split, short K); else the exponent pass writes tags it reads
+      d.lx = (d.ksplit == 1 && d.K <= kLocalExpK) ? 1 : 0;
+      if (!d.lx) {
+        const int64_t kb = ceil_div(K1, EX_IN);
+        eb += int64_t(d.batch) *
+              (ceil_div(std::max<int64_t>(d.M, 1), EX_OUT) + ceil_div(std::max<int64_t>(d.N, 1), EX_OUT)) * kb;
+        d.ex_row = ex_base ? ex_base + ex : nullptr;
+        ex += int64_t(d.batch) * d.M;
+        d.ex_col = ex_base ? ex_base + ex : nullptr;
+        ex += int64_t(d.batch) * d.N;
+      }
+    } else {
+      const int64_t kb = ceil_div(K1, EX_IN);
+      if (d.K > kLocalExpK)
+        eb += int64_t(d.batch) *
+              (ceil_div(std::max<int64_t>(d.M, 1), EX_OUT) + ceil_div(std::max<int64_t>(d.N, 1), EX_OUT)) * kb;
+      sb += int64_t(d.batch) * (int64_t(d.mt) * 4 + d.nt) * (d.lx ? 1 : d.nkc);
+      d.ex_row = ex_base ? ex_base + ex : nullptr;
+      ex += int64_t(d.batch) * d.M;
+      d.ex_col = ex_base ? ex_base + ex : nullptr;
+      ex += int64_t(d.batch) * d.N;
+      const int64_t pa_bytes = int64_t(d.batch) * d.mt * d.nkc * s * (TC_BM * d.bkc * 2);
+      const int64_t pb_bytes = int64_t(d.batch) * d.nt * d.nkc * s * (TC_BN * d.bkc * 2);
+      d.pa = plane_base ? plane_base + pl : nullptr;
+      pl += pa_bytes;
+      d.pb = plane_base ? plane_base + pl : nullptr;
+      pl += pb_bytes;
+    }
     d.P = nullptr;
     d.acc = nullptr;
     d.cnt = nullptr;
@@ -671,9 +1012,25 @@ int gemm_tc_launch(const GemmDesc* d_descs, int ndesc, const TcPlan& plan, int s
   static bool attr = false;
   if (!attr) {
     TTR_CHECK_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 164 * 1024));
+    TTR_CHECK_CUDA(cudaFuncSetAttribute(gemm_tcf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 164 * 1024));
     attr = true;
   }
   TcArgs a{d_descs, ndesc, s, epoch};
+  if (plan.fused) {
+    if (plan.exp_blocks > 0) {
+      TTR_PREFER_SHARED(tc_exponent_kernel);
+      tc_exponent_kernel<<<unsigned(plan.exp_blocks), 256, 0, st>>>(a);
+      TTR_CHECK_LAUNCH();
+    }
+    cudaEvent_t e0;
+    const bool prof = prof_gemm_begin(st, &e0);
+    TTR_PREFER_SHARED(gemm_tcf_kernel);
+    gemm_tcf_kernel<<<unsigned(plan.tiles), TC_THREADS, smem, st>>>(a, err);
+    TTR_CHECK_LAUNCH();
+    prof_count_launch(plan.exp_blocks > 0 ? 2 : 1);
+    if (prof) prof_gemm_end(st, flops);
+    return TT_OK;
+  }
   if (plan.exp_blocks > 0) {
     TTR_PREFER_SHARED(tc_exponent_kernel);
     tc_exponent_kernel<<<unsigned(plan.exp_blocks), 256, 0, st>>>(a);

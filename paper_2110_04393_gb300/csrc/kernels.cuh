@@ -63,7 +63,14 @@ int gemm_launch(const GemmDesc* d_descs, int ndesc, int64_t tiles, double flops,
 // first group and is left zero. *err (device) becomes 1 if a bounded wait gave up.
 struct TcPlan {
   int64_t tiles = 0, exp_blocks = 0, split_blocks = 0, acc_words = 0, ex_ints = 0, counters = 0, plane_bytes = 0;
+  bool fused = true;   // one launch per group (exponents and digit split inside the product kernel)
 };
+// 0 (default): per group, fused when its digit planes would exceed 64 MB, else
+// three-pass; 1: always the three-pass form (exponent pass, digit planes in
+// global memory, products); 2: always fused (exponents -- scanned in the
+// product kernel for short unsplit K, else one exponent pass -- and the digit
+// split inside the product kernel). Bit-identical results.
+int set_gemm_mode(int mode);
 int tc_digits_for_accuracy(double rel);
 void gemm_tc_prepare(std::vector<GemmDesc>& g, int s, int target_ctas, TcPlan* plan, long long* acc_base,
                      int* ex_base, int* cbase, uint8_t* plane_base);

@@ -13,6 +13,8 @@ struct SumProblem {
   std::vector<int64_t> ell;    // [N+1] clamped sketch ranks
   std::vector<const double*> cores;
   std::vector<double> coeffs;
+  tt_allreduce_fn allreduce = nullptr;   // summand-sharded rounding: sums the sketch over the ranks
+  void* allreduce_ctx = nullptr;
   int64_t r(int j, int n) const { return R[size_t(j) * (N + 1) + n]; }
   int64_t o(int j, int n) const { return off[size_t(j) * (N + 1) + n]; }
   const double* core(int j, int n) const { return cores[size_t(j) * N + (n - 1)]; }   // n is 1-based

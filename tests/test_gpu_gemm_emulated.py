@@ -151,3 +151,66 @@ def test_nonfinite_rows_and_columns_give_nan():
     keep_c = [c for c in range(20) if c != 4]
     A2, B2 = A[keep_r], B[:, keep_c]
     assert np.allclose(C[np.ix_(keep_r, keep_c)], A2 @ B2, rtol=1e-13, atol=1e-13)
+
+
+@pytest.fixture
+def _gemm_mode_restore():
+    yield
+    tt.set_gemm_mode(tt.GEMM_AUTO)
+
+
+@pytest.mark.parametrize("M,N,K,digits", [(300, 30, 200, 8), (30, 200, 3000, 8), (2048, 24, 480, 6),
+                                          (130, 70, 1100, 2), (5, 3, 7, 4), (257, 33, 64, 8)])
+def test_fused_and_three_pass_products_are_bit_identical(M, N, K, digits, _gemm_mode_restore):
+    """The single-launch product (exponent scan and digit split in the product
+    kernel) and the three-pass form compute the same integers: equal bits."""
+    rng = np.random.default_rng(M + 7 * N + K)
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-20, 20, size=(M, 1)))
+    B = rng.standard_normal((K, N)) * np.exp(rng.uniform(-20, 20, size=(1, N)))
+    A[M // 2, :] = 0.0
+    C0 = rng.standard_normal((M, N))
+    outs = []
+    for mode in (tt.GEMM_THREE_PASS, tt.GEMM_FUSED):
+        tt.set_gemm_mode(mode)
+        Ad = torch.from_numpy(A).cuda()
+        Bd = torch.from_numpy(B).cuda()
+        Cd = torch.from_numpy(C0.copy()).cuda()
+        tt.tt_gemm_emulated_f64(Ad, Bd, Cd, alpha=-0.5, beta=1.0, digits=digits)
+        Ct = torch.from_numpy(C0.T.copy()).cuda().t()      # a transposed output view, A given transposed
+        tt.tt_gemm_emulated_f64(torch.from_numpy(A.T.copy()).cuda().t(), Bd, Ct, digits=digits)
+        torch.cuda.synchronize()
+        outs.append((Cd.cpu(), Ct.cpu()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    ref = A @ B
+    scale = np.abs(A).max(axis=1, keepdims=True) * np.abs(B).max(axis=0, keepdims=True)
+    assert np.all(np.abs(outs[1][1].numpy() - ref) <= K * 2.0 ** (4 - 7 * digits) * scale + 2.0 ** -52 * np.abs(ref))
+
+
+def test_fused_products_flag_non_finite_rows(_gemm_mode_restore):
+    tt.set_gemm_mode(tt.GEMM_FUSED)
+    A = np.ones((40, 50))
+    A[3, 7] = np.inf
+    B = np.ones((50, 20))
+    B[9, 5] = np.nan
+    C = _run(A, B, 8)
+    assert np.all(np.isnan(C[3, :])) and np.all(np.isnan(C[:, 5]))
+    mask = np.ones_like(C, dtype=bool)
+    mask[3, :] = False
+    mask[:, 5] = False
+    assert np.all(C[mask] == 50.0)
+
+
+@pytest.mark.parametrize("tol", [0.0, 1e-8])
+def test_mixed_rounding_identical_in_both_gemm_modes(tol, _gemm_mode_restore):
+    import synth
+    dims = [30, 40, 36, 30, 40]
+    N = len(dims)
+    Ys = [synth.gaussian_tt(synth.rng_for(650, j), dims, [1] + [r] * (N - 1) + [1]) for j, r in enumerate([4, 6, 5])]
+    ell = [1] + [12] * (N - 1) + [1]
+    Yd = [[torch.from_numpy(c).cuda() for c in Y] for Y in Ys]
+    res = []
+    for mode in (tt.GEMM_THREE_PASS, tt.GEMM_FUSED):
+        tt.set_gemm_mode(mode)
+        res.append([c.cpu() for c in tt.tt_round_sum_rand(Yd, ell, seed=3, tol=tol, precision="mixed")])
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
