@@ -617,6 +617,16 @@ int tt_tsqr_fallback_runs(int64_t* runs);
 int tt_set_gemm_mode(int32_t mode);
 
 /*
+ * tt_probe_fp64_rate -- diagnostic (no counterpart in the paper): the measured
+ * FP64 fused multiply-add rate of the current GPU in TFLOP/s (2 flops per
+ * FMA), from one timed launch of independent register-only FMA chains over
+ * every SM (iters steps of 8 chains per thread; about 2^16 gives a launch of a
+ * few milliseconds). The benchmark takes it as the FP64 roofline peak.
+ * Errors: TT_EINVAL, TT_ECUDA.
+ */
+int tt_probe_fp64_rate(int32_t iters, double* tflops, void* stream);
+
+/*
  * Measurement hooks (no counterpart in the paper; used by the benchmark).
  * tt_prof_enable(1) makes the library record a CUDA event pair on the caller's
  * stream around every grouped-GEMM launch (all contraction steps) and add up the

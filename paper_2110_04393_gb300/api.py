@@ -904,6 +904,14 @@ def tsqr_fallback_runs():
     return int(v.value)
 
 
+def probe_fp64_rate(iters=1 << 16, stream=None):
+    """Measured FP64 FMA rate of the current GPU (TFLOP/s), from a register-only FMA loop."""
+    v = ctypes.c_double()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    _check(nat.lib().tt_probe_fp64_rate(int(iters), ctypes.byref(v), _stream(stream, dev)))
+    return float(v.value)
+
+
 def prof_enable(on=True):
     _check(nat.lib().tt_prof_enable(1 if on else 0))
 

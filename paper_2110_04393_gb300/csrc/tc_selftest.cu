@@ -107,3 +107,58 @@ extern "C" int tt_selftest_tcgen05_bf16(int32_t M, int32_t N, int32_t K, const v
   prof_count_launch(1);
   return TT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Diagnostic: the FP64 fused multiply-add rate of the GPU. Every thread runs 8
+// independent FMA chains (the FP64 pipe's latency is covered by 8 chains x 8
+// warps x resident CTAs) for `iters` steps on register values only; the sum of
+// the chains is stored so nothing is optimized away. The timed launch covers
+// every SM with `ctas_per_sm` CTAs.
+namespace ttr {
+namespace {
+__global__ void __launch_bounds__(256) fp64_rate_kernel(int iters, double a, double b, double* out) {
+  double x[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) x[u] = double(threadIdx.x + u) * 1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = fma(x[u], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) s += x[u];
+  if (s == 12345.678) out[0] = s;        // never true for these inputs; keeps the chains live
+}
+}  // namespace
+}  // namespace ttr
+
+extern "C" int tt_probe_fp64_rate(int32_t iters, double* tflops, void* stream) {
+  using namespace ttr;
+  if (iters < 1 || !tflops) {
+    set_error("tt_probe_fp64_rate: need iters >= 1 and an output");
+    return TT_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int ctas = 4 * num_sms();
+  double* dummy = nullptr;
+  TTR_CHECK_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dummy), sizeof(double), s));
+  cudaEvent_t e0, e1;
+  TTR_CHECK_CUDA(cudaEventCreate(&e0));
+  TTR_CHECK_CUDA(cudaEventCreate(&e1));
+  fp64_rate_kernel<<<ctas, 256, 0, s>>>(16, 0.999999, 1e-7, dummy);     // warm-up
+  TTR_CHECK_LAUNCH();
+  TTR_CHECK_CUDA(cudaEventRecord(e0, s));
+  fp64_rate_kernel<<<ctas, 256, 0, s>>>(iters, 0.999999, 1e-7, dummy);
+  TTR_CHECK_LAUNCH();
+  TTR_CHECK_CUDA(cudaEventRecord(e1, s));
+  TTR_CHECK_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  TTR_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(dummy, s);
+  prof_count_launch(2);
+  const double flops = 2.0 * 8.0 * double(iters) * double(ctas) * 256.0;
+  *tflops = flops / (double(ms) * 1e-3) / 1e12;
+  return TT_OK;
+}

@@ -83,3 +83,14 @@ def test_plan_replay_reports_device_status():
         plan(Ys, seed=2)
     finally:
         plan.close()
+
+
+@pytest.mark.gpu
+def test_fp64_rate_probe_in_range():
+    # the FP64 FMA rate of a GB300: well above zero and not above the unit-count
+    # ceiling (152 SMs x 2 FMA per clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s) by much
+    import paper_2110_04393_gb300 as tt
+    r = tt.probe_fp64_rate(1 << 12)
+    assert 0.3 < r < 1.4
+    with pytest.raises(tt.TTError):
+        tt.probe_fp64_rate(0)
