@@ -627,6 +627,16 @@ int tt_set_gemm_mode(int32_t mode);
 int tt_probe_fp64_rate(int32_t iters, double* tflops, void* stream);
 
 /*
+ * tt_probe_pivot_rsqrt -- diagnostic (no counterpart in the paper): compares
+ * the reciprocal square root that the Cholesky-QR pivots use (a hardware
+ * approximation with one third-order correction) with CUDA's rsqrt on n points
+ * spread over the normal range; *max_ulp is the largest distance in units in
+ * the last place, *ndiff the number of points that differ at all.
+ * Errors: TT_EINVAL, TT_ECUDA.
+ */
+int tt_probe_pivot_rsqrt(int64_t n, int64_t* max_ulp, int64_t* ndiff, void* stream);
+
+/*
  * Measurement hooks (no counterpart in the paper; used by the benchmark).
  * tt_prof_enable(1) makes the library record a CUDA event pair on the caller's
  * stream around every grouped-GEMM launch (all contraction steps) and add up the

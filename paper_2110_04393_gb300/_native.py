@@ -85,6 +85,7 @@ SIGNATURES = {
                                      c_vp, c_i64, c_i64, c_i32, c_vp, c_size, c_vp]),
     "tt_selftest_tcgen05_bf16": (c_i32, [c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "tt_probe_fp64_rate": (c_i32, [c_i32, P_dbl, c_vp]),
+    "tt_probe_pivot_rsqrt": (c_i32, [c_i64, P_i64, P_i64, c_vp]),
     "tt_prof_enable": (c_i32, [c_i32]),
     "tt_prof_reset": (c_i32, []),
     "tt_prof_read": (c_i32, [P_dbl, P_dbl, P_i64, P_i64]),

@@ -912,6 +912,15 @@ def probe_fp64_rate(iters=1 << 16, stream=None):
     return float(v.value)
 
 
+def probe_pivot_rsqrt(n=1 << 22, stream=None):
+    """(max ulp distance, points that differ) of the QR pivots' reciprocal
+    square root against CUDA's rsqrt over n points of the normal range."""
+    mu, nd = ctypes.c_int64(), ctypes.c_int64()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    _check(nat.lib().tt_probe_pivot_rsqrt(int(n), ctypes.byref(mu), ctypes.byref(nd), _stream(stream, dev)))
+    return int(mu.value), int(nd.value)
+
+
 def prof_enable(on=True):
     _check(nat.lib().tt_prof_enable(1 if on else 0))
 

@@ -150,6 +150,135 @@ __device__ bool chol_with_inverse(double* G, double* X, int k) {
   return true;
 }
 
+// 1/sqrt(d) for a positive normal d: the hardware approximation y of
+// rsqrt.approx.ftz.f64 (relative error below 2^-20) corrected by the
+// third-order terms of the binomial series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 +
+// O(e^3), e = 1 - d y^2 (Householder's method of order 2); the neglected term is
+// below 2^-58, so the result is within rounding of 1/sqrt(d). Five FP64
+// operations after the approximation instead of the longer IEEE sequence:
+// this is the pivot chain's critical step.
+__device__ __forceinline__ double rsqrt_refined(double d) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  const double t = d * y;
+  const double e = fma(-t, y, 1.0);
+  const double p = fma(0.375, e, 0.5);
+  const double r = y * e;
+  return fma(r, p, y);
+}
+
+// The same Cholesky with inverse for k <= 32 * NQ with G and X in shared
+// memory, scheduled for GB300's FP64 issue: one warp issues one FP64
+// instruction per ~64 cycles whether or not its lanes are active, and the SM
+// retires ~1.7 FP64 lanes per clock, so work is packed densely into few warp
+// instructions and the pivot chain runs alone on one SM sub-partition.
+//   * warp 0 (look-ahead): in step j it applies column j to column j+1 and to
+//     row j+1 of X (k entries, one lane each), takes the pivot d_{j+1} from
+//     lane 0, its reciprocal square root, and stores column j+1 of L and row
+//     j+1 of X scaled: L(j+1, j+1) = d rd, L(i, j+1) = G(i, j+1) rd,
+//     X(j+1, :) = X(j+1, :) rd, X(j+1, j+1) = rd;
+//   * the worker warps (sub-partitions 1..3) apply column j to rows i >= j+2:
+//     row i has exactly i entries to update, X(i, 0..j) and G(i, j+2..i), so
+//     one warp instruction covers a row (lane = position), without divisions.
+// One block barrier per step; blockDim.x must be a multiple of 128.
+template <int NQ>
+__device__ bool chol_la(double* G, double* X, int k) {
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int nww = (nt >> 5) / 4 * 3;                       // worker warps
+  const int wk = (warp >> 2) * 3 + (warp & 3) - 1;         // rank of a worker warp
+  for (int r = warp; r < k; r += (nt >> 5))
+    for (int c = lane; c < k; c += 32) X[r * k + c] = (r == c) ? 1.0 : 0.0;
+  __syncthreads();
+  if (warp == 0) {
+    const double d = G[0];
+    const bool bad = !pivot_ok(d);
+    const double rd = bad ? 1.0 : rsqrt_refined(d);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int t = lane + 32 * q;
+      if (t < k) G[t * k] = G[t * k] * rd;
+    }
+    if (lane == 0) {
+      X[0] = rd;
+      s_bad = bad ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j + 1 < k; ++j) {
+    if (s_bad) return false;
+    const int n = k - 1 - j;                       // column j+1 has rows j+1 .. k-1
+    if (warp == 0) {
+      const double l1 = G[(j + 1) * k + j];        // L(j+1, j)
+      // entry t < n: G(j+1+t, j+1); n <= t < k: X(j+1, t-n); per-lane
+      // addresses so that one instruction stream serves both
+      double v[NQ];
+      double* dst[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int t = lane + 32 * q;
+        const int tc = t < k ? t : k - 1;
+        const bool col = tc < n;
+        const double* a = col ? G + (j + 1 + tc) * k + j : X + j * k + (tc - n);
+        dst[q] = col ? G + (j + 1 + tc) * k + j + 1 : X + (j + 1) * k + (tc - n);
+        v[q] = fma(-*a, l1, *dst[q]);
+      }
+      const double d = __shfl_sync(0xffffffffu, v[0], 0);
+      const bool bad = !pivot_ok(d);
+      const double rd = bad ? 1.0 : rsqrt_refined(d);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const double o = v[q] * rd;
+        if (lane + 32 * q < k) *dst[q] = o;
+      }
+      if (lane == 0) {
+        X[(j + 1) * k + j + 1] = rd;
+        if (bad) s_bad = 1;
+      }
+    } else if (warp & 3) {
+      // rows i = j+2 .. k-1; position p < j+1 is X(i, p), the rest G(i, p+1)
+      constexpr int RB = NQ == 1 ? 4 : 2;          // rows per batch: loads first, then FMAs
+      for (int i0 = j + 2 + wk; i0 < k; i0 += RB * nww) {
+        double a[RB], b[RB][NQ], c[RB][NQ];
+        double* dp[RB][NQ];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const int ic = min(i0 + r * nww, k - 1);
+          a[r] = G[ic * k + j];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const int pc = min(lane + 32 * q, ic - 1);
+            const bool xp = pc <= j;
+            b[r][q] = xp ? X[j * k + pc] : G[(pc + 1) * k + j];
+            dp[r][q] = xp ? X + ic * k + pc : G + ic * k + pc + 1;
+            c[r][q] = *dp[r][q];
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const int i = i0 + r * nww;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const double o = fma(-a[r], b[r][q], c[r][q]);
+            if (i < k && lane + 32 * q < i) *dp[r][q] = o;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return s_bad == 0;
+}
+
+// Cholesky with inverse: the scheduled form in shared memory for k <= 96, the
+// general one (shared or global scratch) above.
+__device__ bool chol_inverse(double* G, double* X, int k) {
+  if (k <= 32) return chol_la<1>(G, X, k);
+  if (k <= 64) return chol_la<2>(G, X, k);
+  if (k <= CQ_SMEM_K) return chol_la<3>(G, X, k);
+  return chol_with_inverse(G, X, k);
+}
+
 // Position (i, j), i <= j, of entry p of the row-wise packed upper triangle.
 __device__ __forceinline__ void tri_ij(int p, int k, int* i, int* j) {
   int r = 0;
@@ -260,7 +389,7 @@ __device__ void cqr_decide(double* G, double* X, double* G0, int k, int64_t m, i
       return;
     }
   }
-  bool ok = chol_with_inverse(G, X, k);
+  bool ok = chol_inverse(G, X, k);
   bool shifted = false;
   if (!ok) {
     __shared__ double s_shift;
@@ -272,7 +401,7 @@ __device__ void cqr_decide(double* G, double* X, double* G0, int k, int64_t m, i
     __syncthreads();
     for (int idx = tid; idx < k * k; idx += nt) G[idx] = G0[idx] + (((idx / k) == (idx % k)) ? s_shift : 0.0);
     __syncthreads();
-    ok = chol_with_inverse(G, X, k);
+    ok = chol_inverse(G, X, k);
     shifted = true;
   }
   if (!ok) {                                    // not even the shifted Gram is positive definite
@@ -1164,3 +1293,48 @@ void qr_fallback_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_
 }
 
 }  // namespace ttr
+
+// ---------------------------------------------------------------------------
+// Diagnostic: the pivot reciprocal square root against CUDA's rsqrt over n
+// points of [1, 4) scaled by 4^s, s in [-480, 480] (so every exponent parity
+// and nearly the whole normal range).
+namespace ttr {
+namespace {
+__global__ void pivot_rsqrt_check_kernel(int64_t n, unsigned long long* max_ulp, unsigned long long* ndiff) {
+  unsigned long long worst = 0, cnt = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double f = 1.0 + 3.0 * double(i) / double(n);
+    const double x = ldexp(f, 2 * int(i % 961 - 480));
+    const double a = rsqrt_refined(x), b = rsqrt(x);
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const unsigned long long du = (unsigned long long)(ia > ib ? ia - ib : ib - ia);   // same sign: ulps apart
+    worst = du > worst ? du : worst;
+    cnt += du != 0;
+  }
+  atomicMax(max_ulp, worst);
+  atomicAdd(ndiff, cnt);
+}
+}  // namespace
+}  // namespace ttr
+
+extern "C" int tt_probe_pivot_rsqrt(int64_t n, int64_t* max_ulp, int64_t* ndiff, void* stream) {
+  using namespace ttr;
+  if (n < 1 || !max_ulp || !ndiff) {
+    set_error("tt_probe_pivot_rsqrt: need n >= 1 and outputs");
+    return TT_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* d = nullptr;
+  TTR_CHECK_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), 2 * sizeof(unsigned long long), s));
+  TTR_CHECK_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), s));
+  pivot_rsqrt_check_kernel<<<4 * num_sms(), 256, 0, s>>>(n, d, d + 1);
+  TTR_CHECK_LAUNCH();
+  prof_count_launch(1);
+  unsigned long long h[2] = {0, 0};
+  TTR_CHECK_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+  TTR_CHECK_CUDA(cudaStreamSynchronize(s));
+  cudaFreeAsync(d, s);
+  *max_ulp = int64_t(h[0]);
+  *ndiff = int64_t(h[1]);
+  return TT_OK;
+}

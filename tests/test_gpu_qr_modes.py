@@ -105,3 +105,33 @@ def test_plan_in_each_mode_matches_eager():
         Xe = to_host(tt.tt_round_sum_rand(Yd, ell, seed=5, tol=1e-9))
         assert O.ranks_of(Xp) == O.ranks_of(Xe)
         assert rel_diff(Xp, Xe) <= 1e-13
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["coop", "chain"])
+@pytest.mark.parametrize("k", [1, 2, 16, 31, 32, 33, 47, 64, 65, 96])
+def test_sketch_rank_sizes_match_oracle(mode, k):
+    # every width class of the shared-memory Cholesky with inverse (one, two or
+    # three 32-lane chunks per column) through the sketch QRs of bonds 1 and 2
+    # (100 x k and 12k x k), and no Householder fallback
+    dims = [100, 12, 100]
+    Y = synth.gaussian_tt(synth.rng_for(160, k), dims, [1, 100, 100, 1])
+    ell = O.clamp_ranks(dims, [1, k, k, 1])
+    sk = synth.gaussian_tt(synth.rng_for(161, k), dims, ell)
+    Xo = O.round_sum_randorth([Y], sk)
+    tt.set_qr_mode(mode)
+    before = tt.tsqr_fallback_runs()
+    Xg = to_host(tt.tt_round_sum_rand([to_dev(Y)], ell, sketch=to_dev(sk)))
+    assert tt.tsqr_fallback_runs() == before
+    assert O.ranks_of(Xg) == O.ranks_of(Xo)
+    assert rel_diff(Xg, Xo) <= FP64_TOL
+    for n in range(len(Xg) - 1):
+        Vn = O.V(Xg[n])
+        assert np.abs(Vn.T @ Vn - np.eye(Vn.shape[1])).max() < 1e-13
+
+
+def test_pivot_rsqrt_matches_cuda_rsqrt():
+    # the QR pivots' reciprocal square root (approximation + third-order
+    # correction) against CUDA's rsqrt over the normal range
+    max_ulp, ndiff = tt.probe_pivot_rsqrt(1 << 22)
+    assert max_ulp <= 1
+    assert ndiff <= (1 << 22) // 1000
