@@ -470,23 +470,36 @@ __device__ __forceinline__ void cqr_pass_body(const CqrPass& a, const int blk) {
       for (int c = lane; c < k; c += 32) Rs[i * k + c] = __ldcg(Rin + i * k + c);
   __syncthreads();
   if (Rin) {
-    // T2 = T R^{-1} (R^{-1} upper): item (row, column pair c1 = cp, c2 = k-1-cp)
-    // so every item costs k + 1 fused multiply-adds
-    // (a first-order correction I - E/2 is a full matrix: all k terms)
+    // T2 = T R^{-1} (R^{-1} upper; a first-order correction I - E/2 is a full
+    // matrix: all k terms): one output entry per item, four independent
+    // partial sums, items down the columns so that the lanes of a warp share
+    // the length c + 1 of their sums (a warp instruction costs the same
+    // whatever its active lanes)
     const double* Rr = big ? Rin : Rs;
-    const int ncp = (k + 1) / 2;
-    for (int it = tid; it < b * ncp; it += nt) {
-      const int r = it / ncp, cp = it - r * ncp;
-      const int c1 = cp, c2 = k - 1 - cp;
-      const int j1 = first_order ? k - 1 : c1, j2 = first_order ? k - 1 : c2;
-      double s1 = 0.0, s2 = 0.0;
-      for (int j = 0; j <= j2; ++j) {
-        const double tj = T[r * k + j];
-        if (j <= j1) s1 = fma(tj, big ? __ldcg(Rr + j * k + c1) : Rr[j * k + c1], s1);
-        s2 = fma(tj, big ? __ldcg(Rr + j * k + c2) : Rr[j * k + c2], s2);
+    for (int i = tid; i < b * k; i += nt) {
+      const int c = i / b, r = i - c * b;
+      const int jn = first_order ? k : c + 1;
+      const double* tr = T + r * k;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      if (big) {
+        for (; j + 4 <= jn; j += 4) {
+          s0 = fma(tr[j], __ldcg(Rr + j * k + c), s0);
+          s1 = fma(tr[j + 1], __ldcg(Rr + (j + 1) * k + c), s1);
+          s2 = fma(tr[j + 2], __ldcg(Rr + (j + 2) * k + c), s2);
+          s3 = fma(tr[j + 3], __ldcg(Rr + (j + 3) * k + c), s3);
+        }
+        for (; j < jn; ++j) s0 = fma(tr[j], __ldcg(Rr + j * k + c), s0);
+      } else {
+        for (; j + 4 <= jn; j += 4) {
+          s0 = fma(tr[j], Rr[j * k + c], s0);
+          s1 = fma(tr[j + 1], Rr[(j + 1) * k + c], s1);
+          s2 = fma(tr[j + 2], Rr[(j + 2) * k + c], s2);
+          s3 = fma(tr[j + 3], Rr[(j + 3) * k + c], s3);
+        }
+        for (; j < jn; ++j) s0 = fma(tr[j], Rr[j * k + c], s0);
       }
-      T2[r * k + c1] = s1;
-      T2[r * k + c2] = s2;
+      T2[r * k + c] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
     T = T2;
@@ -520,19 +533,17 @@ __device__ __forceinline__ void cqr_pass_body(const CqrPass& a, const int blk) {
   }
   // two-level arrival: the last CTA of each group of CQ_GROUP sums the group's
   // partials (block order) into a group partial; the last group sums those.
-  __threadfence();
   __syncthreads();
   const int grp = blk / CQ_GROUP;
   const int ngrp = (a.P + CQ_GROUP - 1) / CQ_GROUP;
   const int gsize = min(CQ_GROUP, a.P - grp * CQ_GROUP);
   if (tid == 0) {
-    const int old = atomicAdd(a.counter + 1 + grp, 1);
+    const int old = atom_add_acq_rel_gpu(a.counter + 1 + grp, 1);
     s_last = (old == gsize - 1);
     if (s_last) a.counter[1 + grp] = 0;
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
   {
     double* Gg = a.Gpart + int64_t(a.P + grp) * npair;
     const double* base = a.Gpart + int64_t(grp) * CQ_GROUP * npair;
@@ -546,16 +557,14 @@ __device__ __forceinline__ void cqr_pass_body(const CqrPass& a, const int blk) {
       Gg[p] = acc;
     }
   }
-  __threadfence();
   __syncthreads();
   if (tid == 0) {
-    const int old = atomicAdd(a.counter, 1);
+    const int old = atom_add_acq_rel_gpu(a.counter, 1);
     s_last = (old == ngrp - 1);
     if (s_last) *a.counter = 0;
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
 
   // ---- last group: G = sum of group partials in order, then check or factor
   double* G = big ? a.big : sm;                 // k x k
@@ -722,12 +731,16 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
       } else {
         // T := T Rinv (upper triangular, or the full first-order correction):
         // one output entry per item, four independent partial sums (FP64
-        // issues a dependent operation only every ~65 cycles)
+        // issues a dependent operation only every ~65 cycles). Items run
+        // down the columns, so the lanes of a warp share one or two columns
+        // and hence the length c + 1 of their triangular sums: a warp
+        // instruction costs the same whatever its active lanes, so mixing
+        // columns in a warp would pay the longest sum on every lane.
         double* T2 = U + k * k;
         for (int i = tid; i < k * k; i += nt) Rs[i] = __ldcg(a.Rinv + i);
         __syncthreads();
         for (int i = tid; i < b * k; i += nt) {
-          const int r = i / k, c = i - r * k;
+          const int c = i / b, r = i - c * b;
           const int jn = first_order ? k : c + 1;
           const double* tr = T + r * k;
           double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -739,7 +752,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
             s3 = fma(tr[j + 3], Rs[(j + 3) * k + c], s3);
           }
           for (; j < jn; ++j) s0 = fma(tr[j], Rs[j * k + c], s0);
-          T2[i] = (s0 + s1) + (s2 + s3);
+          T2[r * k + c] = (s0 + s1) + (s2 + s3);
         }
         __syncthreads();
         for (int i = tid; i < b * k; i += nt) T[i] = T2[i];
@@ -804,19 +817,17 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
       Gp[p] = (g0 + g1) + (g2 + g3);
     }
     // two-level arrival: the last CTA of each group sums its group's partials
-    __threadfence();
     __syncthreads();
     const int grp = lb / CQ_GROUP;
     const int gsize = min(CQ_GROUP, a.P - grp * CQ_GROUP);
     if (tid == 0) {
-      const int old = atomicAdd(st + 6 + grp, 1);
+      const int old = atom_add_acq_rel_gpu(st + 6 + grp, 1);
       s_flag = (old == gsize - 1);
       if (s_flag) st[6 + grp] = 0;
     }
     __syncthreads();
     bool decider = false;
     if (s_flag) {
-      __threadfence();
       double* Gg = a.Gpart + int64_t(a.P + grp) * npair;
       const double* base = a.Gpart + int64_t(grp) * CQ_GROUP * npair;
       for (int p = tid; p < npair; p += 2 * nt) {
@@ -838,10 +849,9 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
         Gg[p] = u[0];
         if (p2 < npair) Gg[p2] = v[0];
       }
-      __threadfence();
       __syncthreads();
       if (tid == 0) {
-        const int old = atomicAdd(st + 5, 1);
+        const int old = atom_add_acq_rel_gpu(st + 5, 1);
         s_flag = (old == ngrp - 1);
         if (s_flag) st[5] = 0;
       }
@@ -849,7 +859,6 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
       decider = s_flag;
     }
     if (decider) {
-      __threadfence();
       double* G = U;
       double* X = G + k * k;
       double* G0 = X + k * k;
@@ -897,9 +906,8 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
           *a.rank_out = k;
         }
       }
-      __threadfence();
       __syncthreads();
-      if (tid == 0) st_release_gpu(released, pass + 1);
+      if (tid == 0) st_release_gpu(released, pass + 1);   // cumulative over the block's writes
     } else {
       if (final_pass) return;
       if (tid == 0) {
@@ -912,7 +920,6 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
           }
           __nanosleep(64);
         }
-        __threadfence();
         s_flag = ok;
       }
       __syncthreads();

@@ -102,17 +102,15 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_f64_kernel(const GemmDesc* 
       int64_t gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
       if (gm < d.M && gn < d.N) d.P[(b * d.ksplit + ks) * MN + gm * d.N + gn] = acc[i][j];
     }
-  __threadfence();
   __syncthreads();
   const int64_t tile_id = (b * d.mt + mtile) * d.nt + ntile;
   if (tid == 0) {
-    const int old = atomicAdd(d.cnt + tile_id, 1);
+    const int old = atom_add_acq_rel_gpu(d.cnt + tile_id, 1);
     s_last = (old == d.ksplit - 1);
     if (s_last) d.cnt[tile_id] = 0;
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
   // sum the partials in split order; eight independent loads per output in flight
 #pragma unroll
   for (int i = 0; i < 2; ++i)

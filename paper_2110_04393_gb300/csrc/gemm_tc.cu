@@ -545,16 +545,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int
         if (accH[j]) atomicAdd(acc + cc * TC_BM + rr, (unsigned long long)accH[j]);
         if (accL[j]) atomicAdd(acc + TC_BM * TC_BN + cc * TC_BM + rr, (unsigned long long)accL[j]);
       }
-      __threadfence();
       __syncthreads();
       if (tid == 0) {
-        const int old = atomicAdd(d.cnt + tile_id, 1);
+        const int old = atom_add_acq_rel_gpu(d.cnt + tile_id, 1);
         s_last = (old == d.ksplit - 1);
         if (s_last) d.cnt[tile_id] = 0;
       }
       __syncthreads();
       if (s_last) {
-        __threadfence();
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int cc = ch * 16 + j;
@@ -841,16 +839,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tcf_kernel(TcArgs args, in
         if (accH[j]) atomicAdd(acc + cc * TC_BM + rr, (unsigned long long)accH[j]);
         if (accL[j]) atomicAdd(acc + TC_BM * TC_BN + cc * TC_BM + rr, (unsigned long long)accL[j]);
       }
-      __threadfence();
       __syncthreads();
       if (tid == 0) {
-        const int old = atomicAdd(d.cnt + tile_id, 1);
+        const int old = atom_add_acq_rel_gpu(d.cnt + tile_id, 1);
         s_last = (old == d.ksplit - 1);
         if (s_last) d.cnt[tile_id] = 0;
       }
       __syncthreads();
       if (s_last) {
-        __threadfence();
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int cc = ch * 16 + j;

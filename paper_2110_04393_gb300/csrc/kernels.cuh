@@ -4,6 +4,17 @@
 
 namespace ttr {
 
+// Arrival on a counter at GPU scope with acquire-release semantics. Called by
+// one thread right after a block barrier: the release covers the whole block's
+// earlier writes (cumulativity through the barrier) and the acquire makes the
+// writes published by the other arrivals visible to the block once it passes
+// its next barrier, so no thread needs a separate fence.
+__device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v) {
+  int old;
+  asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // ----------------------------------------------------------------------------
 // Grouped, batched, strided FP64 GEMM:  C_b = alpha * A_b B_b + beta * C_b for
 // every descriptor and batch entry b. Element (r, c) of A_b is at

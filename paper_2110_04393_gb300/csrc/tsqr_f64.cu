@@ -183,16 +183,14 @@ __global__ void __launch_bounds__(TQ_THREADS) tsqr_up_kernel(TsqrArgs a) {
     const int parent = q >> 1;
     const int nchild = (2 * parent + 1 < level_count(a.P, l)) ? 2 : 1;
     const int inner = level_offset(a.P, l + 1) - a.P + parent;   // index among inner nodes
-    __threadfence();
     __syncthreads();
     if (tid == 0) {
-      const int old = atomicAdd(a.w.counters + inner, 1);
+      const int old = atom_add_acq_rel_gpu(a.w.counters + inner, 1);
       s_last = (old == nchild - 1);
       if (s_last) a.w.counters[inner] = 0;   // every child has arrived: reset for the next call
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     const int off_l = level_offset(a.P, l);
     const double* Rt = a.w.nodeR + int64_t(off_l + 2 * parent) * k * k;
     const double* Rb = a.w.nodeR + int64_t(off_l + 2 * parent + 1) * k * k;
