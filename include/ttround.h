@@ -611,7 +611,9 @@ int tt_tsqr_fallback_runs(int64_t* runs);
  * exponents scanned there too for an unsplit K <= 512, else one exponent pass
  * first); 1 = three passes, the digit planes written to and re-read from
  * global memory; 0 (default) = fused for groups whose planes would exceed
- * 64 MB, else three passes. The results are bit-identical.
+ * 64 MB and whose operands the fused kernels would split at most twice over
+ * (A once per output tile along N, B once per tile along M), else three
+ * passes. The results are bit-identical.
  * Errors: TT_EINVAL for an unknown mode.
  */
 int tt_set_gemm_mode(int32_t mode);

@@ -46,6 +46,10 @@ constexpr int CQ_SMEM_K = 96;   // above this the k x k factors live in global s
 
 constexpr int CQ_MAX_PASSES = 6;
 
+// Row stride of a row block in shared memory: odd, so that the lanes of a warp
+// reading one column of consecutive rows hit distinct banks for every k.
+__host__ __device__ inline int cq_ts(int k) { return k | 1; }
+
 struct CqrPass {
   int64_t m;
   int k, b, P, pass;
@@ -455,15 +459,16 @@ __device__ __forceinline__ void cqr_pass_body(const CqrPass& a, const int blk) {
   const bool big = (a.big != nullptr);
 
   // ---- row block: T = src rows (times R^{-1} of the previous pass), stored, partial Gram
-  double* T = sm;                 // b x k
-  double* T2 = T + b * k;         // b x k
-  double* Rs = T2 + b * k;        // k x k (shared when small)
+  const int ts = cq_ts(k);
+  double* T = sm;                 // b x k, row stride ts
+  double* T2 = T + b * ts;        // b x k, row stride ts
+  double* Rs = T2 + b * ts;       // k x k (shared when small)
   const double* Rin = (a.pass == 0) ? nullptr : a.Rinv;
   const int64_t r0 = int64_t(blk) * b;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int r = warp; r < b; r += nw) {
     const int64_t gr = r0 + r;
-    for (int c = lane; c < k; c += 32) T[r * k + c] = (gr < a.m) ? src[gr * s_rs + c * s_cs] : 0.0;
+    for (int c = lane; c < k; c += 32) T[r * ts + c] = (gr < a.m) ? src[gr * s_rs + c * s_cs] : 0.0;
   }
   if (Rin && !big)
     for (int i = warp; i < k; i += nw)
@@ -479,7 +484,7 @@ __device__ __forceinline__ void cqr_pass_body(const CqrPass& a, const int blk) {
     for (int i = tid; i < b * k; i += nt) {
       const int c = i / b, r = i - c * b;
       const int jn = first_order ? k : c + 1;
-      const double* tr = T + r * k;
+      const double* tr = T + r * ts;
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
       int j = 0;
       if (big) {
@@ -499,7 +504,7 @@ __device__ __forceinline__ void cqr_pass_body(const CqrPass& a, const int blk) {
         }
         for (; j < jn; ++j) s0 = fma(tr[j], Rr[j * k + c], s0);
       }
-      T2[r * k + c] = (s0 + s1) + (s2 + s3);
+      T2[r * ts + c] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
     T = T2;
@@ -508,7 +513,7 @@ __device__ __forceinline__ void cqr_pass_body(const CqrPass& a, const int blk) {
     for (int r = warp; r < b; r += nw) {
       const int64_t gr = r0 + r;
       if (gr < a.m)
-        for (int c = lane; c < k; c += 32) dst[gr * d_rs + c * d_cs] = T[r * k + c];
+        for (int c = lane; c < k; c += 32) dst[gr * d_rs + c * d_cs] = T[r * ts + c];
     }
   if (final_pass && first_order) {
     // Q = Q1 (I - E/2) with ||E||_F <= 1e-8 has Q^T Q = I + O(||E||^2): no check needed
@@ -525,8 +530,8 @@ __device__ __forceinline__ void cqr_pass_body(const CqrPass& a, const int blk) {
     if (two) tri_ij(p + nt, k, &i2, &j2);
     double g1 = 0.0, g2 = 0.0;
     for (int r = 0; r < b; ++r) {
-      g1 = fma(T[r * k + i1], T[r * k + j1], g1);
-      if (two) g2 = fma(T[r * k + i2], T[r * k + j2], g2);
+      g1 = fma(T[r * ts + i1], T[r * ts + j1], g1);
+      if (two) g2 = fma(T[r * ts + i2], T[r * ts + j2], g2);
     }
     Gp[p] = g1;
     if (two) Gp[p + nt] = g2;
@@ -681,7 +686,7 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
 // union of [Rinv | product block] and the decision's [G | X | G0].
 __host__ __device__ inline int64_t coop_smem_doubles(int b, int k) {
   const int64_t bk = int64_t(b) * k, kk = int64_t(k) * k;
-  return bk + (3 * kk > kk + bk ? 3 * kk : kk + bk);
+  return int64_t(b) * cq_ts(k) + (3 * kk > kk + bk ? 3 * kk : kk + bk);
 }
 
 __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
@@ -693,12 +698,13 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
   const int ngrp = (a.P + CQ_GROUP - 1) / CQ_GROUP;
   int* st = a.status;
   int* released = st + 6 + ngrp;
-  double* T = sm;                       // b x k row block, kept across passes
-  double* U = sm + int64_t(b) * k;      // union
+  const int ts = cq_ts(k);
+  double* T = sm;                       // b x k row block (row stride ts), kept across passes
+  double* U = sm + int64_t(b) * ts;     // union
   const int64_t r0 = int64_t(lb) * b;
   for (int r = warp; r < b; r += nw) {
     const int64_t gr = r0 + r;
-    for (int c = lane; c < k; c += 32) T[r * k + c] = (gr < a.m) ? a.A[gr * a.a_rs + c * a.a_cs] : 0.0;
+    for (int c = lane; c < k; c += 32) T[r * ts + c] = (gr < a.m) ? a.A[gr * a.a_rs + c * a.a_cs] : 0.0;
   }
   __syncthreads();
   for (int pass = 0; pass < CQ_MAX_PASSES; ++pass) {
@@ -719,13 +725,16 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
         float* Tf = Cf + k * k;                                  // T, b x k
         for (int i = tid; i < k * k; i += nt)
           Cf[i] = float(((i % (k + 1) == 0) ? 1.0 : 0.0) - __ldcg(a.Rinv + i));
-        for (int i = tid; i < b * k; i += nt) Tf[i] = float(T[i]);
+        for (int i = tid; i < b * k; i += nt) {
+          const int r = i / k;
+          Tf[i] = float(T[r * ts + (i - r * k)]);
+        }
         __syncthreads();
         for (int i = tid; i < b * k; i += nt) {
           const int r = i / k, c = i - r * k;
           float corr = 0.0f;
           for (int j = 0; j < k; ++j) corr = fmaf(Tf[r * k + j], Cf[j * k + c], corr);
-          T[i] -= double(corr);
+          T[r * ts + c] -= double(corr);
         }
         __syncthreads();
       } else {
@@ -742,7 +751,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
         for (int i = tid; i < b * k; i += nt) {
           const int c = i / b, r = i - c * b;
           const int jn = first_order ? k : c + 1;
-          const double* tr = T + r * k;
+          const double* tr = T + r * ts;
           double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
           int j = 0;
           for (; j + 4 <= jn; j += 4) {
@@ -755,7 +764,10 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
           T2[r * k + c] = (s0 + s1) + (s2 + s3);
         }
         __syncthreads();
-        for (int i = tid; i < b * k; i += nt) T[i] = T2[i];
+        for (int i = tid; i < b * k; i += nt) {
+          const int r = i / k;
+          T[r * ts + (i - r * k)] = T2[i];
+        }
         __syncthreads();
       }
       if (final_pass) {
@@ -765,7 +777,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
         for (int r = warp; r < b; r += nw) {
           const int64_t gr = r0 + r;
           if (gr < a.m)
-            for (int c = lane; c < k; c += 32) qd[gr * qr + c * qc] = T[r * k + c];
+            for (int c = lane; c < k; c += 32) qd[gr * qr + c * qc] = T[r * ts + c];
         }
         if (cert) {
           // V(X_{n-1}) := V(X_{n-1}) R^T for this CTA's rows (in place)
@@ -808,12 +820,12 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
       double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
       int r = 0;
       for (; r + 4 <= b; r += 4) {
-        g0 = fma(T[r * k + i1], T[r * k + j1], g0);
-        g1 = fma(T[(r + 1) * k + i1], T[(r + 1) * k + j1], g1);
-        g2 = fma(T[(r + 2) * k + i1], T[(r + 2) * k + j1], g2);
-        g3 = fma(T[(r + 3) * k + i1], T[(r + 3) * k + j1], g3);
+        g0 = fma(T[r * ts + i1], T[r * ts + j1], g0);
+        g1 = fma(T[(r + 1) * ts + i1], T[(r + 1) * ts + j1], g1);
+        g2 = fma(T[(r + 2) * ts + i1], T[(r + 2) * ts + j1], g2);
+        g3 = fma(T[(r + 3) * ts + i1], T[(r + 3) * ts + j1], g3);
       }
-      for (; r < b; ++r) g0 = fma(T[r * k + i1], T[r * k + j1], g0);
+      for (; r < b; ++r) g0 = fma(T[r * ts + i1], T[r * ts + j1], g0);
       Gp[p] = (g0 + g1) + (g2 + g3);
     }
     // two-level arrival: the last CTA of each group sums its group's partials
@@ -981,7 +993,8 @@ int coop_launch(const CoopJob& job, size_t smem, cudaStream_t s) {
 
 int cqr_launch(const CqrPass& p, cudaStream_t s) {
   const size_t kk = size_t(p.k) * p.k;
-  const size_t smem = (p.big ? size_t(2) * p.b * p.k : std::max<size_t>(size_t(2) * p.b * p.k + kk, 3 * kk)) *
+  const size_t bts = size_t(p.b) * cq_ts(p.k);
+  const size_t smem = (p.big ? 2 * bts : std::max<size_t>(2 * bts + kk, 3 * kk)) *
                       sizeof(double);
   static bool attr = false;
   if (!attr) {
@@ -1005,7 +1018,7 @@ namespace {
 void qr_shape(int64_t m, int k, int* rows, int* P, int* nstat) {
   const bool big = k > CQ_SMEM_K;
   const int64_t budget = 28000 - (big ? 0 : int64_t(k) * k);                 // doubles of shared memory
-  const int64_t bmax = std::max<int64_t>(1, budget / (2 * int64_t(k)));
+  const int64_t bmax = std::max<int64_t>(1, budget / (2 * int64_t(cq_ts(k))));
   *rows = int(std::min<int64_t>(bmax, std::max<int64_t>(4, ceil_div(m, num_sms()))));
   *P = int(ceil_div(m, *rows));
   *nstat = 5 + 1 + (*P + 15) / 16 + 2;  // [0..4] chain state, arrival counters, released passes, certificate
@@ -1115,7 +1128,7 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
     job.status = b.status;
     if (cert && R && r_may_be_full) {
       const int64_t bp = ceil_div(cert->mp, int64_t(cP));
-      if (bp * b.k + int64_t(b.k) * b.k <= coop_smem_doubles(cb, b.k) - int64_t(cb) * b.k) {
+      if (bp * b.k + int64_t(b.k) * b.k <= coop_smem_doubles(cb, b.k) - int64_t(cb) * cq_ts(b.k)) {
         job.eps = cert->eps;
         job.rcap = cert->rcap;
         job.bp = int(bp);
@@ -1180,7 +1193,7 @@ __global__ void qr_batch_fold_kernel(const int* __restrict__ status, const int* 
 
 static void qr_batch_shape(int64_t m, int k, int ctas_per_job, int* rows, int* P) {
   const int64_t budget = 28000 - int64_t(k) * k;
-  const int64_t bmax = std::max<int64_t>(1, budget / (2 * int64_t(k)));
+  const int64_t bmax = std::max<int64_t>(1, budget / (2 * int64_t(cq_ts(k))));
   *rows = int(std::min<int64_t>(bmax, std::max<int64_t>(4, ceil_div(m, std::max(1, ctas_per_job)))));
   *P = int(ceil_div(m, *rows));
 }
@@ -1230,7 +1243,8 @@ int qr_batch_plan(Arena& ar, Schedule& sc, const std::vector<QrBatchJob>& jobs, 
     soff[j] = int(tot_status);
     tot_status += 5 + 1 + ngrp;
     begin[j + 1] = begin[j] + P;
-    smem = std::max(smem, std::max<size_t>(size_t(2) * rows * k + size_t(k) * k, size_t(3) * k * k) * sizeof(double));
+    smem = std::max(smem, std::max<size_t>(size_t(2) * rows * cq_ts(k) + size_t(k) * k, size_t(3) * k * k) *
+                              sizeof(double));
   }
   int* status = ar.take<int>(size_t(tot_status));
   for (int j = 0; j < nj; ++j) {

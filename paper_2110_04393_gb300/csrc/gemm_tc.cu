@@ -891,30 +891,22 @@ int set_gemm_mode(int mode) {
   return TT_OK;
 }
 
-// Above this many bytes of digit planes a group runs fused: writing and
-// re-reading the planes through HBM then costs more than splitting inside the
-// product kernel (measured: fused wins on the batched sums' GB-sized groups and
-// loses on the 10 MB groups of a single sum, where the separate split kernel's
-// many warps hide the latency better).
+// A group runs fused when its digit planes would exceed this many bytes (so
+// that writing and re-reading them goes through HBM) and the fused kernel's
+// repeated splitting stays cheap: every product CTA splits its own A rows and B
+// columns, so A is split once per tile along N and B once per tile along M.
+// Measured: fused wins on the batched sums' GB-sized groups of narrow products
+// (repeat factor ~1.25) and loses both on a single sum's 10 MB groups (planes in
+// L2) and on the large sum's wide products (repeat factor ~3).
 constexpr int64_t kFusedPlaneBytes = int64_t(64) << 20;
+constexpr double kFusedMaxRepeat = 2.0;
 
 void gemm_tc_prepare(std::vector<GemmDesc>& g, int s, int target_ctas, TcPlan* plan, long long* acc_base,
                      int* ex_base, int* cbase, uint8_t* plane_base) {
   const int mode = g_gemm_mode.load();
-  bool fused = mode == 2;
-  if (mode == 0) {
-    int64_t pl_est = 0;
-    for (const auto& d : g) {
-      const int64_t K1 = std::max<int64_t>(d.K, 1);
-      pl_est += int64_t(d.batch) * (ceil_div(std::max<int64_t>(d.M, 1), TC_BM) * TC_BM +
-                                    ceil_div(std::max<int64_t>(d.N, 1), TC_BN) * TC_BN) *
-                ceil_div(K1, 16) * 16 * s * 2;
-    }
-    fused = pl_est > kFusedPlaneBytes;
-  }
-  plan->fused = fused;
   int64_t t = 0, eb = 0, sb = 0, acc = 0, ex = 0, c = 0, pl = 0;
   int64_t tiles_total = 0;
+  double split_once = 0.0, split_fused = 0.0, pl_est = 0.0;
   for (auto& d : g) {
     // keep the long side on the 128-row tile
     if (d.M < TC_BM && d.N > d.M && d.c_rdiv == 0) {
@@ -928,7 +920,15 @@ void gemm_tc_prepare(std::vector<GemmDesc>& g, int s, int target_ctas, TcPlan* p
     d.mt = int(ceil_div(std::max<int64_t>(d.M, 1), TC_BM));
     d.nt = int(ceil_div(std::max<int64_t>(d.N, 1), TC_BN));
     tiles_total += int64_t(d.batch) * d.mt * d.nt;
+    const double K1 = double(std::max<int64_t>(d.K, 1)), bt = double(d.batch);
+    split_once += bt * K1 * double(d.M + d.N);
+    split_fused += bt * K1 * (double(d.M) * d.nt + double(d.N) * d.mt);
+    pl_est += bt * (double(d.mt) * TC_BM + double(d.nt) * TC_BN) * double(ceil_div(int64_t(K1), 16) * 16) * s * 2;
   }
+  bool fused = mode == 2;
+  if (mode == 0)
+    fused = pl_est > double(kFusedPlaneBytes) && split_fused <= kFusedMaxRepeat * split_once;
+  plan->fused = fused;
   for (auto& d : g) {
     // chunk width: the K extent rounded up to 16 when it is short, else 64
     const int64_t K1 = std::max<int64_t>(d.K, 1);
