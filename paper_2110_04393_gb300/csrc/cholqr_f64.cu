@@ -283,6 +283,40 @@ __device__ bool chol_inverse(double* G, double* X, int k) {
   return chol_with_inverse(G, X, k);
 }
 
+// Sum of two values over the block (blockDim.x a multiple of 32, at most
+// 1024): shuffle trees within the warps and over the warp partials, result in
+// every thread. FP64 adds cost ~64 cycles each, so no serial loop anywhere.
+__device__ __forceinline__ void block_sum2(double* a, double* b) {
+  __shared__ double s_part[2][32];
+  __shared__ double s_tot[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double x = *a, y = *b;
+  for (int off = 16; off; off >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, off);
+    y += __shfl_xor_sync(0xffffffffu, y, off);
+  }
+  if (lane == 0) {
+    s_part[0][warp] = x;
+    s_part[1][warp] = y;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    x = lane < nw ? s_part[0][lane] : 0.0;
+    y = lane < nw ? s_part[1][lane] : 0.0;
+    for (int off = 16; off; off >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, off);
+      y += __shfl_xor_sync(0xffffffffu, y, off);
+    }
+    if (lane == 0) {
+      s_tot[0] = x;
+      s_tot[1] = y;
+    }
+  }
+  __syncthreads();
+  *a = s_tot[0];
+  *b = s_tot[1];
+}
+
 // Position (i, j), i <= j, of entry p of the row-wise packed upper triangle.
 __device__ __forceinline__ void tri_ij(int p, int k, int* i, int* j) {
   int r = 0;
@@ -302,17 +336,20 @@ __device__ __forceinline__ void tri_ij(int p, int k, int* i, int* j) {
 //     status[0] and ends the chain.
 // Returns after the CTA's last write (callers synchronize before publishing).
 __device__ void cqr_decide(double* G, double* X, double* G0, int k, int64_t m, int pass, bool final_pass,
-                           int unshifted_run, double* Rinv, double* Racc, int fo_r, int* status) {
+                           int unshifted_run, double* Rinv, double* Racc, int fo_r, int* status,
+                           double e2_pre = -1.0) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (final_pass) {
     __shared__ int bad;
     if (tid == 0) bad = 0;
     __syncthreads();
     const double tol = 64.0 * k * 0x1p-53;
-    for (int idx = tid; idx < k * k; idx += nt) {
-      const double dv = G[idx] - (((idx / k) == (idx % k)) ? 1.0 : 0.0);
-      if (!(fabs(dv) <= tol)) bad = 1;
-    }
+    const int lane = tid & 31, nw = nt >> 5;
+    for (int r = tid >> 5; r < k; r += nw)
+      for (int c = lane; c < k; c += 32) {
+        const double dv = G[r * k + c] - (r == c ? 1.0 : 0.0);
+        if (!(fabs(dv) <= tol)) bad = 1;
+      }
     __syncthreads();
     if (tid == 0) {
       if (bad) atomicExch(status, 1);
@@ -326,28 +363,22 @@ __device__ void cqr_decide(double* G, double* X, double* G0, int k, int64_t m, i
     // (and allowed to lose its triangular form) it becomes (I + E/2) R: the
     // correction E R / 2 is ~1e-8 of R or less, so an fp32 product of it keeps R
     // accurate to float64 rounding.
-    __shared__ double s_red[CQ_THREADS / 32];
-    double e2 = 0.0;
-    for (int idx = tid; idx < k * k; idx += nt) {
-      const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
-      e2 = fma(dv, dv, e2);
+    const int lane = tid & 31, nw = nt >> 5;
+    double tot = e2_pre;
+    if (!(tot >= 0.0)) {
+      double e2 = 0.0, unused = 0.0;
+      for (int r = tid >> 5; r < k; r += nw)
+        for (int c = lane; c < k; c += 32) {
+          const double dv = G[r * k + c] - (r == c ? 1.0 : 0.0);
+          e2 = fma(dv, dv, e2);
+        }
+      block_sum2(&e2, &unused);
+      tot = e2;
     }
-    for (int off = 16; off; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
-    if ((tid & 31) == 0) s_red[tid >> 5] = e2;
-    __syncthreads();
-    __shared__ double s_e2;
-    if (tid == 0) {
-      double t0 = 0.0;
-      for (int w = 0; w < (nt >> 5); ++w) t0 += s_red[w];
-      s_e2 = t0;
-    }
-    __syncthreads();
-    const double tot = s_e2;
     if (tot <= 1e-16) {                           // ||E||_F <= 1e-8 (false for NaN)
-      for (int idx = tid; idx < k * k; idx += nt) {
-        const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
-        Rinv[idx] = ((idx % (k + 1) == 0) ? 1.0 : 0.0) - 0.5 * dv;
-      }
+      // I - E/2 = 1.5 I - G/2: one rounding of the same exact value
+      for (int r = tid >> 5; r < k; r += nw)
+        for (int c = lane; c < k; c += 32) Rinv[r * k + c] = fma(-0.5, G[r * k + c], r == c ? 1.5 : 0.0);
       if (Racc) {
         // X <- E / 2, G0 <- R (the previous factor), then R += (E / 2) R with R
         // scaled by a power of two near 1 / max|R| for the fp32 product (no
@@ -655,17 +686,6 @@ struct CoopJob {
   int64_t mp;
 };
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < nw; ++w) t += red[w];
-  return t;
-}
-
 constexpr unsigned long long kCoopWaitNs = 1000000000ull;   // 1 s
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -895,21 +915,26 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
       }
       __syncthreads();
       // certificate inputs, before the decision overwrites G and Rinv
-      __shared__ double s_red[CQ_THREADS / 32];
       const bool try_cert = a.eps != nullptr && pass == 1 && !final_pass && a.rcap >= k;
-      double e2 = 0.0, ri2 = 0.0;
-      if (try_cert) {
+      const bool fo_test = pass > 0 && !final_pass && (a.Racc == nullptr || a.fo_r);
+      double e2 = -1.0, ri2 = 0.0;
+      if (try_cert || fo_test) {
+        // ||G - I||_F^2 (the first-order test) and ||R0^{-1}||_F^2 in one reduction
         double pe = 0.0, pr = 0.0;
-        for (int idx = tid; idx < k * k; idx += nt) {
-          const double dv = G[idx] - ((idx % (k + 1) == 0) ? 1.0 : 0.0);
-          const double ri = __ldcg(a.Rinv + idx);
-          pe = fma(dv, dv, pe);
-          pr = fma(ri, ri, pr);
-        }
-        e2 = block_sum(pe, s_red);
-        ri2 = block_sum(pr, s_red);
+        for (int r = warp; r < k; r += nw)
+          for (int c = lane; c < k; c += 32) {
+            const double dv = G[r * k + c] - (r == c ? 1.0 : 0.0);
+            pe = fma(dv, dv, pe);
+            if (try_cert) {
+              const double ri = __ldcg(a.Rinv + r * k + c);
+              pr = fma(ri, ri, pr);
+            }
+          }
+        block_sum2(&pe, &pr);
+        e2 = pe;
+        ri2 = pr;
       }
-      cqr_decide(G, X, G0, k, a.m, pass, final_pass, unshifted_run, a.Rinv, a.Racc, a.fo_r, st);
+      cqr_decide(G, X, G0, k, a.m, pass, final_pass, unshifted_run, a.Rinv, a.Racc, a.fo_r, st, e2);
       if (final_pass) return;
       if (try_cert && tid == 0 && st[4] != 0) {
         const double lbound = (1.0 - sqrt(e2)) * (1.0 - 1e-6) / sqrt(ri2);
