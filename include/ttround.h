@@ -596,7 +596,10 @@ void tt_debug_inject_device_status(int32_t bits);
  *      blocks fit and the grid is co-resident; else as one launch per pass;
  *   1  shifted Cholesky QR, one launch per pass;
  *   2  the Householder TSQR fallback for every QR with k <= 96 (the path that
- *      otherwise runs only when the Cholesky chain breaks down), for testing it.
+ *      otherwise runs only when the Cholesky chain breaks down), for testing it;
+ *   3  testing: the cooperative chain runs, then marks itself failed, so the
+ *      fallback recomputes every QR with k <= 96 the way it does after a real
+ *      breakdown.
  * tt_tsqr_fallback_runs returns how many Householder fallback QRs ran on the
  * current device since the library was loaded (a device counter).
  * Errors: TT_EINVAL for an unknown mode; TT_ECUDA.

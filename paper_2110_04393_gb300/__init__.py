@@ -17,7 +17,7 @@ from .api import (tt_version, tt_sketch_gaussian, tt_round_sum_rand, tt_round_ra
                   tt_mode_products, tt_round_sum_rand_sharded,
                   tt_gemm_emulated_f64, SumRoundingPlan, BatchRoundingPlan, tune_batch_width, tune_batch_schedule, tt_round_rand_backward, clamp_ranks,
                   round_rand_fixed_sketch, debug_inject_device_status, set_qr_mode, tsqr_fallback_runs,
-                  QR_AUTO, QR_CHAIN, QR_FORCE_FALLBACK, set_gemm_mode, GEMM_AUTO, GEMM_FUSED, GEMM_THREE_PASS, probe_fp64_rate, probe_pivot_rsqrt, prof_enable, prof_reset, prof_read, prof_read_kind,
+                  QR_AUTO, QR_CHAIN, QR_FORCE_FALLBACK, QR_COOP_THEN_FALLBACK, set_gemm_mode, GEMM_AUTO, GEMM_FUSED, GEMM_THREE_PASS, probe_fp64_rate, probe_pivot_rsqrt, prof_enable, prof_reset, prof_read, prof_read_kind,
                   PREC_FP64, PREC_MIXED)
 from .costs import flops_sum_randorth, bytes_sum_randorth
 
@@ -27,5 +27,5 @@ __all__ = ["tt_version", "tt_sketch_gaussian", "tt_round_sum_rand", "tt_round_ra
            "tt_mode_products", "tt_round_sum_rand_sharded",
            "tt_gemm_emulated_f64", "SumRoundingPlan", "BatchRoundingPlan", "tune_batch_width", "tune_batch_schedule", "tt_round_rand_backward", "round_rand_fixed_sketch", "clamp_ranks",
            "PREC_FP64", "PREC_MIXED", "debug_inject_device_status", "set_qr_mode",
-           "tsqr_fallback_runs", "QR_AUTO", "QR_CHAIN", "QR_FORCE_FALLBACK", "set_gemm_mode",
+           "tsqr_fallback_runs", "QR_AUTO", "QR_CHAIN", "QR_FORCE_FALLBACK", "QR_COOP_THEN_FALLBACK", "set_gemm_mode",
            "GEMM_AUTO", "GEMM_FUSED", "GEMM_THREE_PASS", "probe_fp64_rate", "probe_pivot_rsqrt", "flops_sum_randorth", "bytes_sum_randorth"]

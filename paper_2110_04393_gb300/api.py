@@ -878,13 +878,15 @@ def debug_inject_device_status(bits):
     nat.lib().tt_debug_inject_device_status(int(bits))
 
 
-QR_AUTO, QR_CHAIN, QR_FORCE_FALLBACK = 0, 1, 2
+QR_AUTO, QR_CHAIN, QR_FORCE_FALLBACK, QR_COOP_THEN_FALLBACK = 0, 1, 2, 3
 
 
 def set_qr_mode(mode):
     """How later calls run their thin QRs: QR_AUTO (one cooperative launch
     where it fits), QR_CHAIN (one launch per Cholesky-QR pass) or
-    QR_FORCE_FALLBACK (Householder TSQR for every QR with k <= 96)."""
+    QR_FORCE_FALLBACK (Householder TSQR for every QR with k <= 96) or
+    QR_COOP_THEN_FALLBACK (testing: the cooperative chain, then the fallback as
+    after a breakdown)."""
     _check(nat.lib().tt_set_qr_mode(int(mode)))
 
 

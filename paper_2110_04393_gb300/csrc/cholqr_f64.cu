@@ -684,6 +684,7 @@ struct CoopJob {
   double* Aw;               // A itself, written with Q when certified
   double* Xp;               // mp x k row-major
   int64_t mp;
+  int force_fail;           // testing: mark the chain failed after its first decision
 };
 
 constexpr unsigned long long kCoopWaitNs = 1000000000ull;   // 1 s
@@ -935,6 +936,7 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
         ri2 = pr;
       }
       cqr_decide(G, X, G0, k, a.m, pass, final_pass, unshifted_run, a.Rinv, a.Racc, a.fo_r, st, e2);
+      if (a.force_fail && tid == 0) st[0] = 1;
       if (final_pass) return;
       if (try_cert && tid == 0 && st[4] != 0) {
         const double lbound = (1.0 - sqrt(e2)) * (1.0 - 1e-6) / sqrt(ri2);
@@ -1113,7 +1115,7 @@ void qr_fallback_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_
 
 static std::atomic<int> g_qr_mode{QR_MODE_AUTO};
 int set_qr_mode(int mode) {
-  if (mode < QR_MODE_AUTO || mode > QR_MODE_FORCE_FALLBACK) return TT_EINVAL;
+  if (mode < QR_MODE_AUTO || mode > QR_MODE_COOP_THEN_FALLBACK) return TT_EINVAL;
   g_qr_mode.store(mode);
   return TT_OK;
 }
@@ -1134,7 +1136,8 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
   });
   int cb = 0, cP = 0;
   size_t csm = 0;
-  if (!force_fallback && mode == QR_MODE_AUTO && coop_shape(b.m, b.k, &cb, &cP, &csm)) {
+  const bool coop_mode = mode == QR_MODE_AUTO || (mode == QR_MODE_COOP_THEN_FALLBACK && b.k <= TSQR_KMAX);
+  if (!force_fallback && coop_mode && coop_shape(b.m, b.k, &cb, &cP, &csm)) {
     CoopJob job{};
     job.m = b.m;
     job.k = b.k;
@@ -1151,7 +1154,8 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
     job.Rinv = b.Rinv;
     job.Racc = R;
     job.status = b.status;
-    if (cert && R && r_may_be_full) {
+    job.force_fail = mode == QR_MODE_COOP_THEN_FALLBACK ? 1 : 0;
+    if (cert && R && r_may_be_full && !job.force_fail) {
       const int64_t bp = ceil_div(cert->mp, int64_t(cP));
       if (bp * b.k + int64_t(b.k) * b.k <= coop_smem_doubles(cb, b.k) - int64_t(cb) * cq_ts(b.k)) {
         job.eps = cert->eps;

@@ -68,7 +68,7 @@ const int* qr_cert_flag(const QrBufs& b);
 // the grid is co-resident, else the multi-launch chain; CHAIN = always the
 // multi-launch chain; FORCE_FALLBACK = skip the Cholesky chain and run the
 // Householder TSQR for every QR with k <= 96 (a diagnostic of that path).
-constexpr int QR_MODE_AUTO = 0, QR_MODE_CHAIN = 1, QR_MODE_FORCE_FALLBACK = 2;
+constexpr int QR_MODE_AUTO = 0, QR_MODE_CHAIN = 1, QR_MODE_FORCE_FALLBACK = 2, QR_MODE_COOP_THEN_FALLBACK = 3;
 int set_qr_mode(int mode);
 // Many independent thin QRs (Q only, k <= 96): one multi-launch Cholesky-QR
 // chain (CQ_MAX_PASSES launches) covering every job, each job on about

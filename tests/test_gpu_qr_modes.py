@@ -95,7 +95,7 @@ def test_plan_in_each_mode_matches_eager():
     R = [const_ranks(N, r) for r in (3, 5)]
     ell = O.clamp_ranks(dims, const_ranks(N, 9))
     Yd = [to_dev(Y) for Y in Ys]
-    for mode in (0, 1, 2):
+    for mode in (0, 1, 2, 3):
         tt.set_qr_mode(mode)
         plan = tt.SumRoundingPlan(dims, R, ell, tol=1e-9, precision="fp64")
         try:
@@ -135,3 +135,41 @@ def test_pivot_rsqrt_matches_cuda_rsqrt():
     max_ulp, ndiff = tt.probe_pivot_rsqrt(1 << 22)
     assert max_ulp <= 1
     assert ndiff <= (1 << 22) // 1000
+
+
+@pytest.mark.parametrize("tol", [0.0, 1e-8])
+def test_fallback_after_breakdown_in_eager_calls_and_plans(tol):
+    """Mode 3 marks every cooperative chain failed after its first decision, so
+    the Householder fallback (its launches return at once unless the chain's
+    device flag is raised) recomputes each QR as after a real breakdown, in
+    eager calls and in captured plans alike. Both give the oracle's rounding,
+    the plan equals the eager call, and the device run counter rises by the
+    number of QRs per call; in the default mode no fallback runs at all."""
+    dims = [20, 24, 22, 26, 20, 24]
+    N = len(dims)
+    Ys = [synth.gaussian_tt(synth.rng_for(170, j), dims, const_ranks(N, r)) for j, r in enumerate([4, 6, 5])]
+    R = [const_ranks(N, r) for r in (4, 6, 5)]
+    ell = O.clamp_ranks(dims, const_ranks(N, 11))
+    sk = O.gaussian_sketch_philox(9, dims, ell)          # the sketch the device draws from seed 9
+    Xo = O.round_sum_randorth(Ys, sk)
+    if tol > 0:
+        Xo = O.truncate_left_orthogonal(Xo, tol)
+    Yd = [to_dev(Y) for Y in Ys]
+    qrs = (N - 1) * (2 if tol > 0 else 1)
+    for mode, expect in ((tt.QR_COOP_THEN_FALLBACK, qrs), (tt.QR_AUTO, 0)):
+        tt.set_qr_mode(mode)
+        before = tt.tsqr_fallback_runs()
+        Xe = to_host(tt.tt_round_sum_rand(Yd, ell, seed=9, tol=tol))
+        assert tt.tsqr_fallback_runs() - before == expect
+        plan = tt.SumRoundingPlan(dims, R, ell, tol=tol, precision="fp64")
+        try:
+            before = tt.tsqr_fallback_runs()
+            Xp = to_host(plan(Yd, seed=9))
+            Xp2 = to_host(plan(Yd, seed=9))
+            assert tt.tsqr_fallback_runs() - before == 2 * expect
+        finally:
+            plan.close()
+        for X in (Xe, Xp, Xp2):
+            assert O.ranks_of(X) == O.ranks_of(Xo)
+            assert rel_diff(X, Xo) <= FP64_TOL
+        assert rel_diff(Xp, Xe) <= 1e-13
