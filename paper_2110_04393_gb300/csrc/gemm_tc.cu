@@ -359,18 +359,37 @@ __global__ void __launch_bounds__(256) tc_split_kernel(TcArgs args) {
     split_chunk(d, s, sideA, bidx, tile, quarter, kc, o0, outer, base, os, is, Es);
     return;
   }
-  // short K: the largest exponent of the 32 rows / columns over all of K here
+  // short K: the largest exponent of the 32 rows / columns over all of K here,
+  // read as in the exponent pass (no per-element index divisions): with K
+  // contiguous a warp walks K for four rows and takes the maximum by shuffles;
+  // otherwise the lanes take the 32 rows / columns (contiguous) and the warps
+  // split K, combined by shared-memory atomics
+  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   if (tid < 32) Emax[tid] = -1;
   __syncthreads();
-  const int64_t tot = int64_t(32) * d.K;
-  for (int64_t e = tid; e < tot; e += blockDim.x) {
-    int64_t o, k;
-    if (is == 1) { o = e / d.K; k = e - o * d.K; }     // consecutive threads along K
-    else { k = e >> 5; o = e & 31; }                   // consecutive threads along the rows
-    if (o0 + o < outer) {
-      const int v = dexp(__ldg(base + (o0 + o) * os + k * is));
-      if (v >= 0) atomicMax(&Emax[o], v);
+  if (is == 1) {
+    for (int o = warp; o < 32; o += nw) {
+      int m = -1;
+      if (o0 + o < outer) {
+        const double* rp = base + (o0 + o) * os;
+        int64_t k = lane;
+        for (; k + 96 < d.K; k += 128) {
+          const double x0 = __ldg(rp + k), x1 = __ldg(rp + k + 32), x2 = __ldg(rp + k + 64), x3 = __ldg(rp + k + 96);
+          m = max(m, max(max(dexp(x0), dexp(x1)), max(dexp(x2), dexp(x3))));
+        }
+        for (; k < d.K; k += 32) m = max(m, dexp(__ldg(rp + k)));
+      }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+      if (lane == 0) Emax[o] = m;
     }
+  } else {
+    int m = -1;
+    if (o0 + lane < outer) {
+      const double* cp = base + (o0 + lane) * os;
+      for (int64_t k = warp; k < d.K; k += nw) m = max(m, dexp(__ldg(cp + k * is)));
+    }
+    if (m >= 0) atomicMax(&Emax[lane], m);
   }
   __syncthreads();
   if (tid < 32) {
