@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int
   const int64_t kc_end = min(d.nkc, kc_begin + cps);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t ncols = tc::tmem_cols_for((2 * s - 1) * TC_BN);   // levels 2 .. 2s
+  const uint32_t ncols = tc::tmem_cols_for(s * TC_BN);   // levels 2 .. s + 1
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, ncols);
     tc::tmem_relinquish();
@@ -481,17 +481,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(TcArgs args, int
     if (tid == 0 && loaded) {
       tc::fence_after_sync();
       // B planes are contiguous, i.e. one K-major operand of 32 s rows: the MMA
-      // of A digit p against it (N = 32 s) adds d_p e_q into columns
-      // (p + q - 2) 32, the region of level p + q. The p = 1 chain starts the
-      // kept levels 2 .. s + 1 (columns below 32 s); columns from 32 s on hold
-      // levels above s + 1, which are never read.
+      // of A digit p against its first 32 (s + 1 - p) rows (digits q <= s + 1
+      // - p) adds d_p e_q into columns (p + q - 2) 32, the region of level
+      // p + q; products of higher levels are never formed (they would be
+      // dropped), so the chains shrink with p and every column written is below
+      // 32 s. The p = 1 chain starts all kept levels 2 .. s + 1.
       const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
-      const uint32_t idesc_s = tc::idesc_bf16_f32(TC_BM, TC_BN * s);
       const int steps = bk / 16;
       for (int p = 1; p <= s; ++p)
         for (int st = 0; st < steps; ++st)
           tc::mma_bf16(taddr + uint32_t((p - 1) * TC_BN), tc::smem_desc(a0 + (p - 1) * pA + 256 * st, 128, 16 * bk),
-                       tc::smem_desc(b0 + 256 * st, 128, 16 * bk), idesc_s, (p == 1 && st == 0) ? 0u : 1u);
+                       tc::smem_desc(b0 + 256 * st, 128, 16 * bk),
+                       tc::idesc_bf16_f32(TC_BM, TC_BN * (s + 1 - p)), (p == 1 && st == 0) ? 0u : 1u);
       tc::mma_commit(&mbar);
     }
     __syncthreads();
@@ -632,7 +633,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tcf_kernel(TcArgs args, in
   const int64_t kc_end = min(d.nkc, kc_begin + cps);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t ncols = tc::tmem_cols_for((2 * s - 1) * TC_BN);   // levels 2 .. 2s
+  const uint32_t ncols = tc::tmem_cols_for(s * TC_BN);   // levels 2 .. s + 1
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, ncols);
     tc::tmem_relinquish();
@@ -775,17 +776,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tcf_kernel(TcArgs args, in
     if (tid == 0 && loaded) {
       tc::fence_after_sync();
       // B planes are contiguous, i.e. one K-major operand of 32 s rows: the MMA
-      // of A digit p against it (N = 32 s) adds d_p e_q into columns
-      // (p + q - 2) 32, the region of level p + q. The p = 1 chain starts the
-      // kept levels 2 .. s + 1 (columns below 32 s); columns from 32 s on hold
-      // levels above s + 1, which are never read.
+      // of A digit p against its first 32 (s + 1 - p) rows (digits q <= s + 1
+      // - p) adds d_p e_q into columns (p + q - 2) 32, the region of level
+      // p + q; products of higher levels are never formed (they would be
+      // dropped), so the chains shrink with p and every column written is below
+      // 32 s. The p = 1 chain starts all kept levels 2 .. s + 1.
       const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
-      const uint32_t idesc_s = tc::idesc_bf16_f32(TC_BM, TC_BN * s);
       const int steps = bk / 16;
       for (int p = 1; p <= s; ++p)
         for (int st = 0; st < steps; ++st)
           tc::mma_bf16(taddr + uint32_t((p - 1) * TC_BN), tc::smem_desc(a0 + (p - 1) * pA + 256 * st, 128, 16 * bk),
-                       tc::smem_desc(b0 + 256 * st, 128, 16 * bk), idesc_s, (p == 1 && st == 0) ? 0u : 1u);
+                       tc::smem_desc(b0 + 256 * st, 128, 16 * bk),
+                       tc::idesc_bf16_f32(TC_BM, TC_BN * (s + 1 - p)), (p == 1 && st == 0) ? 0u : 1u);
       tc::mma_commit(&mbar);
     }
     __syncthreads();
