@@ -175,96 +175,120 @@ __device__ __forceinline__ double rsqrt_refined(double d) {
 // memory, scheduled for GB300's FP64 issue: one warp issues one FP64
 // instruction per ~64 cycles whether or not its lanes are active, and the SM
 // retires ~1.7 FP64 lanes per clock, so work is packed densely into few warp
-// instructions and the pivot chain runs alone on one SM sub-partition.
+// instructions and nothing but the pivot chain waits on warp 0.
 //   * warp 0 (look-ahead): in step j it applies column j to column j+1 and to
 //     row j+1 of X (k entries, one lane each), takes the pivot d_{j+1} from
 //     lane 0, its reciprocal square root, and stores column j+1 of L and row
 //     j+1 of X scaled: L(j+1, j+1) = d rd, L(i, j+1) = G(i, j+1) rd,
-//     X(j+1, :) = X(j+1, :) rd, X(j+1, j+1) = rd;
-//   * the worker warps (sub-partitions 1..3) apply column j to rows i >= j+2:
-//     row i has exactly i entries to update, X(i, 0..j) and G(i, j+2..i), so
-//     one warp instruction covers a row (lane = position), without divisions.
-// One block barrier per step; blockDim.x must be a multiple of 128.
+//     X(j+1, :) = X(j+1, :) rd, X(j+1, j+1) = rd. The multipliers it needs
+//     next are the vector it just stored, shifted down by one entry with rd
+//     last, so it keeps that vector in registers: after the barrier it loads
+//     only the entries the workers updated;
+//   * the worker warps (all others) apply column j to rows i >= j+2, each warp
+//     the rows i = w + 2 (mod number of workers): row i has exactly i entries
+//     to update, X(i, 0..j) and G(i, j+2..i), so one warp instruction covers a
+//     row (lane = position); the multiplied column / row of step j is loaded
+//     once per step and warp.
+// One block barrier per step; blockDim.x a multiple of 32, at least 64.
 template <int NQ>
 __device__ bool chol_la(double* G, double* X, int k) {
   __shared__ int s_bad;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
-  const int nww = (nt >> 5) / 4 * 3;                       // worker warps
-  const int wk = (warp >> 2) * 3 + (warp & 3) - 1;         // rank of a worker warp
+  const int nww = (nt >> 5) - 1;
   for (int r = warp; r < k; r += (nt >> 5))
     for (int c = lane; c < k; c += 32) X[r * k + c] = (r == c) ? 1.0 : 0.0;
   __syncthreads();
+  // warp 0 state for the next step j: multipliers a (entry t: L(j + 1 + t, j)
+  // for t < k - 1 - j, then X(j, t - (k - 1 - j))), l1 = L(j + 1, j), and the
+  // entries' locations in column j + 1 / row j + 1 of X
+  double a[NQ], l1 = 0.0, rd = 1.0;
+  double* dst[NQ];
+  auto next = [&](const double(&o)[NQ], int j) {
+    const int n = k - 1 - j;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const double s = __shfl_down_sync(0xffffffffu, o[q], 1);
+      const double h = __shfl_sync(0xffffffffu, o[q + 1 < NQ ? q + 1 : q], 0);
+      const int t = lane + 32 * q;
+      a[q] = (t == k - 1) ? rd : ((lane == 31) ? h : s);
+      const int tc = t < k ? t : k - 1;
+      dst[q] = tc < n ? G + (j + 1 + tc) * k + j + 1 : X + (j + 1) * k + (tc - n);
+    }
+    l1 = __shfl_sync(0xffffffffu, o[0], 1);
+  };
   if (warp == 0) {
     const double d = G[0];
     const bool bad = !pivot_ok(d);
-    const double rd = bad ? 1.0 : rsqrt_refined(d);
+    rd = bad ? 1.0 : rsqrt_refined(d);
+    double o[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int t = lane + 32 * q;
-      if (t < k) G[t * k] = G[t * k] * rd;
+      o[q] = G[(t < k ? t : k - 1) * k] * rd;
+      if (t < k) G[t * k] = o[q];
     }
     if (lane == 0) {
       X[0] = rd;
       s_bad = bad ? 1 : 0;
     }
+    next(o, 0);
   }
+  int iw = warp + 1;                             // worker: its smallest row >= j + 2
   __syncthreads();
   for (int j = 0; j + 1 < k; ++j) {
     if (s_bad) return false;
-    const int n = k - 1 - j;                       // column j+1 has rows j+1 .. k-1
     if (warp == 0) {
-      const double l1 = G[(j + 1) * k + j];        // L(j+1, j)
-      // entry t < n: G(j+1+t, j+1); n <= t < k: X(j+1, t-n); per-lane
-      // addresses so that one instruction stream serves both
-      double v[NQ];
-      double* dst[NQ];
+      double v[NQ], o[NQ];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int t = lane + 32 * q;
-        const int tc = t < k ? t : k - 1;
-        const bool col = tc < n;
-        const double* a = col ? G + (j + 1 + tc) * k + j : X + j * k + (tc - n);
-        dst[q] = col ? G + (j + 1 + tc) * k + j + 1 : X + (j + 1) * k + (tc - n);
-        v[q] = fma(-*a, l1, *dst[q]);
-      }
+      for (int q = 0; q < NQ; ++q) v[q] = fma(-a[q], l1, *dst[q]);
       const double d = __shfl_sync(0xffffffffu, v[0], 0);
       const bool bad = !pivot_ok(d);
-      const double rd = bad ? 1.0 : rsqrt_refined(d);
+      rd = bad ? 1.0 : rsqrt_refined(d);
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
-        const double o = v[q] * rd;
-        if (lane + 32 * q < k) *dst[q] = o;
+        o[q] = v[q] * rd;
+        if (lane + 32 * q < k) *dst[q] = o[q];
       }
       if (lane == 0) {
         X[(j + 1) * k + j + 1] = rd;
         if (bad) s_bad = 1;
       }
-    } else if (warp & 3) {
-      // rows i = j+2 .. k-1; position p < j+1 is X(i, p), the rest G(i, p+1)
-      constexpr int RB = NQ == 1 ? 4 : 2;          // rows per batch: loads first, then FMAs
-      for (int i0 = j + 2 + wk; i0 < k; i0 += RB * nww) {
-        double a[RB], b[RB][NQ], c[RB][NQ];
-        double* dp[RB][NQ];
+      if (j + 2 < k) next(o, j + 1);
+    } else {
+      // position p < j + 1 of row i is X(i, p), the rest G(i, p + 1)
+      if (iw < j + 2) iw += nww;
+      double b[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int pb = min(lane + 32 * q, k - 2);
+        b[q] = pb <= j ? X[j * k + pb] : G[(pb + 1) * k + j];
+      }
+      constexpr int RB = NQ == 1 ? 4 : 2;        // rows per batch: loads first, then FMAs
+      for (int i = iw; i < k; i += RB * nww) {
+        double ar[RB], c[RB][NQ];
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
-          const int ic = min(i0 + r * nww, k - 1);
-          a[r] = G[ic * k + j];
+          const int ir = min(i + r * nww, k - 1);
+          ar[r] = G[ir * k + j];
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
-            const int pc = min(lane + 32 * q, ic - 1);
-            const bool xp = pc <= j;
-            b[r][q] = xp ? X[j * k + pc] : G[(pc + 1) * k + j];
-            dp[r][q] = xp ? X + ic * k + pc : G + ic * k + pc + 1;
-            c[r][q] = *dp[r][q];
+            const int pc = min(lane + 32 * q, ir - 1);
+            c[r][q] = pc <= j ? X[ir * k + pc] : G[ir * k + pc + 1];
           }
         }
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
-          const int i = i0 + r * nww;
+          const int ir = i + r * nww;
+          if (ir < k) {
 #pragma unroll
-          for (int q = 0; q < NQ; ++q) {
-            const double o = fma(-a[r], b[r][q], c[r][q]);
-            if (i < k && lane + 32 * q < i) *dp[r][q] = o;
+            for (int q = 0; q < NQ; ++q) {
+              const int p = lane + 32 * q;
+              const double ov = fma(-ar[r], b[q], c[r][q]);
+              if (p < ir) {
+                if (p <= j) X[ir * k + p] = ov;
+                else G[ir * k + p + 1] = ov;
+              }
+            }
           }
         }
       }
@@ -760,8 +784,10 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
         __syncthreads();
       } else {
         // T := T Rinv (upper triangular, or the full first-order correction):
-        // one output entry per item, four independent partial sums (FP64
-        // issues a dependent operation only every ~65 cycles). Items run
+        // one output entry per item, one accumulator. A warp issues at most
+        // one FP64 instruction per ~64 cycles whether or not they depend on
+        // each other, and the 8 warps already keep the FP64 pipe busy, so
+        // split partial sums would only add their final adds. Items run
         // down the columns, so the lanes of a warp share one or two columns
         // and hence the length c + 1 of their triangular sums: a warp
         // instruction costs the same whatever its active lanes, so mixing
@@ -773,16 +799,9 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
           const int c = i / b, r = i - c * b;
           const int jn = first_order ? k : c + 1;
           const double* tr = T + r * ts;
-          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-          int j = 0;
-          for (; j + 4 <= jn; j += 4) {
-            s0 = fma(tr[j], Rs[j * k + c], s0);
-            s1 = fma(tr[j + 1], Rs[(j + 1) * k + c], s1);
-            s2 = fma(tr[j + 2], Rs[(j + 2) * k + c], s2);
-            s3 = fma(tr[j + 3], Rs[(j + 3) * k + c], s3);
-          }
-          for (; j < jn; ++j) s0 = fma(tr[j], Rs[j * k + c], s0);
-          T2[r * k + c] = (s0 + s1) + (s2 + s3);
+          double s0 = 0.0;
+          for (int j = 0; j < jn; ++j) s0 = fma(tr[j], Rs[j * k + c], s0);
+          T2[r * k + c] = s0;
         }
         __syncthreads();
         for (int i = tid; i < b * k; i += nt) {
@@ -801,29 +820,57 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
             for (int c = lane; c < k; c += 32) qd[gr * qr + c * qc] = T[r * ts + c];
         }
         if (cert) {
-          // V(X_{n-1}) := V(X_{n-1}) R^T for this CTA's rows (in place)
-          double* Rt = U;                   // R, k x k
-          double* Xr = U + k * k;           // bp x k
+          // V(X_{n-1}) := V(X_{n-1}) R^T for this CTA's rows (in place), with
+          // R = (I + E/2) R0: R0 upper triangular (left in Racc by the
+          // certified decision), E = G - I symmetric. Y = Xp R0^T in FP64 over
+          // the triangle (half the products of a full R), then
+          // Xp := Y (I + E/2). The correction matrix is still in the first k^2
+          // doubles of U from the update of T above: E/2 as floats when
+          // ||E||_F <= 1e-10 (an fp32 product of the correction is then within
+          // float64 rounding of Y), I - E/2 in float64 otherwise.
+          double* R0s = U + k * k;          // R0, k x k
+          double* Xr = R0s + k * k;         // nr x k at row stride ts (odd: no bank conflicts), later Y in fp32
+          double* Y = T;                    // nr x k, the row block is dead once Q is written
           const int64_t p0 = int64_t(lb) * a.bp;
           const int64_t rem = a.mp - p0;
           const int nr = rem <= 0 ? 0 : (rem < a.bp ? int(rem) : a.bp);
-          for (int i = tid; i < k * k; i += nt) Rt[i] = __ldcg(a.Racc + i);
-          for (int i = tid; i < nr * k; i += nt) Xr[i] = a.Xp[p0 * k + i];
-          __syncthreads();
+          for (int i = tid; i < k * k; i += nt) R0s[i] = __ldcg(a.Racc + i);
           for (int i = tid; i < nr * k; i += nt) {
-            const int r = i / k, c = i - r * k;
-            const double* xr = Xr + r * k;
-            const double* rr = Rt + c * k;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int j = 0;
-            for (; j + 4 <= k; j += 4) {
-              s0 = fma(xr[j], rr[j], s0);
-              s1 = fma(xr[j + 1], rr[j + 1], s1);
-              s2 = fma(xr[j + 2], rr[j + 2], s2);
-              s3 = fma(xr[j + 3], rr[j + 3], s3);
+            const int r = i / k;
+            Xr[r * ts + (i - r * k)] = a.Xp[p0 * k + i];
+          }
+          __syncthreads();
+          // items down the columns: a warp's lanes share the triangle's length
+          for (int i = tid; i < nr * k; i += nt) {
+            const int c = i / nr, r = i - c * nr;
+            const double* xr = Xr + r * ts;
+            const double* rr = R0s + c * k;
+            double s0 = 0.0;
+            for (int j = c; j < k; ++j) s0 = fma(xr[j], rr[j], s0);
+            Y[r * k + c] = s0;
+          }
+          __syncthreads();
+          if (fo_kind == 2) {
+            const float* Cf = reinterpret_cast<const float*>(U);   // E/2
+            float* Yf = reinterpret_cast<float*>(Xr);
+            for (int i = tid; i < nr * k; i += nt) Yf[i] = float(Y[i]);
+            __syncthreads();
+            for (int i = tid; i < nr * k; i += nt) {
+              const int r = i / k, c = i - r * k;
+              float corr = 0.0f;
+              for (int l = 0; l < k; ++l) corr = fmaf(Yf[r * k + l], Cf[l * k + c], corr);
+              a.Xp[p0 * k + i] = Y[i] + double(corr);
             }
-            for (; j < k; ++j) s0 = fma(xr[j], rr[j], s0);
-            a.Xp[p0 * k + i] = (s0 + s1) + (s2 + s3);
+          } else {
+            // Y (I + E/2) = 2 Y - Y (I - E/2)
+            const double* Rs = U;
+            for (int i = tid; i < nr * k; i += nt) {
+              const int r = i / k, c = i - r * k;
+              const double* yr = Y + r * k;
+              double s0 = 0.0;
+              for (int j = 0; j < k; ++j) s0 = fma(yr[j], Rs[j * k + c], s0);
+              a.Xp[p0 * k + i] = fma(2.0, yr[c], -s0);
+            }
           }
         }
         if (first_order) {
@@ -833,21 +880,15 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
         }
       }
     }
-    // partial Gram of the row block (packed upper triangle), four partial sums
+    // partial Gram of the row block (packed upper triangle), one accumulator
+    // per entry (as in the product above)
     double* Gp = a.Gpart + int64_t(lb) * npair;
     for (int p = tid; p < npair; p += nt) {
       int i1, j1;
       tri_ij(p, k, &i1, &j1);
-      double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
-      int r = 0;
-      for (; r + 4 <= b; r += 4) {
-        g0 = fma(T[r * ts + i1], T[r * ts + j1], g0);
-        g1 = fma(T[(r + 1) * ts + i1], T[(r + 1) * ts + j1], g1);
-        g2 = fma(T[(r + 2) * ts + i1], T[(r + 2) * ts + j1], g2);
-        g3 = fma(T[(r + 3) * ts + i1], T[(r + 3) * ts + j1], g3);
-      }
-      for (; r < b; ++r) g0 = fma(T[r * ts + i1], T[r * ts + j1], g0);
-      Gp[p] = (g0 + g1) + (g2 + g3);
+      double g0 = 0.0;
+      for (int r = 0; r < b; ++r) g0 = fma(T[r * ts + i1], T[r * ts + j1], g0);
+      Gp[p] = g0;
     }
     // two-level arrival: the last CTA of each group sums its group's partials
     __syncthreads();
@@ -895,6 +936,8 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
       double* G = U;
       double* X = G + k * k;
       double* G0 = X + k * k;
+      // the tolerance's load overlaps the partials' loads below
+      const double eps_v = (a.eps != nullptr && pass == 1) ? __ldcg(a.eps) : 0.0;
       // at most CQ_GROUP group partials (coop_shape keeps P <= CQ_GROUP^2):
       // all loads in flight at once, then a fixed pairwise tree
       for (int p = tid; p < npair; p += nt) {
@@ -935,15 +978,22 @@ __global__ void __launch_bounds__(CQ_THREADS) cqr_coop_kernel(CoopJob a) {
         e2 = pe;
         ri2 = pr;
       }
-      cqr_decide(G, X, G0, k, a.m, pass, final_pass, unshifted_run, a.Rinv, a.Racc, a.fo_r, st, e2);
+      // The certificate is settled before the decision: a certified bond takes
+      // the first-order step (the same test, e2 <= 1e-16), and its R is needed
+      // only by the fold of the final pass, which applies (I + E/2) itself, so
+      // the decision leaves R = R0 (upper triangular) in Racc.
+      bool certify = false;
+      if (try_cert) {
+        const double lbound = (1.0 - sqrt(e2)) * (1.0 - 1e-6) / sqrt(ri2);
+        certify = e2 <= 1e-16 && isfinite(lbound) && ri2 > 0.0 && lbound > 2.0 * eps_v;
+      }
+      cqr_decide(G, X, G0, k, a.m, pass, final_pass, unshifted_run, a.Rinv, certify ? nullptr : a.Racc, a.fo_r,
+                 st, e2);
       if (a.force_fail && tid == 0) st[0] = 1;
       if (final_pass) return;
-      if (try_cert && tid == 0 && st[4] != 0) {
-        const double lbound = (1.0 - sqrt(e2)) * (1.0 - 1e-6) / sqrt(ri2);
-        if (isfinite(lbound) && ri2 > 0.0 && e2 < 1e-4 && lbound > 2.0 * __ldcg(a.eps)) {
-          *a.cert = 1;
-          *a.rank_out = k;
-        }
+      if (certify && tid == 0) {
+        *a.cert = 1;
+        *a.rank_out = k;
       }
       __syncthreads();
       if (tid == 0) st_release_gpu(released, pass + 1);   // cumulative over the block's writes
@@ -1156,8 +1206,11 @@ void qr_plan(Schedule& sc, const QrBufs& b, const double* A, int64_t a_rs, int64
     job.status = b.status;
     job.force_fail = mode == QR_MODE_COOP_THEN_FALLBACK ? 1 : 0;
     if (cert && R && r_may_be_full && !job.force_fail) {
+      // the fold keeps [correction | R0 | rows of V(X_{n-1})] in the union and
+      // Y in the row block
       const int64_t bp = ceil_div(cert->mp, int64_t(cP));
-      if (bp * b.k + int64_t(b.k) * b.k <= coop_smem_doubles(cb, b.k) - int64_t(cb) * cq_ts(b.k)) {
+      const int64_t kk = int64_t(b.k) * b.k;
+      if (bp <= cb && 2 * kk + bp * cq_ts(b.k) <= coop_smem_doubles(cb, b.k) - int64_t(cb) * cq_ts(b.k)) {
         job.eps = cert->eps;
         job.rcap = cert->rcap;
         job.bp = int(bp);

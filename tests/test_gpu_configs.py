@@ -11,7 +11,9 @@ oracle on the same sketch:
 * a scaled-down twin of the large sum (K = 6, N = 8, I = 64, rank 10,
   redundant structure of rank 30 plus a 1e-8 tail, l = 40, rho = 60,
   tolerance 1e-6): Randomize-then-Orthogonalize and the orthogonalized
-  Two-Sided rounding, both precisions.
+  Two-Sided rounding, both precisions;
+* the truncation of a TT whose last bond has a graded spectrum (certified
+  bonds ending with each kind of first-order correction).
 Bars: FP64 path <= 1e-10 relative Frobenius distance from the oracle's result
 (and equal ranks); mixed path error <= 1.1x the oracle's rounding error."""
 import numpy as np
@@ -78,6 +80,30 @@ def test_truncate_lorth_tolerance_matches_oracle():
         assert rel_diff(Xg, Xt) <= FP64_TOL
         if mr == 0:
             assert O.diff_norm(Xg, Xo) <= tol * O.norm(Xo) * (1 + 1e-10)
+
+
+@pytest.mark.parametrize("spread", [1e2, 1e3, 3e3, 1e5])
+def test_truncate_lorth_graded_spectrum_matches_oracle(spread):
+    """Section 3.2 truncation of a left-orthogonal TT whose last core has its
+    rows scaled over `spread`: the QR of the last bond then meets a Gram error
+    E = G - I after one factorization of about spread^2 u, so across the
+    parameters the chain ends with an fp32 first-order correction (||E||_F <=
+    1e-10), a float64 one (1e-10 < ||E||_F <= 1e-8) or a second factorization.
+    With a tolerance far below the smallest singular value nothing is cut, the
+    first-order bonds certify that inside the QR and fold R into the next core,
+    and the result is the input tensor. The last mode (480 = 40 x 12) gives the
+    last bond's QR as many rows as the core it folds into, so its fold runs."""
+    r = 12
+    dims = [40, 40, 40, 480]
+    X = O.orthogonalize_lr(synth.gaussian_tt(synth.rng_for(77), dims, [1, r, r, r, 1]))
+    d = np.logspace(0.0, -np.log10(spread), r)
+    X[-1] = X[-1] * d[:, None, None]
+    tol = 1e-12
+    Xg = to_host(tt.tt_truncate_lorth(to_dev(X), tol=tol))
+    Xt = O.truncate_left_orthogonal(X, tol)
+    assert O.ranks_of(Xg) == O.ranks_of(Xt) == O.ranks_of(X)
+    assert rel_diff(Xg, Xt) <= 1e-12
+    assert rel_diff(Xg, X) <= 1e-12
 
 
 # --------------------------------------------------------- batched uneven sums
