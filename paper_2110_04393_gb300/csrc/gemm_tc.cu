@@ -270,9 +270,9 @@ __device__ __forceinline__ int decode_exp(int v, int epoch) {
 // ---- pass 2: digit planes. A block splits a 32 x bk sub-tile of A (rows) or
 // of B (columns) and writes its s bf16 planes in the canonical K-major layout
 // of the 128 x bk (A) or 32 x bk (B) operand tile, padding with zeros. With a
-// short K (lx) one block covers all chunks of its 32 rows / columns and takes
-// their largest exponents itself (written as the tags the product pass reads),
-// so no exponent pass runs for that descriptor.
+// short K (lx) one block covers all chunks of 8 rows / columns and takes their
+// largest exponents itself (written as the tags the product pass reads), so no
+// exponent pass runs for that descriptor.
 constexpr int64_t kLocalExpK = 512;
 
 __device__ __forceinline__ void split_chunk(const GemmDesc& d, int s, bool sideA, int64_t bidx, int64_t tile,
@@ -319,38 +319,48 @@ __device__ __forceinline__ void split_chunk(const GemmDesc& d, int s, bool sideA
   }
 }
 
+// Short-K blocks: the rows (A) or columns (B) of a block over all of K are
+// staged in shared memory by one round of loads (all in flight), their largest
+// exponents taken there, and every chunk split from shared memory. A block
+// takes 32 rows / columns when K fits one chunk (at most 64) and 8 otherwise
+// (at most kLocalExpK = 512), so that a block's loads stay at 8-16 per thread.
+constexpr int LX_ROWS = 8;                             // rows per block above one chunk
+constexpr int LX_LD = int(kLocalExpK) + 1;             // staged row stride (doubles), 8-row blocks
+constexpr int LX_LD1 = TC_BK + 1;                      // staged row stride, 32-row blocks
+
+__host__ __device__ inline int lx_rows(int64_t nkc) { return nkc == 1 ? 32 : LX_ROWS; }
+
 __global__ void __launch_bounds__(256) tc_split_kernel(TcArgs args) {
   __shared__ int Es[32];
-  __shared__ int Emax[32];
+  __shared__ double stg[LX_ROWS * LX_LD];
   const int64_t t = blockIdx.x;
   const GemmDesc d = args.descs[find_desc(args.descs, args.ndesc, t, 2)];
   const int s = args.s;
   const int64_t nkc = d.nkc;
-  const int64_t per = d.lx ? 1 : nkc;                  // chunk blocks per sub-tile
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int64_t local = t - d.split_begin;
-  const int64_t na = int64_t(d.mt) * 4 * per, per_batch = na + int64_t(d.nt) * per;
-  const int64_t bidx = local / per_batch;
-  local -= bidx * per_batch;
-  const bool sideA = local < na;
-  int64_t kc, tile;
-  int quarter = 0;
-  if (sideA) {
-    kc = local % per;
-    const int64_t q4 = local / per;
-    quarter = int(q4 & 3);
-    tile = q4 >> 2;
-  } else {
-    local -= na;
-    kc = local % per;
-    tile = local / per;
-  }
-  const int tid = threadIdx.x;
-  const int64_t o0 = sideA ? tile * TC_BM + quarter * 32 : tile * TC_BN;   // first row (A) / column (B)
-  const int64_t outer = sideA ? d.M : d.N;
-  const double* base = sideA ? d.A + bidx * d.a_bs : d.B + bidx * d.b_bs;
-  const int64_t os = sideA ? d.a_rs : d.b_cs, is = sideA ? d.a_cs : d.b_rs;
-  int* ex = sideA ? d.ex_row + bidx * d.M : d.ex_col + bidx * d.N;
   if (!d.lx) {
+    const int64_t na = int64_t(d.mt) * 4 * nkc, per_batch = na + int64_t(d.nt) * nkc;
+    const int64_t bidx = local / per_batch;
+    local -= bidx * per_batch;
+    const bool sideA = local < na;
+    int64_t kc, tile;
+    int quarter = 0;
+    if (sideA) {
+      kc = local % nkc;
+      const int64_t q4 = local / nkc;
+      quarter = int(q4 & 3);
+      tile = q4 >> 2;
+    } else {
+      local -= na;
+      kc = local % nkc;
+      tile = local / nkc;
+    }
+    const int64_t o0 = sideA ? tile * TC_BM + quarter * 32 : tile * TC_BN;   // first row (A) / column (B)
+    const int64_t outer = sideA ? d.M : d.N;
+    const double* base = sideA ? d.A + bidx * d.a_bs : d.B + bidx * d.b_bs;
+    const int64_t os = sideA ? d.a_rs : d.b_cs, is = sideA ? d.a_cs : d.b_rs;
+    const int* ex = sideA ? d.ex_row + bidx * d.M : d.ex_col + bidx * d.N;
     if (tid < 32) {
       const int64_t o = o0 + tid;
       Es[tid] = o < outer ? decode_exp(__ldcg(ex + o), args.epoch) : 0;
@@ -359,47 +369,93 @@ __global__ void __launch_bounds__(256) tc_split_kernel(TcArgs args) {
     split_chunk(d, s, sideA, bidx, tile, quarter, kc, o0, outer, base, os, is, Es);
     return;
   }
-  // short K: the largest exponent of the 32 rows / columns over all of K here,
-  // read as in the exponent pass (no per-element index divisions): with K
-  // contiguous a warp walks K for four rows and takes the maximum by shuffles;
-  // otherwise the lanes take the 32 rows / columns (contiguous) and the warps
-  // split K, combined by shared-memory atomics
-  const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  if (tid < 32) Emax[tid] = -1;
-  __syncthreads();
-  if (is == 1) {
-    for (int o = warp; o < 32; o += nw) {
-      int m = -1;
-      if (o0 + o < outer) {
-        const double* rp = base + (o0 + o) * os;
-        int64_t k = lane;
-        for (; k + 96 < d.K; k += 128) {
-          const double x0 = __ldg(rp + k), x1 = __ldg(rp + k + 32), x2 = __ldg(rp + k + 64), x3 = __ldg(rp + k + 96);
-          m = max(m, max(max(dexp(x0), dexp(x1)), max(dexp(x2), dexp(x3))));
-        }
-        for (; k < d.K; k += 32) m = max(m, dexp(__ldg(rp + k)));
-      }
+  // short K: R rows / columns of one operand tile
+  const int R = lx_rows(nkc);
+  const int ld = R == 32 ? LX_LD1 : LX_LD;
+  const int64_t nsa = int64_t(d.mt) * (TC_BM / R);
+  const int64_t per_batch = nsa + int64_t(d.nt) * (TC_BN / R);
+  const int64_t bidx = local / per_batch;
+  local -= bidx * per_batch;
+  const bool sideA = local < nsa;
+  if (!sideA) local -= nsa;
+  const int per_tile = sideA ? TC_BM / R : TC_BN / R;
+  const int64_t tile = local / per_tile;
+  const int sub = int(local - tile * per_tile);
+  const int64_t o0 = tile * (sideA ? TC_BM : TC_BN) + sub * R;
+  const int64_t outer = sideA ? d.M : d.N;
+  const double* base = sideA ? d.A + bidx * d.a_bs : d.B + bidx * d.b_bs;
+  const int64_t os = sideA ? d.a_rs : d.b_cs, is = sideA ? d.a_cs : d.b_rs;
+  int* ex = sideA ? d.ex_row + bidx * d.M : d.ex_col + bidx * d.N;
+  const int bk = d.bkc;
+  const int kp = int(nkc) * bk;                        // K padded to whole chunks
+  {
+    // slot u of this thread: row o, K position k. K contiguous: a warp walks
+    // K along one row; else the lanes take consecutive rows. Zeros beyond K
+    // and beyond the last row.
+    const bool small = R == 32;
+    const int nsl = small ? 8 : 16;
+    double x[16];
 #pragma unroll
-      for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
-      if (lane == 0) Emax[o] = m;
+    for (int u = 0; u < 16; ++u) {
+      int o, k;
+      if (is == 1) {
+        o = small ? warp + 8 * (u >> 1) : warp;
+        k = small ? lane + 32 * (u & 1) : lane + 32 * u;
+      } else {
+        o = small ? lane : (tid & 7);
+        k = small ? warp + 8 * u : (tid >> 3) + 32 * u;
+      }
+      x[u] = (u < nsl && o0 + o < outer && k < d.K) ? __ldg(base + (o0 + o) * os + int64_t(k) * is) : 0.0;
     }
-  } else {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      int o, k;
+      if (is == 1) {
+        o = small ? warp + 8 * (u >> 1) : warp;
+        k = small ? lane + 32 * (u & 1) : lane + 32 * u;
+      } else {
+        o = small ? lane : (tid & 7);
+        k = small ? warp + 8 * u : (tid >> 3) + 32 * u;
+      }
+      if (u < nsl && k < kp) stg[o * ld + k] = x[u];
+    }
+  }
+  __syncthreads();
+  for (int o = warp; o < R; o += 8) {
     int m = -1;
-    if (o0 + lane < outer) {
-      const double* cp = base + (o0 + lane) * os;
-      for (int64_t k = warp; k < d.K; k += nw) m = max(m, dexp(__ldg(cp + k * is)));
+    for (int k = lane; k < kp; k += 32) m = max(m, dexp(stg[o * ld + k]));
+#pragma unroll
+    for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) {
+      const int tag = m >= 0 ? ((args.epoch << 16) | m) : 0;
+      if (o0 + o < outer) ex[o0 + o] = tag;
+      Es[o] = decode_exp(tag, args.epoch);
     }
-    if (m >= 0) atomicMax(&Emax[lane], m);
   }
   __syncthreads();
-  if (tid < 32) {
-    const int m = Emax[tid];
-    const int tag = m >= 0 ? ((args.epoch << 16) | m) : 0;
-    if (o0 + tid < outer) ex[o0 + tid] = tag;
-    Es[tid] = decode_exp(tag, args.epoch);
+  // split: core matrices (8 rows x 8 K positions) of every chunk over the warps
+  const uint32_t plane = sideA ? uint32_t(TC_BM * bk * 2) : uint32_t(TC_BN * bk * 2);
+  const int cr = lane >> 2, ck = (lane & 3) * 2;
+  const int kgs = bk / 8, ncm = (R / 8) * kgs;
+  uint8_t* dst = sideA ? d.pa + (bidx * d.mt + tile) * nkc * int64_t(s) * plane
+                       : d.pb + (bidx * d.nt + tile) * nkc * int64_t(s) * plane;
+  for (int64_t c = 0; c < nkc; ++c) {
+    for (int cm = warp; cm < ncm; cm += 8) {
+      const int rg = cm / kgs, kg = cm - rg * kgs;
+      const int rl = rg * 8 + cr;                      // row within the block
+      const int kk = int(c) * bk + kg * 8 + ck;
+      int d0[8], d1[8];
+      digits(stg[rl * ld + kk], Es[rl], s, d0);
+      digits(stg[rl * ld + kk + 1], Es[rl], s, d1);
+      uint8_t* dc = dst + c * int64_t(s) * plane + tc::canon_off_w(sub * R + rl, kg * 8 + ck, bk);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q >= s) break;
+        const __nv_bfloat162 h = __floats2bfloat162_rn(int_to_float_small(d0[q]), int_to_float_small(d1[q]));
+        *reinterpret_cast<__nv_bfloat162*>(dc + q * plane) = h;
+      }
+    }
   }
-  __syncthreads();
-  for (int64_t c = 0; c < nkc; ++c) split_chunk(d, s, sideA, bidx, tile, quarter, c, o0, outer, base, os, is, Es);
 }
 
 // ---- pass 3: digit products on the tensor cores
@@ -987,7 +1043,9 @@ void gemm_tc_prepare(std::vector<GemmDesc>& g, int s, int target_ctas, TcPlan* p
       if (d.K > kLocalExpK)
         eb += int64_t(d.batch) *
               (ceil_div(std::max<int64_t>(d.M, 1), EX_OUT) + ceil_div(std::max<int64_t>(d.N, 1), EX_OUT)) * kb;
-      sb += int64_t(d.batch) * (int64_t(d.mt) * 4 + d.nt) * (d.lx ? 1 : d.nkc);
+      const int R = lx_rows(d.nkc);
+      sb += d.lx ? int64_t(d.batch) * (int64_t(d.mt) * (TC_BM / R) + int64_t(d.nt) * (TC_BN / R))
+                 : int64_t(d.batch) * (int64_t(d.mt) * 4 + d.nt) * d.nkc;
       d.ex_row = ex_base ? ex_base + ex : nullptr;
       ex += int64_t(d.batch) * d.M;
       d.ex_col = ex_base ? ex_base + ex : nullptr;
