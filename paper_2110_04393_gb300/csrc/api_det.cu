@@ -271,11 +271,10 @@ int build_det(const DetProblem& P, double tol, int64_t max_rank, double* const* 
     sc.add([=](cudaStream_t s) -> int {
       return svd_trunc_launch(int(k), Rb, tol > 0.0 ? eps : nullptr, rcap, G1, G2, sig, rk + n, s, sbig);
     });
-    // V(X_n) := Q U   (row-major m x k)
-    sc.gemm({gdesc(qtmp, k, 1, G1, k, 1, Xn, k, 1, m, k, k)});
-    // H(X_{n+1}) := (V S)^T H(X_{n+1})
+    // V(X_n) := Q U (row-major m x k) and (V S)^T H(X_{n+1}) into scratch
+    // (copied over H(X_{n+1}) next): independent products, one grouped launch
     const int64_t w = In(n + 1) * Rp[n + 1];
-    sc.gemm({gdesc(G2, 1, k, Xq, w, 1, tmp, w, 1, k, w, k)});
+    sc.gemm({gdesc(qtmp, k, 1, G1, k, 1, Xn, k, 1, m, k, k), gdesc(G2, 1, k, Xq, w, 1, tmp, w, 1, k, w, k)});
     sc.add([=](cudaStream_t s) -> int {
       if (!Xq) return int(TT_OK);
       TTR_CHECK_CUDA(cudaMemcpyAsync(Xq, tmp, sizeof(double) * k * w, cudaMemcpyDeviceToDevice, s));

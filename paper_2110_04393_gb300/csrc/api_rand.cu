@@ -447,14 +447,14 @@ int plan_truncation(Arena& ar, Schedule& sc, int N, const std::vector<int64_t>& 
     sc.add([=](cudaStream_t s) -> int {
       return svd_trunc_launch(int(k), b.Rb, epsp, rcap, b.G1, b.G2, b.sig, b.rk + (n - 1), s, sbig, skip);
     });
-    // new H(X_n) = (Q G1)^T : column-major m x k view of core n
+    // new H(X_n) = (Q G1)^T : column-major m x k view of core n, and
+    // V(X_{n-1}) G2 into scratch (copied over V(X_{n-1}) next): independent
+    // products, one grouped launch
     GemmDesc g1 = gdesc(b.Qt, k, 1, b.G1, k, 1, Xn, 1, m, m, k, k);
     g1.skip = skip;
-    sc.gemm({g1});
-    // V(X_{n-1}) := V(X_{n-1}) G2
     GemmDesc g2 = gdesc(Xp, k, 1, b.G2, k, 1, b.tmp, k, 1, mp, k, k);
     g2.skip = skip;
-    sc.gemm({g2});
+    sc.gemm({g1, g2});
     sc.add([=](cudaStream_t s) -> int { return copy_if_launch(Xp, b.tmp, mp * k, skip, s); });
   }
   // compact every core to its decided ranks
