@@ -57,10 +57,12 @@ __global__ void sketch_kernel(double* out, int64_t E, int core_index, uint32_t k
     k0 = uint32_t(sd);
     k1 = uint32_t(sd >> 32);
   }
+  // equal contiguous chunks per block: the pairs are FP64-bound (log, sqrt,
+  // sincospi), so the SM with the most pairs sets the kernel's length
   const int64_t npairs = (E + 1) / 2;
-  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < npairs;
-       p += int64_t(gridDim.x) * blockDim.x)
-    sketch_pair(out, E, p, core_index, k0, k1, stdv);
+  const int64_t chunk = (npairs + gridDim.x - 1) / gridDim.x;
+  const int64_t p0 = blockIdx.x * chunk, p1 = min(npairs, p0 + chunk);
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) sketch_pair(out, E, p, core_index, k0, k1, stdv);
 }
 
 // Many sketch cores at once: job blockIdx.y, its pairs over blockIdx.x.
@@ -144,8 +146,9 @@ int sketch_launch(double* out, int64_t r0, int64_t I, int64_t r1, int core_index
   if (E <= 0) return TT_OK;
   const double stdv = 1.0 / std::sqrt(double(r0) * double(I) * double(r1));
   TTR_PREFER_SHARED(sketch_kernel);
-  sketch_kernel<<<grid_for((E + 1) / 2, 256), 256, 0, s>>>(out, E, core_index, uint32_t(seed),
-                                                            uint32_t(seed >> 32), stdv, seed_dev);
+  // two blocks per SM, each an equal share of the pairs (at least 32)
+  const unsigned nb = unsigned(std::max<int64_t>(1, std::min<int64_t>(2 * int64_t(num_sms()), ceil_div((E + 1) / 2, 32))));
+  sketch_kernel<<<nb, 256, 0, s>>>(out, E, core_index, uint32_t(seed), uint32_t(seed >> 32), stdv, seed_dev);
   TTR_CHECK_LAUNCH();
   prof_count_launch(1);
   return TT_OK;
